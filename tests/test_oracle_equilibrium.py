@@ -1,0 +1,91 @@
+"""Equilibrium pins of the oracle's Markov chain (CPU only).
+
+Long oracle runs are compared with exact values: enumeration (Eq. 1) on 4x4,
+2x2x2 and 3x3x3 lattices, Kaufman's finite-torus <E>, and Onsager's
+infinite-lattice energy and spontaneous magnetisation.  Error bars come from
+blocking analysis; the acceptance bands are 5 sigma.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+
+Z5 = 5.0
+
+
+def _check(series, want, what, extra=0.0):
+    mean = float(np.mean(series))
+    err = exact.blocking_error(series)
+    assert abs(mean - want) <= Z5 * err + extra, \
+        f"{what}: got {mean:.6f} +- {err:.2e}, exact {want:.6f}"
+
+
+@pytest.mark.parametrize("dims,L,beta,nsweeps", [
+    (2, 4, 0.2, 200_000),
+    (2, 4, exact.BETA_C_2D, 400_000),
+    (2, 4, 0.6, 200_000),
+    (3, 2, 0.15, 200_000),
+    (3, 2, 0.2216544, 200_000),
+    (3, 2, 0.3, 200_000),
+])
+def test_checkerboard_vs_enumeration(orc, dims, L, beta, nsweeps):
+    hist = orc.enumerate_states(dims, L)
+    want = exact.boltzmann_averages(hist, dims, L, beta)
+    _, E, M = orc.run(dims, L, beta, 4242, nsweeps, measure_every=1)
+    E = E[1000:].astype(np.float64)
+    M = M[1000:].astype(np.float64)
+    _check(E, want["E"], "E")
+    _check(M * M, want["M2"], "M^2")
+    _check(np.abs(M), want["absM"], "|M|")
+
+
+@pytest.mark.parametrize("beta", [0.15, 0.2216544, 0.3])
+def test_sequential_3x3x3_vs_enumeration(orc, beta):
+    """Odd L has no checkerboard; the sequential single-site chain uses the
+    same acceptance rule and thresholds and must reach Eq. 1's averages."""
+    hist = orc.enumerate_states(3, 3)
+    want = exact.boltzmann_averages(hist, 3, 3, beta)
+    _, E, M = orc.run(3, 3, beta, 777, 150_000, measure_every=1, sequential=True)
+    E = E[1000:].astype(np.float64)
+    M = M[1000:].astype(np.float64)
+    _check(E, want["E"], "E")
+    _check(M * M, want["M2"], "M^2")
+
+
+@pytest.mark.parametrize("L,beta,nsweeps", [(16, 0.40, 150_000), (32, 0.4406868, 120_000)])
+def test_kaufman_finite_torus_energy(orc, L, beta, nsweeps):
+    want = exact.kaufman_mean_energy(beta, L)
+    _, E, _ = orc.run(2, L, beta, 31337, nsweeps, measure_every=1)
+    _check(E[2000:].astype(np.float64), want, f"<E> L={L}")
+
+
+@pytest.mark.parametrize("beta,start", [(0.30, oracle.HOT), (0.50, oracle.COLD_UP),
+                                        (0.60, oracle.COLD_UP)])
+def test_onsager_energy_and_magnetisation(orc, beta, start):
+    """L = 128 is many correlation lengths at these betas, so the infinite-
+    lattice values apply up to exponentially small corrections."""
+    L, nsweeps, burn = 128, 3000, 300
+    n = L * L
+    _, E, M = orc.run(2, L, beta, 1000 + int(beta * 100), nsweeps, measure_every=1,
+                      start=start)
+    u = E[burn:].astype(np.float64) / n
+    _check(u, exact.onsager_energy_per_site(beta), f"u({beta})", extra=2e-4)
+    if beta > exact.BETA_C_2D:
+        m = np.abs(M[burn:].astype(np.float64)) / n
+        _check(m, exact.onsager_magnetization(beta), f"m({beta})", extra=1e-3)
+
+
+def test_critical_energy_approaches_minus_sqrt2():
+    """Onsager: u(beta_c) = -sqrt 2.  Kaufman's exact finite-torus energy per
+    site approaches it with a 1/L correction: L * (u_L + sqrt 2) settles to a
+    constant as L doubles (this ties the finite-L formula, which pins the
+    oracle above, to the infinite-lattice closed form)."""
+    d = {L: abs(exact.kaufman_mean_energy(exact.BETA_C_2D, L) / L ** 2 + math.sqrt(2.0))
+         for L in (16, 32, 64, 128)}
+    assert d[16] > d[32] > d[64] > d[128] > 0
+    scaled = [L * d[L] for L in (32, 64, 128)]
+    assert abs(scaled[2] - scaled[1]) < 0.02 * scaled[2]
+    assert d[128] < 6e-3
