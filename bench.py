@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: checkerboard-Metropolis sweeps of the 2D Ising beta scan.
+
+Workload (default): 2D square lattice L = 8192 (67,108,864 sites), 16 betas
+evenly spaced in [0.30, 0.60], cold start (all +1), seeds 20031109 + j, E and M
+recorded after every sweep, int8 layout.  One step = one sweep (black pass,
+white pass, fused E/M) of each of the 16 lattices in turn, so the 1 GiB of
+spin state that a step touches is far larger than the 129 MB L2 between
+timed iterations.  The default K = 2000 steps is the full run of the
+workload; the lattices are re-initialised (cold) inside the timed region.
+
+Metric: site updates per second (attempted single-spin Metropolis updates,
+one per site per sweep), whole job over all ranks.
+
+Arms
+  default          the CUDA engine (C ABI via ctypes), device-timed with CUDA
+                   events; plus an end-to-end figure through the same public
+                   API with host buffers (initial spins uploaded from pinned
+                   host memory, E/M read back to the host every step, final
+                   spins read back), a roofline object for the int8 pass
+                   kernel, clock samples, and the CPU oracle timed on a
+                   bounded sample (rank 0, N = 1).
+  --impl reference the CPU oracle (single-threaded C) on the same workload,
+                   each step a bounded sample sized so the run ends in
+                   minutes.
+
+Multi-GPU (torchrun): every rank runs its own 16 independent lattices (seeds
+offset by 16 * rank), no collective on the data path; scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L_SCAN = 8192
+N_BETA = 16
+BASE_SEED = 20031109
+BYTES_PER_UPDATE_INT8 = 3  # per colour pass: read own N/2, read other N/2, write own N/2
+
+
+def scan_betas():
+    return [round(0.30 + 0.02 * j, 10) for j in range(N_BETA)]
+
+
+def workload_config(L: int, steps: int) -> dict:
+    return {"workload": f"2D Ising beta scan: L={L} square lattice, 16 betas evenly spaced in "
+                        f"[0.30,0.60], cold start, {steps} sweeps, E/M every sweep",
+            "lattices_per_gpu": N_BETA,
+            "l2": "inputs larger than L2: a step touches 16 x L^2 bytes of int8 spins",
+            "step": "one sweep (black pass, white pass, fused E/M) of each lattice"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(budget_s: float, L: int, betas, n_lattices: int):
+    """Time the oracle (as it stands) sweeping cold-started lattices of size L
+    with E/M recomputed after each sweep; returns (updates/s, description)."""
+    import oracle
+    oracle.build()
+    done = 0
+    t0 = time.perf_counter()
+    j = 0
+    while True:
+        b = betas[j % len(betas)]
+        oracle.run(2, L, b, BASE_SEED + (j % len(betas)), 1, measure_every=1,
+                   start=oracle.COLD_UP)
+        done += L * L
+        j += 1
+        if time.perf_counter() - t0 >= budget_s or j >= n_lattices:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, f"{j} single sweeps (cold start, E/M after each) of 2D L={L} lattices"
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    betas = scan_betas()
+    total_steps = args.steps + args.warmup
+    # each step sweeps one lattice once; pick the largest L <= 8192 whose whole
+    # run stays within ~90 s at the oracle's ~2.5e7 updates/s
+    L = args.L
+    while L > 64 and total_steps * L * L / 2.5e7 > 90.0:
+        L //= 2
+    import oracle
+    oracle.build()
+    for w in range(args.warmup):
+        oracle.run(2, L, betas[w % N_BETA], BASE_SEED + w, 1, measure_every=1,
+                   start=oracle.COLD_UP)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        j = k % N_BETA
+        oracle.run(2, L, betas[j], BASE_SEED + j, 1, measure_every=1, start=oracle.COLD_UP)
+    dt = time.perf_counter() - t0
+    value = args.steps * L * L / dt
+    sample = (f"each step: one sweep (cold start, E/M recomputed) of one 2D L={L} lattice "
+              f"of the 16-beta scan (beta cycling), single-threaded C oracle; the workload's "
+              f"L={args.L} is sampled at L={L} so that {total_steps} steps end in minutes")
+    line = {
+        "impl": "reference", "metric": "site updates/s", "value": value,
+        "unit": "site updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": workload_config(args.L, args.steps),
+        "cpu_baseline": {"value": value, "unit": "site updates/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "site updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the engine has no CPU path)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_cs_0312006_gb300 import _build, engine
+    _build.build()
+    engine.load_library()
+
+    L = args.L
+    n_sites = L * L
+    betas = scan_betas()
+    stream = torch.cuda.current_stream()
+    lats = [engine.Lattice(2, L, b, BASE_SEED + 16 * rank + j, layout=engine.INT8,
+                           start=engine.COLD_UP, stream=stream)
+            for j, b in enumerate(betas)]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---------------- device-timed value ----------------
+    for _ in range(args.warmup):
+        for lat in lats:
+            lat.sweep(1, 1)
+    for lat in lats:
+        lat.observables()
+    torch.cuda.synchronize()
+
+    # events around every lattice's sweep call on timed steps, read after the run
+    pairs = []
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for lat in lats:
+        lat.init(engine.COLD_UP)
+    for k in range(args.steps):
+        time_this = k % args.time_every == 0
+        for lat in lats:
+            if time_this:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lat.sweep(1, 1)
+                e1.record(stream)
+                pairs.append((e0, e1))
+            else:
+                lat.sweep(1, 1)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(stop)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = world * len(lats) * n_sites * args.steps
+    value = updates / (ms / 1e3)
+    # E/M sanity: every step recorded one (E, M) per lattice
+    n_rec = [len(lat.observables()[0]) for lat in lats]
+    assert all(n == args.steps for n in n_rec), n_rec
+
+    pass_ms = sum(a.elapsed_time(b) for a, b in pairs) / (2 * len(pairs))
+    bytes_per_pass = BYTES_PER_UPDATE_INT8 * n_sites // 2
+    peak, peak_kind = load_peaks()
+    achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
+
+    # ---------------- end to end through the C ABI, host buffers ----------------
+    e2e = None
+    if not args.no_e2e:
+        host_init = torch.ones(n_sites, dtype=torch.int8).pin_memory().numpy()
+        host_out = [torch.empty(n_sites, dtype=torch.int8).pin_memory().numpy()
+                    for _ in range(len(lats))]
+        e2e_steps = args.e2e_steps or args.steps
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for lat in lats:
+            lat.set_spins(host_init, 0)  # H2D of the initial configuration
+        d2h = 0
+        for k in range(e2e_steps):
+            for lat in lats:
+                lat.sweep(1, 1)
+            for lat in lats:
+                E, M = lat.observables()  # D2H of this step's (E, M)
+                d2h += 16 * len(E)
+        for j, lat in enumerate(lats):
+            lat.get_spins(host_out[j])  # D2H of the final configuration
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d_total = len(lats) * n_sites
+        d2h_total = d2h + len(lats) * n_sites
+        e2e = {"value": world * len(lats) * n_sites * e2e_steps / dt, "unit": "site updates/s",
+               "h2d_bytes_per_step": h2d_total / e2e_steps,
+               "d2h_bytes_per_step": d2h_total / e2e_steps, "steps": e2e_steps,
+               "note": "ising_set_spins from pinned host memory, then per step one sweep of each "
+                       "lattice and ising_observables to host, then ising_get_spins"}
+
+    for lat in lats:
+        lat.close()
+
+    if rank != 0:
+        return 0
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, sample = oracle_sample_rate(args.cpu_seconds, L_SCAN, betas, 64)
+        cpu = {"value": rate, "unit": "site updates/s", "cores": 1, "kind": "oracle",
+               "sample": sample}
+
+    line = {
+        "metric": "site updates/s", "value": value, "unit": "site updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+        "data": "synthetic",
+        "config": workload_config(L, args.steps),
+        "layout": "int8 half-lattice per colour",
+        "roofline": {"kernel": "pass_int8_vec<2,measure>", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
+                     "peak_source": peak_kind},
+        "gpu_launches": len(lats) * (2 * args.steps + 1),
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--L", type=int, default=L_SCAN)
+    ap.add_argument("--time-every", type=int, default=1,
+                    help="time each lattice's sweep with events on every k-th step")
+    ap.add_argument("--e2e-steps", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "engine":
+        raise SystemExit("bench.py: at least 3 warm-up steps are required")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

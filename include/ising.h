@@ -1,0 +1,163 @@
+/*
+ * ising.h -- C ABI of the GB300 checkerboard-Metropolis Ising engine.
+ *
+ * The engine simulates the Ising model of Tomov et al. (2003), Sec. 2.2: spins
+ * s = +-1 on a periodic 2D square or 3D cubic lattice of linear size L, energy
+ * E = -sum over nearest-neighbour bonds of s_j s_k (J = 1, no field) and
+ * magnetisation M = sum of s.  One sweep is a pass over all black sites
+ * (x+y[+z] even) followed by a pass over all white sites (Sec. 2.2,
+ * "consecutive black and white sweeps"); each site flips by the Metropolis
+ * rule of Sec. 2.2 with dE = 2k, k = s_i * (sum of its neighbours): k <= 0
+ * always flips, k > 0 flips iff u < floor(exp(-2 beta k) 2^32), where u is the
+ * 32-bit Philox4x32-10 draw keyed by (seed) and counted by (site, sweep,
+ * colour), so results do not depend on layout or launch shape.  The per-sweep
+ * E and M are reduced inside the sweep kernels.
+ *
+ * Conventions shared by every call:
+ *   - Canonical site order: i = x + L*y (+ L*L*z), x fastest; spins are int8
+ *     +1 / -1 in host and device spin buffers.
+ *   - Every call returns ISING_OK (0) or a negative ISING_E* code; nothing
+ *     aborts.  ising_strerror() names a code.  After ISING_ECUDA the handle
+ *     should be destroyed.
+ *   - Handles are not thread-safe: one handle, one thread at a time.
+ *   - Work is issued on the handle's CUDA stream (default: the legacy default
+ *     stream); calls that return host data synchronise that stream.
+ *   - The library owns all device memory it allocates for a handle and frees
+ *     it in ising_destroy().
+ */
+#ifndef ISING_GB300_H
+#define ISING_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ising_lattice ising_lattice; /* opaque, owned by the library */
+
+/* Spin layouts on the device. */
+enum {
+    ISING_INT8 = 0,    /* one int8 per site, one array per colour (the two-lattice
+                          checkerboard of Sec. 5), row-major half rows */
+    ISING_BITPACK = 1, /* 32 same-colour sites per uint32 word; L % 64 == 0 */
+    ISING_AUTO = 2     /* the engine picks; never changes results */
+};
+
+/* Initial states (Sec. 2.2: spins up with probability p). */
+enum {
+    ISING_HOT = 0,       /* p = 1/2: s_i = +1 iff Philox(seed; i>>2, 0, 0, 1)[i&3] < 2^31 */
+    ISING_COLD_UP = 1,   /* p = 1: all +1 */
+    ISING_COLD_DOWN = 2  /* p = 0: all -1 */
+};
+
+/* Status codes. */
+enum {
+    ISING_OK = 0,
+    ISING_EINVAL = -1,   /* invalid argument */
+    ISING_ENOMEM = -2,   /* device or host allocation failed */
+    ISING_ECUDA = -3,    /* a CUDA call failed */
+    ISING_ETIMEOUT = -4, /* a bounded device wait gave up */
+    ISING_EBUDGET = -5,  /* would exceed a memory budget */
+    ISING_ERANGE = -6    /* counter/capacity exhausted or buffer too small */
+};
+
+typedef struct ising_info_t {
+    int dims;              /* 2 or 3 */
+    int L;                 /* linear size */
+    int layout;            /* ISING_INT8 or ISING_BITPACK (never AUTO) */
+    int reserved;
+    double beta;           /* inverse temperature J/kT */
+    uint64_t seed;         /* Philox key */
+    uint64_t sweeps_done;  /* global sweep counter t (next sweep's index) */
+    uint64_t sites;        /* L^dims */
+    uint64_t device_bytes; /* device memory held by the spin arrays */
+    int64_t pending_records; /* E/M records not yet read by ising_observables */
+} ising_info_t;
+
+/*
+ * Create a lattice and put it in the hot start (ISING_HOT), sweep counter 0.
+ *   out    receives the handle (set to NULL on failure).
+ *   dims   2 or 3.
+ *   L      even, >= 2 (odd L has no valid checkerboard on a torus: the wrap
+ *          bond would join two sites of one colour); ISING_BITPACK needs
+ *          L % 64 == 0; L^dims <= 2^34.
+ *   beta   > 0 (may be +inf for a zero-temperature quench).  The thresholds
+ *          floor(exp(-2 beta k) 2^32), k = 2..2*dims, are built on the host;
+ *          a beta whose exact value lies within 2^-24 of an integer boundary
+ *          at long-double precision is rejected with ISING_EINVAL.
+ *   seed   64-bit Philox key (low word, high word).
+ *   layout ISING_INT8, ISING_BITPACK or ISING_AUTO.
+ * Allocates device memory; issues the init kernel on the default stream.
+ */
+int ising_create(ising_lattice **out, int dims, int L, double beta,
+                 uint64_t seed, int layout);
+
+/* Re-initialise the spins (ISING_HOT / ISING_COLD_UP / ISING_COLD_DOWN), reset
+ * the sweep counter to 0 and drop pending E/M records. Asynchronous. */
+int ising_init(ising_lattice *lat, int start);
+
+/*
+ * Run n >= 0 sweeps, numbered t, t+1, ..., t+n-1 (t = sweeps done so far).
+ * After sweep number u the fused kernels record (E, M) iff
+ * (u + 1) % measure_every == 0 (measure_every >= 1).  Asynchronous on the
+ * handle's stream; may grow the device record buffer.  ISING_ERANGE if the
+ * counter would pass 2^32 - 1.
+ */
+int ising_sweep(ising_lattice *lat, int64_t n, int measure_every);
+
+/*
+ * Read the pending E/M records (oldest first) and clear them.  Synchronises
+ * the stream.  *count receives the number pending.  With E == NULL or
+ * M == NULL only the count is reported.  If cap < pending nothing is copied,
+ * nothing is cleared and ISING_ERANGE is returned.
+ */
+int ising_observables(ising_lattice *lat, int64_t *E, int64_t *M, int64_t cap,
+                      int64_t *count);
+
+/* Copy the spins to host memory in canonical order (L^dims int8).  Syncs. */
+int ising_get_spins(ising_lattice *lat, int8_t *host_out);
+
+/* Load spins (canonical int8 +-1, host memory) and set the sweep counter to
+ * t; pending records are dropped.  Values other than +-1 give ISING_EINVAL
+ * (checked on the host before anything changes).  Syncs. */
+int ising_set_spins(ising_lattice *lat, const int8_t *host_in, uint64_t t);
+
+/* Write the spins in canonical order into caller-owned DEVICE memory
+ * (L^dims bytes).  Asynchronous on the handle's stream. */
+int ising_export_device(ising_lattice *lat, int8_t *dev_out);
+
+/* Use this CUDA stream (a cudaStream_t, may be NULL = legacy default stream)
+ * for all later work of the handle.  The caller keeps ownership. */
+int ising_set_stream(ising_lattice *lat, void *stream);
+
+/* The thresholds in use: out[j] = floor(exp(-2 beta (2j+2)) 2^32) for
+ * j < dims, 0 beyond. */
+int ising_thresholds(const ising_lattice *lat, uint32_t out[3]);
+
+/* The same thresholds for (dims, beta) without a handle or a GPU (host-only
+ * computation; ISING_EINVAL for dims not in {2,3}, beta <= 0 or NaN, or a
+ * beta whose floor cannot be decided as described at ising_create). */
+int ising_compute_thresholds(int dims, double beta, uint32_t out[3]);
+
+/* Describe the handle. */
+int ising_get_info(const ising_lattice *lat, ising_info_t *out);
+
+/* Block until the handle's stream is idle. */
+int ising_synchronize(ising_lattice *lat);
+
+/* Free everything the handle owns.  NULL is accepted. */
+void ising_destroy(ising_lattice *lat);
+
+/* Static description of a status code. */
+const char *ising_strerror(int code);
+
+/* Library version string. */
+const char *ising_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_GB300_H */

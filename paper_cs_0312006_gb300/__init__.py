@@ -1,0 +1,12 @@
+"""GB300-native checkerboard-Metropolis Ising engine (2D square / 3D cubic,
+J = 1, h = 0, periodic), after Tomov et al. (2003), Sec. 2.2.
+
+The simulation runs in hand-written CUDA kernels for sm_103a behind the C ABI
+of ``include/ising.h``; ``engine`` is its Python binding.  There is no CPU
+fallback: without the compiled library, ``engine.load_library()`` raises.
+"""
+from .engine import (AUTO, BITPACK, COLD_DOWN, COLD_UP, HOT, INT8, IsingError,  # noqa: F401
+                     Lattice, load_library)
+
+__all__ = ["Lattice", "IsingError", "load_library", "INT8", "BITPACK", "AUTO", "HOT",
+           "COLD_UP", "COLD_DOWN"]

@@ -1,0 +1,382 @@
+// engine.cu -- host side of the C ABI declared in include/ising.h: lattice
+// handles, acceptance thresholds, the per-sweep launch sequence and the E/M
+// record buffer.  All simulation arithmetic runs in the kernels of
+// sweep_int8.cu / sweep_bitpack.cu.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "engine_internal.h"
+#include "ising.h"
+#include "ising_device.cuh"
+
+using ising::DeviceProps;
+using ising::PassArgs;
+
+struct ising_lattice {
+    int dims = 0, L = 0, layout = ISING_INT8;
+    double beta = 0.0;
+    uint64_t seed = 0;
+    uint32_t thr[3] = {0, 0, 0};
+    int64_t sites = 0, half_sites = 0, rows = 0;
+    int W = 0;
+    void* col[2] = {nullptr, nullptr};  // colour 0 (black) and colour 1 (white) arrays
+    size_t col_bytes = 0;
+    uint64_t t = 0;                     // index of the next sweep
+    cudaStream_t stream = nullptr;
+    unsigned long long* obs = nullptr;  // (E, M) int64 pairs
+    int64_t obs_cap = 0, n_rec = 0;
+    const DeviceProps* dp = nullptr;
+};
+
+namespace {
+
+constexpr uint64_t kMaxSites = 1ull << 34;
+constexpr uint64_t kMaxSweep = 0xFFFFFFFFull;  // the sweep index is a 32-bit counter word
+
+std::mutex g_props_mu;
+DeviceProps g_props[64];
+
+int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? ISING_ENOMEM : ISING_ECUDA; }
+
+#define ISING_CHECK(call)                          \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+int device_props(const DeviceProps** out) {
+    int dev = 0;
+    ISING_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return ISING_ECUDA;
+    std::lock_guard<std::mutex> lk(g_props_mu);
+    DeviceProps& p = g_props[dev];
+    if (p.device != dev) {
+        DeviceProps q;
+        q.device = dev;
+        ISING_CHECK(cudaDeviceGetAttribute(&q.sm_count, cudaDevAttrMultiProcessorCount, dev));
+        ISING_CHECK(ising::int8_query_occupancy(q));
+        p = q;
+    }
+    *out = &p;
+    return ISING_OK;
+}
+
+// floor(exp(-x) * 2^32) for x = 2 beta k > 0, decided exactly.  The double
+// result is accepted when a relative bracket of 2^-40 around it (far wider than
+// the error of exp() and of forming x) holds no integer; otherwise the value
+// is recomputed in long double with a 2^-56 bracket; if even that straddles an
+// integer the input is refused rather than rounded either way.
+int floor_exp_scaled(double beta, int k, uint32_t* out) {
+    const double x = 2.0 * beta * (double)k;
+    if (std::isinf(x)) {
+        *out = 0u;
+        return ISING_OK;
+    }
+    if (x < 0x1p-33) {  // 2^32 (1 - x) <= value < 2^32, so the floor is 2^32 - 1
+        *out = 0xFFFFFFFFu;
+        return ISING_OK;
+    }
+    const double v = std::ldexp(std::exp(-x), 32);
+    const double lo = v * (1.0 - 0x1p-40), hi = v * (1.0 + 0x1p-40);
+    if (hi < 1.0) {
+        *out = 0u;
+        return ISING_OK;
+    }
+    if (std::floor(lo) == std::floor(hi)) {
+        *out = (uint32_t)std::floor(v);
+        return ISING_OK;
+    }
+    const long double xl = 2.0L * (long double)beta * (long double)k;
+    const long double vl = std::ldexp(std::exp(-xl), 32);
+    const long double lol = vl * (1.0L - 0x1p-56L), hil = vl * (1.0L + 0x1p-56L);
+    if (std::floor(lol) != std::floor(hil)) return ISING_EINVAL;
+    *out = (uint32_t)std::floor(vl);
+    return ISING_OK;
+}
+
+int build_thresholds(int dims, double beta, uint32_t thr[3]) {
+    if (!(beta > 0.0)) return ISING_EINVAL;  // also rejects NaN
+    thr[0] = thr[1] = thr[2] = 0u;
+    for (int j = 0; j < dims; ++j) {
+        const int rc = floor_exp_scaled(beta, 2 * (j + 1), &thr[j]);
+        if (rc != ISING_OK) return rc;
+    }
+    return ISING_OK;
+}
+
+void free_device(ising_lattice* h) {
+    for (void*& p : h->col) {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
+    if (h->obs) cudaFree(h->obs);
+    h->obs = nullptr;
+    h->obs_cap = 0;
+}
+
+// Record slots at index >= n_rec are kept zero, so a sweep call never needs
+// its own memset: the fused kernels add into already-zeroed slots.
+int ensure_records(ising_lattice* h, int64_t need) {
+    if (need <= h->obs_cap) return ISING_OK;
+    int64_t cap = h->obs_cap * 2;
+    if (cap < need) cap = need;
+    if (cap < 64) cap = 64;
+    unsigned long long* nb = nullptr;
+    ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&nb), (size_t)cap * 16, h->stream));
+    ISING_CHECK(cudaMemsetAsync(nb, 0, (size_t)cap * 16, h->stream));
+    if (h->n_rec > 0)
+        ISING_CHECK(cudaMemcpyAsync(nb, h->obs, (size_t)h->n_rec * 16, cudaMemcpyDeviceToDevice,
+                                    h->stream));
+    if (h->obs) ISING_CHECK(cudaFreeAsync(h->obs, h->stream));
+    h->obs = nb;
+    h->obs_cap = cap;
+    return ISING_OK;
+}
+
+// Drop pending records and restore the zero invariant of their slots.
+int clear_records(ising_lattice* h) {
+    if (h->n_rec > 0)
+        ISING_CHECK(cudaMemsetAsync(h->obs, 0, (size_t)h->n_rec * 16, h->stream));
+    h->n_rec = 0;
+    return ISING_OK;
+}
+
+int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
+    PassArgs a;
+    a.own = h->col[c];
+    a.other = h->col[1 - c];
+    a.obs = slot;
+    a.rows = h->rows;
+    a.L = h->L;
+    a.W = h->W;
+    a.thr0 = h->thr[0];
+    a.thr1 = h->thr[1];
+    a.thr2 = h->thr[2];
+    a.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
+    a.key1 = (uint32_t)(h->seed >> 32);
+    a.t = t;
+    a.c = c;
+    ISING_CHECK(ising::int8_pass(a, h->dims, h->half_sites, slot != nullptr, *h->dp, h->stream));
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ising_version(void) { return "paper_cs_0312006_gb300 1.0 (sm_103a)"; }
+
+const char* ising_strerror(int code) {
+    switch (code) {
+        case ISING_OK: return "ok";
+        case ISING_EINVAL: return "invalid argument";
+        case ISING_ENOMEM: return "out of memory";
+        case ISING_ECUDA: return "CUDA error";
+        case ISING_ETIMEOUT: return "bounded device wait timed out";
+        case ISING_EBUDGET: return "memory budget exceeded";
+        case ISING_ERANGE: return "counter or capacity out of range";
+        default: return "unknown status";
+    }
+}
+
+int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t seed, int layout) {
+    if (!out) return ISING_EINVAL;
+    *out = nullptr;
+    if (dims != 2 && dims != 3) return ISING_EINVAL;
+    if (L < 2 || (L & 1)) return ISING_EINVAL;
+    if (layout != ISING_INT8 && layout != ISING_BITPACK && layout != ISING_AUTO)
+        return ISING_EINVAL;
+    const uint64_t sites = dims == 2 ? (uint64_t)L * L : (uint64_t)L * L * L;
+    if ((uint64_t)L > (1u << 20) || sites > kMaxSites) return ISING_EINVAL;
+    if (layout == ISING_BITPACK) return ISING_EINVAL;  // bit-packed layout: not built yet
+    uint32_t thr[3];
+    int rc = build_thresholds(dims, beta, thr);
+    if (rc != ISING_OK) return rc;
+    const DeviceProps* dp = nullptr;
+    rc = device_props(&dp);
+    if (rc != ISING_OK) return rc;
+
+    ising_lattice* h = new (std::nothrow) ising_lattice();
+    if (!h) return ISING_ENOMEM;
+    h->dims = dims;
+    h->L = L;
+    h->layout = ISING_INT8;
+    h->beta = beta;
+    h->seed = seed;
+    std::memcpy(h->thr, thr, sizeof(thr));
+    h->sites = (int64_t)sites;
+    h->half_sites = (int64_t)(sites / 2);
+    h->W = L / 2;
+    h->rows = dims == 2 ? L : (int64_t)L * L;
+    h->dp = dp;
+    h->col_bytes = ((size_t)h->half_sites + 15) & ~(size_t)15;
+    for (int c = 0; c < 2; ++c) {
+        cudaError_t e = cudaMalloc(&h->col[c], h->col_bytes);
+        if (e != cudaSuccess) {
+            free_device(h);
+            delete h;
+            return cuda_fail(e);
+        }
+    }
+    rc = ising_init(h, ISING_HOT);
+    if (rc != ISING_OK) {
+        free_device(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return ISING_OK;
+}
+
+int ising_init(ising_lattice* h, int start) {
+    if (!h) return ISING_EINVAL;
+    if (start != ISING_HOT && start != ISING_COLD_UP && start != ISING_COLD_DOWN)
+        return ISING_EINVAL;
+    ISING_CHECK(ising::int8_init(static_cast<int8_t*>(h->col[0]), static_cast<int8_t*>(h->col[1]),
+                                 h->L, h->dims, h->sites, start,
+                                 (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32),
+                                 *h->dp, h->stream));
+    h->t = 0;
+    return clear_records(h);
+}
+
+int ising_sweep(ising_lattice* h, int64_t n, int measure_every) {
+    if (!h || n < 0 || measure_every < 1) return ISING_EINVAL;
+    if (n == 0) return ISING_OK;
+    if (h->t + (uint64_t)n - 1 > kMaxSweep) return ISING_ERANGE;
+    const uint64_t every = (uint64_t)measure_every;
+    const int64_t new_rec = (int64_t)((h->t + (uint64_t)n) / every - h->t / every);
+    if (new_rec > 0) {
+        int rc = ensure_records(h, h->n_rec + new_rec);
+        if (rc != ISING_OK) return rc;
+    }
+    int64_t rec = h->n_rec;
+    for (int64_t s = 0; s < n; ++s) {
+        const uint64_t t = h->t + (uint64_t)s;
+        unsigned long long* slot = nullptr;
+        if ((t + 1) % every == 0) slot = h->obs + 2 * (rec++);
+        int rc = run_pass(h, 0, (uint32_t)t, slot);
+        if (rc == ISING_OK) rc = run_pass(h, 1, (uint32_t)t, slot);
+        if (rc != ISING_OK) return rc;
+    }
+    h->t += (uint64_t)n;
+    h->n_rec = rec;
+    return ISING_OK;
+}
+
+int ising_observables(ising_lattice* h, int64_t* E, int64_t* M, int64_t cap, int64_t* count) {
+    if (!h) return ISING_EINVAL;
+    ISING_CHECK(cudaStreamSynchronize(h->stream));
+    if (count) *count = h->n_rec;
+    if (!E || !M) return ISING_OK;
+    if (cap < h->n_rec) return ISING_ERANGE;
+    if (h->n_rec > 0) {
+        std::vector<long long> buf((size_t)h->n_rec * 2);
+        ISING_CHECK(cudaMemcpy(buf.data(), h->obs, buf.size() * 8, cudaMemcpyDeviceToHost));
+        for (int64_t r = 0; r < h->n_rec; ++r) {
+            E[r] = buf[2 * r];
+            M[r] = buf[2 * r + 1];
+        }
+    }
+    return clear_records(h);
+}
+
+int ising_export_device(ising_lattice* h, int8_t* dev_out) {
+    if (!h || !dev_out) return ISING_EINVAL;
+    ISING_CHECK(ising::int8_export(static_cast<const int8_t*>(h->col[0]),
+                                   static_cast<const int8_t*>(h->col[1]), dev_out, h->L,
+                                   h->dims, h->sites, *h->dp, h->stream));
+    return ISING_OK;
+}
+
+int ising_get_spins(ising_lattice* h, int8_t* host_out) {
+    if (!h || !host_out) return ISING_EINVAL;
+    int8_t* tmp = nullptr;
+    ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+    int rc = ising_export_device(h, tmp);
+    if (rc == ISING_OK) {
+        cudaError_t e = cudaMemcpyAsync(host_out, tmp, (size_t)h->sites, cudaMemcpyDeviceToHost,
+                                        h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+    }
+    cudaFreeAsync(tmp, h->stream);
+    if (rc != ISING_OK) return rc;
+    ISING_CHECK(cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
+int ising_set_spins(ising_lattice* h, const int8_t* host_in, uint64_t t) {
+    if (!h || !host_in) return ISING_EINVAL;
+    if (t > kMaxSweep + 1) return ISING_ERANGE;
+    for (int64_t i = 0; i < h->sites; ++i)
+        if (host_in[i] != 1 && host_in[i] != -1) return ISING_EINVAL;
+    int8_t* tmp = nullptr;
+    ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+    cudaError_t e = cudaMemcpyAsync(tmp, host_in, (size_t)h->sites, cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess)
+        e = ising::int8_import(static_cast<int8_t*>(h->col[0]), static_cast<int8_t*>(h->col[1]),
+                               tmp, h->L, h->dims, h->sites, *h->dp, h->stream);
+    cudaFreeAsync(tmp, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->t = t;
+    int rc = clear_records(h);
+    if (rc != ISING_OK) return rc;
+    ISING_CHECK(cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
+int ising_set_stream(ising_lattice* h, void* stream) {
+    if (!h) return ISING_EINVAL;
+    if (h->stream != static_cast<cudaStream_t>(stream)) {
+        // order the new stream after everything already issued on the old one
+        ISING_CHECK(cudaStreamSynchronize(h->stream));
+    }
+    h->stream = static_cast<cudaStream_t>(stream);
+    return ISING_OK;
+}
+
+int ising_thresholds(const ising_lattice* h, uint32_t out[3]) {
+    if (!h || !out) return ISING_EINVAL;
+    std::memcpy(out, h->thr, sizeof(h->thr));
+    return ISING_OK;
+}
+
+int ising_compute_thresholds(int dims, double beta, uint32_t out[3]) {
+    if (!out || (dims != 2 && dims != 3)) return ISING_EINVAL;
+    return build_thresholds(dims, beta, out);
+}
+
+int ising_get_info(const ising_lattice* h, ising_info_t* out) {
+    if (!h || !out) return ISING_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->dims = h->dims;
+    out->L = h->L;
+    out->layout = h->layout;
+    out->beta = h->beta;
+    out->seed = h->seed;
+    out->sweeps_done = h->t;
+    out->sites = (uint64_t)h->sites;
+    out->device_bytes = (uint64_t)(2 * h->col_bytes);
+    out->pending_records = h->n_rec;
+    return ISING_OK;
+}
+
+int ising_synchronize(ising_lattice* h) {
+    if (!h) return ISING_EINVAL;
+    ISING_CHECK(cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
+void ising_destroy(ising_lattice* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_device(h);
+    delete h;
+}
+
+}  // extern "C"

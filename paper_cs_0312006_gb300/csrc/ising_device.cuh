@@ -1,0 +1,111 @@
+// ising_device.cuh -- device building blocks shared by the sweep kernels:
+// the counter-based Philox4x32-10 generator, the per-sweep kernel arguments
+// and the exact integer reductions of E and M.
+//
+// Philox4x32-10 follows Salmon, Moraes, Dror and Shaw, "Parallel Random
+// Numbers: As Easy as 1, 2, 3" (SC'11): ten rounds, each multiplying counter
+// words 0 and 2 by two fixed odd 32-bit constants, exchanging the high halves
+// of the products into words 0 and 2 (xored with the neighbouring word and a
+// round key) and keeping the low halves in words 1 and 3; the two key words
+// advance by Weyl increments between rounds.  It replaces the paper's linear
+// congruential generator (Sec. 2.1) so that each site's draw is a pure
+// function of (seed, sweep, colour, site group), independent of layout and
+// launch shape.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ising {
+
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u;
+constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u;
+constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
+
+// Counter word 3 ("tag") separates the uses of the stream.
+constexpr uint32_t kTagSweep = 0u;
+constexpr uint32_t kTagInit = 1u;
+
+struct Philox4 {
+    uint32_t w0, w1, w2, w3;
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t a_hi = __umulhi(kPhiloxMulA, c0);
+        const uint32_t a_lo = kPhiloxMulA * c0;
+        const uint32_t b_hi = __umulhi(kPhiloxMulB, c2);
+        const uint32_t b_lo = kPhiloxMulB * c2;
+        c0 = b_hi ^ c1 ^ k0;
+        c1 = b_lo;
+        c2 = a_hi ^ c3 ^ k1;
+        c3 = a_lo;
+        k0 += kPhiloxWeylA;
+        k1 += kPhiloxWeylB;
+    }
+    return Philox4{c0, c1, c2, c3};
+}
+
+// Arguments of one colour pass.  The colour-c array is updated in place; it
+// reads only the colour-(1-c) array, so no site reads a value written by the
+// same pass (Sec. 2.2: a pass through all sites of one colour).
+struct PassArgs {
+    void* own;              // colour-c spins (int8 +-1, or packed words)
+    const void* other;      // colour-(1-c) spins
+    unsigned long long* obs; // (E, M) int64 slot of this sweep, or nullptr
+    int64_t rows;           // half rows per colour: L^(dims-1)
+    int L;                  // linear size
+    int W;                  // sites of one colour per row: L / 2
+    uint32_t thr0, thr1, thr2; // floor(exp(-2 beta k) 2^32), k = 2, 4, 6
+    uint32_t key0, key1;    // seed (low, high)
+    uint32_t t;             // sweep index
+    int c;                  // colour of this pass: 0 black, 1 white
+};
+
+// Number of thresholds a 32-bit draw u lies below.  The thresholds decrease
+// with k, so for k = 2(dims - d) (d = disagreeing neighbours, d < dims) the
+// Metropolis test u < thr[k] holds iff count(u) + d >= dims.
+template <int DIMS>
+__device__ __forceinline__ uint32_t below_count(uint32_t u, const PassArgs& a) {
+    uint32_t n = (u < a.thr0) + (u < a.thr1);
+    if (DIMS == 3) n += (u < a.thr2);
+    return n;
+}
+
+// Block-wide sum of two ints followed by one 64-bit atomic each into the
+// sweep's slot.  Integer addition is exact, so the order of the atomics does
+// not matter and the totals are bit-reproducible.
+__device__ __forceinline__ void block_reduce_add(int e, int m, unsigned long long* slot,
+                                                 bool with_e) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, off);
+        m += __shfl_xor_sync(0xffffffffu, m, off);
+    }
+    __shared__ long long red_e[32], red_m[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red_e[warp] = e;
+        red_m[warp] = m;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        long long se = lane < nw ? red_e[lane] : 0;
+        long long sm = lane < nw ? red_m[lane] : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            se += __shfl_xor_sync(0xffffffffu, se, off);
+            sm += __shfl_xor_sync(0xffffffffu, sm, off);
+        }
+        if (lane == 0) {
+            if (with_e && se != 0) atomicAdd(&slot[0], (unsigned long long)se);
+            if (sm != 0) atomicAdd(&slot[1], (unsigned long long)sm);
+        }
+    }
+}
+
+}  // namespace ising

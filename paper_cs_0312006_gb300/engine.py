@@ -1,0 +1,199 @@
+"""Thin Python binding of the C ABI in ``include/ising.h`` (argument marshalling
+only; every step of the simulation runs in the CUDA kernels of the shared
+library).
+
+There is no CPU path: if the compiled library is missing or cannot be loaded,
+``load_library()`` raises ``ImportError``.  PyTorch is used only to hand the
+engine a CUDA stream (``Lattice.set_stream``) and to receive device exports
+into a tensor (``Lattice.export_device``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+INT8, BITPACK, AUTO = 0, 1, 2
+HOT, COLD_UP, COLD_DOWN = 0, 1, 2
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, ERANGE = 0, -1, -2, -3, -4, -5, -6
+
+_lock = threading.Lock()
+_lib = None
+
+
+class IsingError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = load_library().ising_strerror(code).decode()
+        super().__init__(f"{what}: {msg} ({code})")
+
+
+class IsingInfo(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int), ("L", ctypes.c_int), ("layout", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("beta", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("sweeps_done", ctypes.c_uint64),
+                ("sites", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("pending_records", ctypes.c_int64)]
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load_library():
+    """Load the compiled engine (built by ``__graft_entry__.build()`` or
+    ``python -m paper_cs_0312006_gb300._build``).  Raises ImportError if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA engine library not built: {path} is missing; "
+                              "run paper_cs_0312006_gb300._build.build() first")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        sig = {
+            "ising_create": ([ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                              ctypes.c_uint64, ctypes.c_int], ctypes.c_int),
+            "ising_init": ([P, ctypes.c_int], ctypes.c_int),
+            "ising_sweep": ([P, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
+            "ising_observables": ([P, i64p, i64p, ctypes.c_int64, i64p], ctypes.c_int),
+            "ising_get_spins": ([P, P], ctypes.c_int),
+            "ising_set_spins": ([P, P, ctypes.c_uint64], ctypes.c_int),
+            "ising_export_device": ([P, P], ctypes.c_int),
+            "ising_set_stream": ([P, P], ctypes.c_int),
+            "ising_thresholds": ([P, u32p], ctypes.c_int),
+            "ising_compute_thresholds": ([ctypes.c_int, ctypes.c_double, u32p], ctypes.c_int),
+            "ising_get_info": ([P, ctypes.POINTER(IsingInfo)], ctypes.c_int),
+            "ising_synchronize": ([P], ctypes.c_int),
+            "ising_destroy": ([P], None),
+            "ising_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "ising_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != OK:
+        raise IsingError(rc, what)
+
+
+def compute_thresholds(dims: int, beta: float) -> np.ndarray:
+    """``ising_compute_thresholds``: the engine's host-side threshold table."""
+    out = np.zeros(3, dtype=np.uint32)
+    _check(load_library().ising_compute_thresholds(
+        dims, float(beta), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))),
+        f"ising_compute_thresholds(dims={dims}, beta={beta})")
+    return out
+
+
+class Lattice:
+    """One lattice on the current CUDA device (``ising_create``)."""
+
+    def __init__(self, dims: int, L: int, beta: float, seed: int, layout: int = INT8,
+                 start: int = HOT, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        _check(lib.ising_create(ctypes.byref(self._h), dims, L, float(beta),
+                                ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), layout),
+               f"ising_create(dims={dims}, L={L}, beta={beta})")
+        if stream is not None:
+            self.set_stream(stream)
+        if start != HOT:
+            self.init(start)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.ising_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls ------------------------------------------------------------
+    def init(self, start: int = HOT) -> None:
+        _check(self._lib.ising_init(self._h, start), "ising_init")
+
+    def sweep(self, n: int, measure_every: int = 1) -> None:
+        _check(self._lib.ising_sweep(self._h, int(n), int(measure_every)), "ising_sweep")
+
+    def observables(self):
+        """Pending (E, M) records as two int64 numpy arrays (clears them)."""
+        cnt = ctypes.c_int64(0)
+        _check(self._lib.ising_observables(self._h, None, None, 0, ctypes.byref(cnt)),
+               "ising_observables")
+        n = cnt.value
+        E = np.zeros(max(n, 1), dtype=np.int64)
+        M = np.zeros(max(n, 1), dtype=np.int64)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        _check(self._lib.ising_observables(self._h, E.ctypes.data_as(i64p),
+                                           M.ctypes.data_as(i64p), len(E), ctypes.byref(cnt)),
+               "ising_observables")
+        return E[:n].copy(), M[:n].copy()
+
+    def get_spins(self, out: np.ndarray | None = None) -> np.ndarray:
+        info = self.info()
+        if out is None:
+            out = np.empty(info.sites, dtype=np.int8)
+        assert out.dtype == np.int8 and out.size == info.sites and out.flags.c_contiguous
+        _check(self._lib.ising_get_spins(self._h, out.ctypes.data), "ising_get_spins")
+        return out
+
+    def set_spins(self, spins: np.ndarray, t: int = 0) -> None:
+        s = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1)
+        _check(self._lib.ising_set_spins(self._h, s.ctypes.data, int(t)), "ising_set_spins")
+
+    def export_device(self, out_ptr: int) -> None:
+        """Write canonical int8 spins to device memory at ``out_ptr``
+        (e.g. ``tensor.data_ptr()`` of an int8 CUDA tensor), on the handle's stream."""
+        _check(self._lib.ising_export_device(self._h, ctypes.c_void_p(out_ptr)),
+               "ising_export_device")
+
+    def set_stream(self, stream) -> None:
+        """Accepts a raw cudaStream_t (int) or an object with ``.cuda_stream``."""
+        raw = getattr(stream, "cuda_stream", stream)
+        _check(self._lib.ising_set_stream(self._h, ctypes.c_void_p(int(raw) if raw else 0)),
+               "ising_set_stream")
+
+    def thresholds(self) -> np.ndarray:
+        out = np.zeros(3, dtype=np.uint32)
+        _check(self._lib.ising_thresholds(self._h,
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))),
+               "ising_thresholds")
+        return out
+
+    def info(self) -> IsingInfo:
+        inf = IsingInfo()
+        _check(self._lib.ising_get_info(self._h, ctypes.byref(inf)), "ising_get_info")
+        return inf
+
+    def synchronize(self) -> None:
+        _check(self._lib.ising_synchronize(self._h), "ising_synchronize")
+
+    @property
+    def handle(self) -> int:
+        return int(self._h.value or 0)

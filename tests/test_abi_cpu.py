@@ -1,0 +1,81 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every function
+that include/ising.h declares, validates arguments on the host, and its
+host-side threshold builder agrees with the oracle and with mpmath."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_cs_0312006_gb300 import _build, engine
+    _build.build()
+    return engine.load_library()
+
+
+def _declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(ising_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_symbols_exported(lib):
+    names = _declared_functions()
+    assert "ising_create" in names and "ising_sweep" in names
+    assert "ising_observables" in names and "ising_destroy" in names
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_version_and_strerror(lib):
+    assert b"sm_103a" in lib.ising_version()
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert lib.ising_strerror(code)
+    assert lib.ising_strerror(-99) == b"unknown status"
+
+
+@pytest.mark.parametrize("dims,L,beta,layout", [
+    (1, 64, 0.4, 0), (4, 64, 0.4, 0), (2, 63, 0.4, 0), (2, 0, 0.4, 0), (2, 1, 0.4, 0),
+    (2, -4, 0.4, 0), (2, 64, 0.0, 0), (2, 64, -0.3, 0), (2, 64, float("nan"), 0),
+    (2, 64, 0.4, 7), (3, 1 << 12, 0.2, 0),
+])
+def test_create_rejects_invalid_arguments_on_host(lib, dims, L, beta, layout):
+    h = ctypes.c_void_p(1234)
+    rc = lib.ising_create(ctypes.byref(h), dims, L, beta, 1, layout)
+    assert rc == -1  # ISING_EINVAL, decided before any CUDA call
+    assert not h.value
+
+
+def test_null_handles(lib):
+    assert lib.ising_sweep(None, 1, 1) == -1
+    assert lib.ising_init(None, 0) == -1
+    assert lib.ising_synchronize(None) == -1
+    lib.ising_destroy(None)  # NULL-safe
+
+
+def test_engine_thresholds_match_oracle_and_mpmath(lib, orc):
+    from oracle import exact
+    from paper_cs_0312006_gb300.engine import compute_thresholds
+    rng = np.random.default_rng(3)
+    betas = [0.4406868, 0.2216544, 1e-30, 1e-9, 50.0, math.inf] + \
+        list(rng.uniform(0.01, 2.0, size=300))
+    for beta in betas:
+        for dims in (2, 3):
+            eng = compute_thresholds(dims, beta)
+            assert eng.tolist() == orc.thresholds(dims, beta).tolist()
+            if math.isfinite(beta) and beta < 10:
+                assert eng[:dims].tolist() == exact.exact_thresholds(dims, beta)
+    for bad in (0.0, -1.0, float("nan")):
+        with pytest.raises(Exception):
+            compute_thresholds(2, bad)
