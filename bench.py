@@ -3,11 +3,12 @@
 
 Workload (default): 2D square lattice L = 8192 (67,108,864 sites), 16 betas
 evenly spaced in [0.30, 0.60], cold start (all +1), seeds 20031109 + j, E and M
-recorded after every sweep, int8 layout.  One step = one sweep (black pass,
-white pass, fused E/M) of each of the 16 lattices in turn, so the 1 GiB of
-spin state that a step touches is far larger than the 129 MB L2 between
-timed iterations.  The default K = 2000 steps is the full run of the
-workload; the lattices are re-initialised (cold) inside the timed region.
+recorded after every sweep, run in the int8 layout and again in the
+bit-packed layout.  One step = one sweep (black pass, white pass, fused E/M)
+of each of the 16 lattices in turn, so the 1 GiB of int8 spin state that a
+step touches is far larger than the 129 MB L2 between timed iterations.  The
+default K = 2000 steps is the full run of the workload; the lattices are
+re-initialised (cold) inside the timed region; `value` covers both layouts.
 
 Metric: site updates per second (attempted single-spin Metropolis updates,
 one per site per sweep), whole job over all ranks.
@@ -52,11 +53,12 @@ def scan_betas():
     return [round(0.30 + 0.02 * j, 10) for j in range(N_BETA)]
 
 
-def workload_config(L: int, steps: int) -> dict:
+def workload_config(L: int, steps: int, lattices: int = N_BETA) -> dict:
     return {"workload": f"2D Ising beta scan: L={L} square lattice, 16 betas evenly spaced in "
-                        f"[0.30,0.60], cold start, {steps} sweeps, E/M every sweep",
-            "lattices_per_gpu": N_BETA,
-            "l2": "inputs larger than L2: a step touches 16 x L^2 bytes of int8 spins",
+                        f"[0.30,0.60], cold start, {steps} sweeps, E/M every sweep, int8 and "
+                        f"bit-packed layouts",
+            "lattices_per_gpu": lattices,
+            "l2": f"inputs larger than L2: a step touches {lattices} x L^2 bytes of int8 spins",
             "step": "one sweep (black pass, white pass, fused E/M) of each lattice"}
 
 
@@ -184,7 +186,7 @@ def run_reference(args, world, rank):
         "unit": "site updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-        "config": workload_config(args.L, args.steps),
+        "config": workload_config(args.L, args.steps, args.lattices),
         "cpu_baseline": {"value": value, "unit": "site updates/s", "cores": 1,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "site updates/s", "h2d_bytes_per_step": 0,
@@ -197,8 +199,14 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def philox_alu_peak_sites_per_s(sm_count: int, sm_mhz: float) -> float:
+    """Integer-pipe ceiling of a pass: one Philox4x32-10 call per 4 sites needs
+    18 non-uniform 32x32->64-bit multiplies, and an SM retires 32 of them per
+    clock (measured on this GPU with a Philox-only kernel)."""
+    return sm_count * (32.0 / 18.0) * 4.0 * sm_mhz * 1e6
+
+
 def run_gpu(args, world, rank, local):
-    import numpy as np
     import torch
 
     if not torch.cuda.is_available():
@@ -214,46 +222,58 @@ def run_gpu(args, world, rank, local):
 
     L = args.L
     n_sites = L * L
-    betas = scan_betas()
+    betas = scan_betas()[:args.lattices]
+    layouts = [("int8", engine.INT8), ("bitpack", engine.BITPACK)]
+    if args.layout != "both":
+        layouts = [x for x in layouts if x[0] == args.layout]
     stream = torch.cuda.current_stream()
-    lats = [engine.Lattice(2, L, b, BASE_SEED + 16 * rank + j, layout=engine.INT8,
-                           start=engine.COLD_UP, stream=stream)
-            for j, b in enumerate(betas)]
+    sets = {name: [engine.Lattice(2, L, b, BASE_SEED + 16 * rank + j, layout=lay,
+                                  start=engine.COLD_UP, stream=stream)
+                   for j, b in enumerate(betas)] for name, lay in layouts}
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    # ---------------- device-timed value ----------------
-    for _ in range(args.warmup):
+    # ---------------- warm-up ----------------
+    for lats in sets.values():
+        for _ in range(args.warmup):
+            for lat in lats:
+                lat.sweep(1, 1)
         for lat in lats:
-            lat.sweep(1, 1)
-    for lat in lats:
-        lat.observables()
+            lat.observables()
     torch.cuda.synchronize()
 
-    # events around every lattice's sweep call on timed steps, read after the run
-    pairs = []
+    # ---------------- device-timed value ----------------
     sampler = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
     sampler.start()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = {}
+    pairs = {name: [] for name in sets}
+    start = torch.cuda.Event(enable_timing=True)
     start.record(stream)
-    for lat in lats:
-        lat.init(engine.COLD_UP)
-    for k in range(args.steps):
-        time_this = k % args.time_every == 0
+    for name, lats in sets.items():
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
         for lat in lats:
-            if time_this:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                lat.sweep(1, 1)
-                e1.record(stream)
-                pairs.append((e0, e1))
-            else:
-                lat.sweep(1, 1)
+            lat.init(engine.COLD_UP)
+        for k in range(args.steps):
+            time_this = k % args.time_every == 0
+            for lat in lats:
+                if time_this:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    lat.sweep(1, 1)
+                    e1.record(stream)
+                    pairs[name].append((e0, e1))
+                else:
+                    lat.sweep(1, 1)
+        b1.record(stream)
+        marks[name] = (b0, b1)
+    stop = torch.cuda.Event(enable_timing=True)
     stop.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -264,38 +284,64 @@ def run_gpu(args, world, rank, local):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    updates = world * len(lats) * n_sites * args.steps
-    value = updates / (ms / 1e3)
-    # E/M sanity: every step recorded one (E, M) per lattice
-    n_rec = [len(lat.observables()[0]) for lat in lats]
-    assert all(n == args.steps for n in n_rec), n_rec
+    per_layout_updates = world * len(betas) * n_sites * args.steps
+    value = per_layout_updates * len(sets) / (ms / 1e3)
+    for lats in sets.values():  # every step recorded one (E, M) per lattice
+        n_rec = [len(lat.observables()[0]) for lat in lats]
+        assert all(n == args.steps for n in n_rec), n_rec
 
-    pass_ms = sum(a.elapsed_time(b) for a, b in pairs) / (2 * len(pairs))
-    bytes_per_pass = BYTES_PER_UPDATE_INT8 * n_sites // 2
-    peak, peak_kind = load_peaks()
-    achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
+    peak_hbm, peak_kind = load_peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    layout_stats = {}
+    rooflines = {}
+    for name in sets:
+        part_ms = marks[name][0].elapsed_time(marks[name][1])
+        pass_ms = sum(a.elapsed_time(b) for a, b in pairs[name]) / (2 * len(pairs[name]))
+        updates_per_pass = n_sites // 2
+        layout_stats[name] = {"value": world * len(betas) * n_sites * args.steps / (part_ms / 1e3),
+                              "ms": part_ms, "pass_ms": pass_ms,
+                              "pass_updates_per_s": updates_per_pass / (pass_ms / 1e3)}
+        if name == "int8":
+            bytes_per_pass = BYTES_PER_UPDATE_INT8 * updates_per_pass
+            achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
+            rooflines[name] = {"kernel": "pass_int8_strip<2,measure>", "bound": "hbm",
+                               "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                               "frac": achieved / peak_hbm, "traffic": None,
+                               "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
+                               "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+        else:
+            peak = philox_alu_peak_sites_per_s(sm_count, sm_mhz)
+            achieved = updates_per_pass / (pass_ms / 1e3)
+            rooflines[name] = {"kernel": "pass_packed<2,measure>", "bound": "alu",
+                               "achieved": achieved, "peak": peak, "unit": "site updates/s",
+                               "frac": achieved / peak, "traffic": None,
+                               "launch_ms": pass_ms,
+                               "peak_source": "derived: SMs x 32 wide multiplies/clk / 18 per "
+                                              "Philox call x 4 sites x median SM clock"}
 
     # ---------------- end to end through the C ABI, host buffers ----------------
     e2e = None
     if not args.no_e2e:
         host_init = torch.ones(n_sites, dtype=torch.int8).pin_memory().numpy()
-        host_out = [torch.empty(n_sites, dtype=torch.int8).pin_memory().numpy()
-                    for _ in range(len(lats))]
+        host_out = torch.empty(n_sites, dtype=torch.int8).pin_memory().numpy()
         e2e_steps = args.e2e_steps or args.steps
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for lat in lats:
-            lat.set_spins(host_init, 0)  # H2D of the initial configuration
         d2h = 0
-        for k in range(e2e_steps):
+        for lats in sets.values():
             for lat in lats:
-                lat.sweep(1, 1)
+                lat.set_spins(host_init, 0)  # H2D of the initial configuration
+            for k in range(e2e_steps):
+                for lat in lats:
+                    lat.sweep(1, 1)
+                for lat in lats:
+                    E, M = lat.observables()  # D2H of this step's (E, M)
+                    d2h += 16 * len(E)
             for lat in lats:
-                E, M = lat.observables()  # D2H of this step's (E, M)
-                d2h += 16 * len(E)
-        for j, lat in enumerate(lats):
-            lat.get_spins(host_out[j])  # D2H of the final configuration
+                lat.get_spins(host_out)  # D2H of the final configuration
+                d2h += n_sites
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         if world > 1:
@@ -303,16 +349,17 @@ def run_gpu(args, world, rank, local):
             t = torch.tensor([dt], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
-        h2d_total = len(lats) * n_sites
-        d2h_total = d2h + len(lats) * n_sites
-        e2e = {"value": world * len(lats) * n_sites * e2e_steps / dt, "unit": "site updates/s",
-               "h2d_bytes_per_step": h2d_total / e2e_steps,
-               "d2h_bytes_per_step": d2h_total / e2e_steps, "steps": e2e_steps,
-               "note": "ising_set_spins from pinned host memory, then per step one sweep of each "
-                       "lattice and ising_observables to host, then ising_get_spins"}
+        h2d_total = len(sets) * len(betas) * n_sites
+        e2e = {"value": world * len(sets) * len(betas) * n_sites * e2e_steps / dt,
+               "unit": "site updates/s", "h2d_bytes_per_step": h2d_total / e2e_steps,
+               "d2h_bytes_per_step": d2h / e2e_steps, "steps": e2e_steps,
+               "note": "per layout: ising_set_spins from pinned host memory, then per step one "
+                       "sweep of each lattice and ising_observables to host, then "
+                       "ising_get_spins"}
 
-    for lat in lats:
-        lat.close()
+    for lats in sets.values():
+        for lat in lats:
+            lat.close()
 
     if rank != 0:
         return 0
@@ -328,14 +375,11 @@ def run_gpu(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
         "data": "synthetic",
-        "config": workload_config(L, args.steps),
-        "layout": "int8 half-lattice per colour",
-        "roofline": {"kernel": "pass_int8_vec<2,measure>", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
-                     "peak_source": peak_kind},
-        "gpu_launches": len(lats) * (2 * args.steps + 1),
+        "config": workload_config(L, args.steps, len(betas)),
+        "layouts": layout_stats,
+        "roofline": rooflines.get("int8") or rooflines.get("bitpack"),
+        "roofline_bitpack": rooflines.get("bitpack"),
+        "gpu_launches": len(sets) * len(betas) * (2 * args.steps + 1),
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -354,6 +398,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--L", type=int, default=L_SCAN)
+    ap.add_argument("--layout", choices=["both", "int8", "bitpack"], default="both")
+    ap.add_argument("--lattices", type=int, default=N_BETA,
+                    help="how many of the 16 betas to run (profiling uses fewer)")
     ap.add_argument("--time-every", type=int, default=1,
                     help="time each lattice's sweep with events on every k-th step")
     ap.add_argument("--e2e-steps", type=int, default=0)

@@ -59,6 +59,7 @@ int device_props(const DeviceProps** out) {
         q.device = dev;
         ISING_CHECK(cudaDeviceGetAttribute(&q.sm_count, cudaDevAttrMultiProcessorCount, dev));
         ISING_CHECK(ising::int8_query_occupancy(q));
+        ISING_CHECK(ising::packed_query_occupancy(q));
         p = q;
     }
     *out = &p;
@@ -160,7 +161,11 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     a.key1 = (uint32_t)(h->seed >> 32);
     a.t = t;
     a.c = c;
-    ISING_CHECK(ising::int8_pass(a, h->dims, h->half_sites, slot != nullptr, *h->dp, h->stream));
+    if (h->layout == ISING_BITPACK)
+        ISING_CHECK(ising::packed_pass(a, h->dims, slot != nullptr, *h->dp, h->stream));
+    else
+        ISING_CHECK(ising::int8_pass(a, h->dims, h->half_sites, slot != nullptr, *h->dp,
+                                     h->stream));
     return ISING_OK;
 }
 
@@ -192,7 +197,11 @@ int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t see
         return ISING_EINVAL;
     const uint64_t sites = dims == 2 ? (uint64_t)L * L : (uint64_t)L * L * L;
     if ((uint64_t)L > (1u << 20) || sites > kMaxSites) return ISING_EINVAL;
-    if (layout == ISING_BITPACK) return ISING_EINVAL;  // bit-packed layout: not built yet
+    if (layout == ISING_BITPACK && L % 64 != 0) return ISING_EINVAL;
+    // ISING_AUTO: the bit-packed layout whenever its shape rule allows (results
+    // are identical in both layouts)
+    const int use_layout = layout == ISING_AUTO ? (L % 64 == 0 ? ISING_BITPACK : ISING_INT8)
+                                                : layout;
     uint32_t thr[3];
     int rc = build_thresholds(dims, beta, thr);
     if (rc != ISING_OK) return rc;
@@ -204,7 +213,7 @@ int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t see
     if (!h) return ISING_ENOMEM;
     h->dims = dims;
     h->L = L;
-    h->layout = ISING_INT8;
+    h->layout = use_layout;
     h->beta = beta;
     h->seed = seed;
     std::memcpy(h->thr, thr, sizeof(thr));
@@ -213,7 +222,10 @@ int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t see
     h->W = L / 2;
     h->rows = dims == 2 ? L : (int64_t)L * L;
     h->dp = dp;
-    h->col_bytes = ((size_t)h->half_sites + 15) & ~(size_t)15;
+    if (use_layout == ISING_BITPACK)
+        h->col_bytes = (size_t)h->rows * (size_t)(L / 64) * sizeof(uint32_t);
+    else
+        h->col_bytes = ((size_t)h->half_sites + 15) & ~(size_t)15;
     for (int c = 0; c < 2; ++c) {
         cudaError_t e = cudaMalloc(&h->col[c], h->col_bytes);
         if (e != cudaSuccess) {
@@ -236,10 +248,15 @@ int ising_init(ising_lattice* h, int start) {
     if (!h) return ISING_EINVAL;
     if (start != ISING_HOT && start != ISING_COLD_UP && start != ISING_COLD_DOWN)
         return ISING_EINVAL;
-    ISING_CHECK(ising::int8_init(static_cast<int8_t*>(h->col[0]), static_cast<int8_t*>(h->col[1]),
-                                 h->L, h->dims, h->sites, start,
-                                 (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32),
-                                 *h->dp, h->stream));
+    const uint32_t k0 = (uint32_t)(h->seed & 0xFFFFFFFFu), k1 = (uint32_t)(h->seed >> 32);
+    if (h->layout == ISING_BITPACK)
+        ISING_CHECK(ising::packed_init(static_cast<uint32_t*>(h->col[0]),
+                                       static_cast<uint32_t*>(h->col[1]), h->L, h->dims, h->rows,
+                                       start, k0, k1, *h->dp, h->stream));
+    else
+        ISING_CHECK(ising::int8_init(static_cast<int8_t*>(h->col[0]),
+                                     static_cast<int8_t*>(h->col[1]), h->L, h->dims, h->sites,
+                                     start, k0, k1, *h->dp, h->stream));
     h->t = 0;
     return clear_records(h);
 }
@@ -287,9 +304,14 @@ int ising_observables(ising_lattice* h, int64_t* E, int64_t* M, int64_t cap, int
 
 int ising_export_device(ising_lattice* h, int8_t* dev_out) {
     if (!h || !dev_out) return ISING_EINVAL;
-    ISING_CHECK(ising::int8_export(static_cast<const int8_t*>(h->col[0]),
-                                   static_cast<const int8_t*>(h->col[1]), dev_out, h->L,
-                                   h->dims, h->sites, *h->dp, h->stream));
+    if (h->layout == ISING_BITPACK)
+        ISING_CHECK(ising::packed_export(static_cast<const uint32_t*>(h->col[0]),
+                                         static_cast<const uint32_t*>(h->col[1]), dev_out, h->L,
+                                         h->dims, h->sites, *h->dp, h->stream));
+    else
+        ISING_CHECK(ising::int8_export(static_cast<const int8_t*>(h->col[0]),
+                                       static_cast<const int8_t*>(h->col[1]), dev_out, h->L,
+                                       h->dims, h->sites, *h->dp, h->stream));
     return ISING_OK;
 }
 
@@ -318,9 +340,16 @@ int ising_set_spins(ising_lattice* h, const int8_t* host_in, uint64_t t) {
     ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
     cudaError_t e = cudaMemcpyAsync(tmp, host_in, (size_t)h->sites, cudaMemcpyHostToDevice,
                                     h->stream);
-    if (e == cudaSuccess)
-        e = ising::int8_import(static_cast<int8_t*>(h->col[0]), static_cast<int8_t*>(h->col[1]),
-                               tmp, h->L, h->dims, h->sites, *h->dp, h->stream);
+    if (e == cudaSuccess) {
+        if (h->layout == ISING_BITPACK)
+            e = ising::packed_import(static_cast<uint32_t*>(h->col[0]),
+                                     static_cast<uint32_t*>(h->col[1]), tmp, h->L, h->dims,
+                                     h->rows, *h->dp, h->stream);
+        else
+            e = ising::int8_import(static_cast<int8_t*>(h->col[0]),
+                                   static_cast<int8_t*>(h->col[1]), tmp, h->L, h->dims, h->sites,
+                                   *h->dp, h->stream);
+    }
     cudaFreeAsync(tmp, h->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     h->t = t;

@@ -28,4 +28,15 @@ cudaError_t int8_export(const int8_t* col0, const int8_t* col1, int8_t* out, int
 cudaError_t int8_import(int8_t* col0, int8_t* col1, const int8_t* in, int L, int dims,
                         int64_t sites, const DeviceProps& dp, cudaStream_t st);
 
+// bit-packed layout (sweep_bitpack.cu)
+cudaError_t packed_query_occupancy(DeviceProps& dp);
+cudaError_t packed_pass(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
+                        cudaStream_t st);
+cudaError_t packed_init(uint32_t* col0, uint32_t* col1, int L, int dims, int64_t rows, int start,
+                        uint32_t key0, uint32_t key1, const DeviceProps& dp, cudaStream_t st);
+cudaError_t packed_export(const uint32_t* col0, const uint32_t* col1, int8_t* out, int L,
+                          int dims, int64_t sites, const DeviceProps& dp, cudaStream_t st);
+cudaError_t packed_import(uint32_t* col0, uint32_t* col1, const int8_t* in, int L, int dims,
+                          int64_t rows, const DeviceProps& dp, cudaStream_t st);
+
 }  // namespace ising

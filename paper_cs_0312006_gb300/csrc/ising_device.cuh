@@ -35,14 +35,13 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
                                                  uint32_t c3, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t a_hi = __umulhi(kPhiloxMulA, c0);
-        const uint32_t a_lo = kPhiloxMulA * c0;
-        const uint32_t b_hi = __umulhi(kPhiloxMulB, c2);
-        const uint32_t b_lo = kPhiloxMulB * c2;
-        c0 = b_hi ^ c1 ^ k0;
-        c1 = b_lo;
-        c2 = a_hi ^ c3 ^ k1;
-        c3 = a_lo;
+        // one 32x32 -> 64-bit product per multiplier: high half mixes, low half carries over
+        const uint64_t pa = (uint64_t)c0 * kPhiloxMulA;
+        const uint64_t pb = (uint64_t)c2 * kPhiloxMulB;
+        c0 = (uint32_t)(pb >> 32) ^ c1 ^ k0;
+        c1 = (uint32_t)pb;
+        c2 = (uint32_t)(pa >> 32) ^ c3 ^ k1;
+        c3 = (uint32_t)pa;
         k0 += kPhiloxWeylA;
         k1 += kPhiloxWeylB;
     }
@@ -63,6 +62,8 @@ struct PassArgs {
     uint32_t key0, key1;    // seed (low, high)
     uint32_t t;             // sweep index
     int c;                  // colour of this pass: 0 black, 1 white
+    int nv;                 // 16-byte vectors per half row (W / 16), vector kernels only
+    int strips;             // row strips per column, vector kernels only
 };
 
 // Number of thresholds a 32-bit draw u lies below.  The thresholds decrease

@@ -34,118 +34,208 @@ constexpr uint32_t kBit1 = 0x02020202u;
 constexpr uint32_t kBit7 = 0x80808080u;
 constexpr uint32_t kOnes = 0x01010101u;
 
-// Update four sites held in one 32-bit word (one Philox group).  n0..n5 are
-// the words of the other colour that line up with the four sites' neighbours.
-// Returns the new word; accumulates M (and E in the white pass).
-template <int DIMS, bool MEASURE>
-__device__ __forceinline__ uint32_t update_word(uint32_t s, uint32_t n0, uint32_t n1,
-                                                uint32_t n2, uint32_t n3, uint32_t n4,
-                                                uint32_t n5, uint32_t group,
-                                                const PassArgs& a, int& e_acc, int& m_acc) {
+// Byte mask 0xFE of each site whose flip is decided without a draw.  Byte j of
+// D is 2*d_j (d_j = disagreeing neighbours); bit 7 of D + bias is set iff
+// d_j >= dims, i.e. dE <= 0.  0x80 -> 0xFE by F | (F - (F >> 6)), borrow-free.
+template <int DIMS>
+__device__ __forceinline__ uint32_t downhill_mask(uint32_t D) {
+    constexpr uint32_t bias = (0x80u - 2u * DIMS) * kOnes;
+    const uint32_t F = (D + bias) & kBit7;
+    return F | (F - (F >> 6));
+}
+
+// Metropolis test of site j of a word with d_j < dims: u_j < thr[k], k = 2(dims - d_j).
+// The threshold is selected from d_j on the integer ALU; the result ORs 0xFE into
+// byte j of the xor mask.
+template <int DIMS>
+__device__ __forceinline__ uint32_t uphill_accept(uint32_t D, uint32_t u, int j,
+                                                  const PassArgs& a) {
+    const uint32_t dj = D & (0x0Eu << (8 * j));  // 2*d_j in place
+    uint32_t t;
+    if (DIMS == 2) {
+        t = dj == 0u ? a.thr1 : a.thr0;  // d = 0: k = 4; d = 1: k = 2
+    } else {
+        t = dj == 0u ? a.thr2 : (dj == (0x02u << (8 * j)) ? a.thr1 : a.thr0);
+    }
+    return u < t ? (0xFEu << (8 * j)) : 0u;
+}
+
+template <int DIMS>
+__device__ __forceinline__ uint32_t disagreements(uint32_t s, uint32_t n0, uint32_t n1,
+                                                  uint32_t n2, uint32_t n3, uint32_t n4,
+                                                  uint32_t n5) {
     uint32_t D = ((s ^ n0) & kBit1) + ((s ^ n1) & kBit1) + ((s ^ n2) & kBit1) +
                  ((s ^ n3) & kBit1);
     if (DIMS == 3) D += ((s ^ n4) & kBit1) + ((s ^ n5) & kBit1);
-    // byte j of D is 2*d_j; bias so that bit 7 is set iff 2*(count + d) >= 2*dims
-    constexpr uint32_t bias = (0x80u - 2u * DIMS) * kOnes;
-    uint32_t F = (D + bias) & kBit7;  // sites that flip without a draw
-    if (F != kBit7) {
-        const Philox4 u = philox4x32_10(group, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
-        const uint32_t cnt = below_count<DIMS>(u.w0, a) | (below_count<DIMS>(u.w1, a) << 8) |
-                             (below_count<DIMS>(u.w2, a) << 16) |
-                             (below_count<DIMS>(u.w3, a) << 24);
-        F = (D + 2u * cnt + bias) & kBit7;
+    return D;
+}
+
+// Update the 16 sites of one 16-byte vector (four Philox groups g0..g0+3).
+// The four Philox calls are independent and computed together when any of
+// the 16 sites needs its draw.  Accumulates the number of -1 spins (m_neg)
+// and, in the white pass, sum_j 2*d_new_j (e_acc).
+template <int DIMS, bool MEASURE>
+__device__ __forceinline__ uint4 update_vec(const uint4& s, const uint4& x, const uint4& xs,
+                                            const uint4& ym, const uint4& yp, const uint4& zm,
+                                            const uint4& zp, uint32_t g0, const PassArgs& a,
+                                            int& e_acc, int& m_neg) {
+    const uint32_t sv[4] = {s.x, s.y, s.z, s.w};
+    uint32_t D[4], X[4];
+    D[0] = disagreements<DIMS>(s.x, x.x, xs.x, ym.x, yp.x, zm.x, zp.x);
+    D[1] = disagreements<DIMS>(s.y, x.y, xs.y, ym.y, yp.y, zm.y, zp.y);
+    D[2] = disagreements<DIMS>(s.z, x.z, xs.z, ym.z, yp.z, zm.z, zp.z);
+    D[3] = disagreements<DIMS>(s.w, x.w, xs.w, ym.w, yp.w, zm.w, zp.w);
+    bool need = false;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        X[w] = downhill_mask<DIMS>(D[w]);
+        need |= X[w] != 0xFEFEFEFEu;
     }
-    const uint32_t snew = s ^ ((F >> 7) * 0xFEu);  // 0x01 <-> 0xFF where flipped
-    if (MEASURE) {
-        m_acc += 4 - 2 * __popc(snew & kBit7);
-        if (a.c == 1) {
-            // white pass: E = -sum_white s_i h_i = sum (2 d_new - 2 dims)
-            const uint32_t fmask = (F >> 7) * 0xFFu;
-            constexpr uint32_t q2 = 4u * DIMS * kOnes;  // 2 * (2 dims) per byte
-            const uint32_t Dn = (D & ~fmask) | ((q2 - D) & fmask);
-            e_acc += (int)((Dn * kOnes) >> 24) - 8 * DIMS;
+    if (need) {
+        Philox4 u[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            u[w] = philox4x32_10(g0 + (uint32_t)w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            X[w] |= uphill_accept<DIMS>(D[w], u[w].w0, 0, a) |
+                    uphill_accept<DIMS>(D[w], u[w].w1, 1, a) |
+                    uphill_accept<DIMS>(D[w], u[w].w2, 2, a) |
+                    uphill_accept<DIMS>(D[w], u[w].w3, 3, a);
         }
     }
-    return snew;
+    uint32_t out[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        out[w] = sv[w] ^ X[w];  // 0x01 <-> 0xFF where flipped
+        if (MEASURE) {
+            m_neg += __popc(out[w] & kBit7);
+            if (a.c == 1) {
+                // 2*d_new = 2*(2 dims) - 2*d where flipped; X covers bits 1..7 there
+                constexpr uint32_t q2 = 4u * DIMS * kOnes;
+                const uint32_t Dn = (D[w] & ~X[w]) | ((q2 - D[w]) & X[w]);
+                e_acc = __dp4a((int)Dn, (int)kOnes, e_acc);
+            }
+        }
+    }
+    return make_uint4(out[0], out[1], out[2], out[3]);
 }
 
 __device__ __forceinline__ int wrap_prev(int v, int n) { return v == 0 ? n - 1 : v - 1; }
 __device__ __forceinline__ int wrap_next(int v, int n) { return v == n - 1 ? 0 : v + 1; }
 
-// Vector kernel: W % 16 == 0.  One item = 16 sites (one uint4) of one half
-// row; consecutive lanes take consecutive items, so the byte that crosses an
-// item boundary in the x-shift comes from the neighbouring lane.
+// Strip kernel: W % 16 == 0.  Each thread owns one 16-byte column v of the
+// colour arrays and walks a strip of consecutive half rows, keeping the other
+// colour's rows y-1, y, y+1 of its column in registers (a sliding window) and
+// prefetching the next row's data before computing the current one.  Lanes
+// hold consecutive columns, so the byte that crosses a column boundary in the
+// x-shift comes from the neighbouring lane.  Strips are as balanced as the
+// row count allows; a strip that reaches the end of a plane reloads its
+// window for the next plane.
 template <int DIMS, bool MEASURE>
-__global__ void __launch_bounds__(256) pass_int8_vec(PassArgs a) {
-    const int nv = a.W >> 4;
-    const int64_t items = (int64_t)nv * a.rows;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+__global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 2) pass_int8_strip(PassArgs a) {
+    const int nv = a.nv, S = a.strips, L = a.L;
+    const int rows = (int)a.rows;
     const int lane = threadIdx.x & 31;
-    const int L = a.L;
-    int8_t* own = static_cast<int8_t*>(a.own);
-    const int8_t* other = static_cast<const int8_t*>(a.other);
-    int e_acc = 0, m_acc = 0;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = tid < S * nv;
+    const int sidx = active ? tid / nv : 0;
+    const int v = active ? tid - sidx * nv : 0;
+    const int r_begin = (int)(((int64_t)sidx * rows) / S);
+    const int len = active ? (int)(((int64_t)(sidx + 1) * rows) / S) - r_begin : 0;
+    const int max_len = (rows + S - 1) / S;
+    const uint4* __restrict__ O = reinterpret_cast<const uint4*>(a.other) + v;
+    uint4* __restrict__ Sv = reinterpret_cast<uint4*>(a.own) + v;
+    const uint32_t* __restrict__ Ow = reinterpret_cast<const uint32_t*>(a.other);
+    const uint32_t vm_word = 4u * (uint32_t)wrap_prev(v, nv) + 3u;  // last word of column v-1
+    const uint32_t vp_word = 4u * (uint32_t)wrap_next(v, nv);       // first word of column v+1
 
-    // items and stride are multiples of 32, so whole warps enter each trip
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride) {
-        const int64_t r = g / nv;
-        const int v = (int)(g - r * nv);
-        int y, z;
-        if (DIMS == 2) {
-            y = (int)r;
-            z = 0;
-        } else {
-            z = (int)(r / L);
-            y = (int)(r - (int64_t)z * L);
-        }
-        const int p = (a.c + y + z) & 1;
-        const int64_t plane = (int64_t)z * L;
-        const int64_t r_ym = plane + wrap_prev(y, L), r_yp = plane + wrap_next(y, L);
-
-        const uint4* orow = reinterpret_cast<const uint4*>(other + r * a.W);
-        const uint4 o = __ldg(orow + v);
-        const uint4 oym = __ldg(reinterpret_cast<const uint4*>(other + r_ym * a.W) + v);
-        const uint4 oyp = __ldg(reinterpret_cast<const uint4*>(other + r_yp * a.W) + v);
-        uint4 ozm = make_uint4(0, 0, 0, 0), ozp = make_uint4(0, 0, 0, 0);
-        if (DIMS == 3) {
-            const int64_t r_zm = (int64_t)wrap_prev(z, L) * L + y;
-            const int64_t r_zp = (int64_t)wrap_next(z, L) * L + y;
-            ozm = __ldg(reinterpret_cast<const uint4*>(other + r_zm * a.W) + v);
-            ozp = __ldg(reinterpret_cast<const uint4*>(other + r_zp * a.W) + v);
-        }
-        uint4* srow = reinterpret_cast<uint4*>(own + r * a.W);
-        uint4 s = srow[v];
-
-        // x-neighbour bytes shifted by one site
-        uint32_t prev_w = __shfl_up_sync(0xffffffffu, o.w, 1);
-        uint32_t next_x = __shfl_down_sync(0xffffffffu, o.x, 1);
-        uint4 sh;
-        if (p == 0) {
-            if (lane == 0 || v == 0) prev_w = __ldg(orow + wrap_prev(v, nv)).w;
-            sh.x = __funnelshift_l(prev_w, o.x, 8);
-            sh.y = __funnelshift_l(o.x, o.y, 8);
-            sh.z = __funnelshift_l(o.y, o.z, 8);
-            sh.w = __funnelshift_l(o.z, o.w, 8);
-        } else {
-            if (lane == 31 || v == nv - 1) next_x = __ldg(orow + wrap_next(v, nv)).x;
-            sh.x = __funnelshift_r(o.x, o.y, 8);
-            sh.y = __funnelshift_r(o.y, o.z, 8);
-            sh.z = __funnelshift_r(o.z, o.w, 8);
-            sh.w = __funnelshift_r(o.w, next_x, 8);
-        }
-
-        const uint32_t group0 = (uint32_t)((r * a.W + 16 * v) >> 2);
-        s.x = update_word<DIMS, MEASURE>(s.x, o.x, sh.x, oym.x, oyp.x, ozm.x, ozp.x, group0,
-                                         a, e_acc, m_acc);
-        s.y = update_word<DIMS, MEASURE>(s.y, o.y, sh.y, oym.y, oyp.y, ozm.y, ozp.y, group0 + 1,
-                                         a, e_acc, m_acc);
-        s.z = update_word<DIMS, MEASURE>(s.z, o.z, sh.z, oym.z, oyp.z, ozm.z, ozp.z, group0 + 2,
-                                         a, e_acc, m_acc);
-        s.w = update_word<DIMS, MEASURE>(s.w, o.w, sh.w, oym.w, oyp.w, ozm.w, ozp.w, group0 + 3,
-                                         a, e_acc, m_acc);
-        srow[v] = s;
+    int z = DIMS == 3 ? r_begin / L : 0;
+    int y = r_begin - z * L;
+    int plane = z * L, plane_m = 0, plane_p = 0;
+    if (DIMS == 3) {
+        plane_m = wrap_prev(z, L) * L;
+        plane_p = wrap_next(z, L) * L;
     }
-    if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    uint4 om = zero, oc = zero, op = zero, sc = zero, zm = zero, zp = zero;
+    bool reload = true;
+    int e_acc = 0, m_neg = 0, n_rows = 0;
+
+    for (int i = 0; i < max_len; ++i) {
+        const bool valid = i < len;
+        const int r = r_begin + i;
+        if (valid && reload) {
+            om = __ldg(O + (uint32_t)(plane + wrap_prev(y, L)) * nv);
+            oc = __ldg(O + (uint32_t)r * nv);
+            op = __ldg(O + (uint32_t)(plane + wrap_next(y, L)) * nv);
+            sc = Sv[(uint32_t)r * nv];
+            if (DIMS == 3) {
+                zm = __ldg(O + (uint32_t)(plane_m + y) * nv);
+                zp = __ldg(O + (uint32_t)(plane_p + y) * nv);
+            }
+        }
+        // prefetch row r + 1 while it stays in this plane
+        const bool pf = (i + 1 < len) && (y + 1 < L);
+        uint4 op_n = zero, sc_n = zero, zm_n = zero, zp_n = zero;
+        if (pf) {
+            op_n = __ldg(O + (uint32_t)(plane + (y + 2 < L ? y + 2 : y + 2 - L)) * nv);
+            sc_n = Sv[(uint32_t)(r + 1) * nv];
+            if (DIMS == 3) {
+                zm_n = __ldg(O + (uint32_t)(plane_m + y + 1) * nv);
+                zp_n = __ldg(O + (uint32_t)(plane_p + y + 1) * nv);
+            }
+        }
+        // x-neighbour bytes shifted by one site (all lanes take part in the shuffles)
+        uint32_t prev_w = __shfl_up_sync(0xffffffffu, oc.w, 1);
+        uint32_t next_x = __shfl_down_sync(0xffffffffu, oc.x, 1);
+        if (valid) {
+            const int p = (a.c + y + z) & 1;
+            uint4 sh;
+            if (p == 0) {
+                if (lane == 0 || v == 0) prev_w = __ldg(Ow + (uint32_t)r * nv * 4u + vm_word);
+                sh.x = __funnelshift_l(prev_w, oc.x, 8);
+                sh.y = __funnelshift_l(oc.x, oc.y, 8);
+                sh.z = __funnelshift_l(oc.y, oc.z, 8);
+                sh.w = __funnelshift_l(oc.z, oc.w, 8);
+            } else {
+                if (lane == 31 || v == nv - 1) next_x = __ldg(Ow + (uint32_t)r * nv * 4u + vp_word);
+                sh.x = __funnelshift_r(oc.x, oc.y, 8);
+                sh.y = __funnelshift_r(oc.y, oc.z, 8);
+                sh.z = __funnelshift_r(oc.z, oc.w, 8);
+                sh.w = __funnelshift_r(oc.w, next_x, 8);
+            }
+            const uint32_t g0 = ((uint32_t)r * nv + (uint32_t)v) * 4u;  // Philox group of word 0
+            const uint4 s = update_vec<DIMS, MEASURE>(sc, oc, sh, om, op, zm, zp, g0, a, e_acc,
+                                                      m_neg);
+            Sv[(uint32_t)r * nv] = s;
+            ++n_rows;
+        }
+        // slide the window
+        if (pf) {
+            om = oc;
+            oc = op;
+            op = op_n;
+            sc = sc_n;
+            zm = zm_n;
+            zp = zp_n;
+        }
+        reload = !pf;
+        if (++y == L) {
+            y = 0;
+            ++z;
+            plane += L;
+            if (DIMS == 3) {
+                plane_m = wrap_prev(z, L) * L;
+                plane_p = wrap_next(z, L) * L;
+            }
+        }
+    }
+    if (MEASURE) {
+        e_acc -= n_rows * 16 * 2 * DIMS;          // E_white = sum_j (2 d_new_j - 2 dims)
+        const int m_acc = n_rows * 16 - 2 * m_neg;  // sum of the new spins
+        block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
+    }
 }
 
 // General kernel: any even L.  One item = one 32-bit word (four consecutive
@@ -266,23 +356,28 @@ __global__ void import_int8(int8_t* col0, int8_t* col1, const int8_t* in, int L,
 }
 
 template <int DIMS, bool MEASURE>
-cudaError_t launch_pass_t(const PassArgs& a, int64_t half_sites, bool vec, const DeviceProps& dp,
+cudaError_t launch_pass_t(const PassArgs& a0, int64_t half_sites, bool vec, const DeviceProps& dp,
                           cudaStream_t st) {
     const int threads = 256;
     if (vec) {
-        const int64_t items = (int64_t)(a.W >> 4) * a.rows;
-        int64_t blocks = (items + threads - 1) / threads;
-        const int64_t cap = (int64_t)dp.sm_count * dp.blocks_per_sm_vec[DIMS - 2][MEASURE];
-        if (blocks > cap) blocks = cap;
-        if (blocks < 1) blocks = 1;
-        pass_int8_vec<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a);
+        PassArgs a = a0;
+        a.nv = a.W >> 4;
+        // one wave of resident threads, each walking a strip of rows of one column
+        const int64_t resident = (int64_t)dp.sm_count * dp.blocks_per_sm_vec[DIMS - 2][MEASURE] *
+                                 threads;
+        int64_t strips = resident / a.nv;
+        if (strips > a.rows) strips = a.rows;
+        if (strips < 1) strips = 1;
+        a.strips = (int)strips;
+        const int64_t blocks = (strips * a.nv + threads - 1) / threads;
+        pass_int8_strip<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a);
     } else {
         const int64_t words = (half_sites + 3) >> 2;
         int64_t blocks = (words + threads - 1) / threads;
         const int64_t cap = (int64_t)dp.sm_count * 8;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        pass_int8_any<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a, half_sites);
+        pass_int8_any<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a0, half_sites);
     }
     return cudaGetLastError();
 }
@@ -293,7 +388,7 @@ cudaError_t int8_query_occupancy(DeviceProps& dp) {
     cudaError_t e;
 #define ISING_OCC(D, M)                                                                      \
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_vec[D - 2][M],        \
-                                                      pass_int8_vec<D, M>, 256, 0);           \
+                                                      pass_int8_strip<D, M>, 256, 0);           \
     if (e != cudaSuccess) return e;
     ISING_OCC(2, false)
     ISING_OCC(2, true)

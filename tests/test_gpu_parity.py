@@ -22,6 +22,11 @@ import _oracle_jobs as jobs
 pytestmark = pytest.mark.gpu
 
 HOT, COLD_UP, COLD_DOWN = 0, 1, 2
+INT8, BITPACK, AUTO = 0, 1, 2
+
+
+def layouts_for(L):
+    return [INT8, BITPACK] if L % 64 == 0 else [INT8]
 
 
 @pytest.fixture(scope="module")
@@ -66,41 +71,62 @@ def assert_same(gpu, orc_res, what):
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("dims,L", [(2, 2), (2, 4), (2, 6), (2, 64), (2, 100), (3, 2), (3, 4),
-                                    (3, 6), (3, 32), (3, 34)])
+@pytest.mark.parametrize("dims,L", [(2, 2), (2, 4), (2, 6), (2, 64), (2, 100), (2, 192), (3, 2),
+                                    (3, 4), (3, 6), (3, 32), (3, 34), (3, 64)])
 @pytest.mark.parametrize("start", [HOT, COLD_UP, COLD_DOWN])
 def test_init_matches_oracle(eng, dims, L, start):
-    lat = eng.Lattice(dims, L, 0.3, 20031109, start=start)
-    got = lat.get_spins()
-    lat.close()
-    assert np.array_equal(got, oracle.init(dims, L, 20031109, start))
+    want = oracle.init(dims, L, 20031109, start)
+    for layout in layouts_for(L):
+        lat = eng.Lattice(dims, L, 0.3, 20031109, layout=layout, start=start)
+        got = lat.get_spins()
+        lat.close()
+        assert np.array_equal(got, want), f"layout {layout}"
 
 
-SMALL_2D = [2, 4, 6, 10, 30, 32, 34, 62, 64, 96, 160, 258]
-SMALL_3D = [2, 4, 6, 10, 32, 34, 64]
+SMALL_2D = [2, 4, 6, 10, 30, 32, 34, 62, 64, 96, 128, 160, 192, 258]
+SMALL_3D = [2, 4, 6, 10, 32, 34, 64, 128]
 
 
 @pytest.mark.parametrize("L", SMALL_2D)
 @pytest.mark.parametrize("beta", [0.25, 0.4406868, 0.7])
 def test_sweeps_match_oracle_2d(eng, L, beta):
     n = 25
-    g = gpu_run(eng, 2, L, beta, 77 + L, HOT, n, 1)
     o = oracle.run(2, L, beta, 77 + L, n, measure_every=1, start=HOT)
-    assert_same(g, o, f"2D L={L} beta={beta}")
+    for layout in layouts_for(L):
+        g = gpu_run(eng, 2, L, beta, 77 + L, HOT, n, 1, layout=layout)
+        assert_same(g, o, f"2D L={L} beta={beta} layout={layout}")
 
 
 @pytest.mark.parametrize("L", SMALL_3D)
 @pytest.mark.parametrize("beta", [0.15, 0.2216544, 0.4])
 def test_sweeps_match_oracle_3d(eng, L, beta):
-    n = 12
-    g = gpu_run(eng, 3, L, beta, 99 + L, HOT, n, 1)
+    n = 12 if L < 128 else 4
     o = oracle.run(3, L, beta, 99 + L, n, measure_every=1, start=HOT)
-    assert_same(g, o, f"3D L={L} beta={beta}")
+    for layout in layouts_for(L):
+        g = gpu_run(eng, 3, L, beta, 99 + L, HOT, n, 1, layout=layout)
+        assert_same(g, o, f"3D L={L} beta={beta} layout={layout}")
 
 
-def test_critical_2d_L64_1000_sweeps(eng):
+def test_auto_layout_choice_and_identity(eng):
+    for L, want in ((128, BITPACK), (96, INT8)):
+        lat = eng.Lattice(2, L, 0.44, 3, layout=AUTO)
+        assert lat.info().layout == want
+        lat.close()
+    runs = [gpu_run(eng, 2, 128, 0.44, 3, HOT, 15, 1, layout=lay) for lay in (INT8, BITPACK, AUTO)]
+    for r in runs[1:]:
+        assert_same(r, runs[0], "layout identity")
+
+
+def test_bitpack_rejects_bad_shape(eng):
+    with pytest.raises(eng.IsingError) as ei:
+        eng.Lattice(2, 96, 0.4, 1, layout=BITPACK)
+    assert ei.value.code == eng.EINVAL
+
+
+@pytest.mark.parametrize("layout", [INT8, BITPACK])
+def test_critical_2d_L64_1000_sweeps(eng, layout):
     """2D L=64 at beta_c, hot start, seed 20031109: 1000 sweeps, E/M each sweep."""
-    g = gpu_run(eng, 2, 64, 0.4406868, 20031109, HOT, 1000, 1)
+    g = gpu_run(eng, 2, 64, 0.4406868, 20031109, HOT, 1000, 1, layout=layout)
     o = oracle.run(2, 64, 0.4406868, 20031109, 1000, measure_every=1, start=HOT)
     assert_same(g, o, "2D L=64 beta_c")
 
@@ -112,15 +138,17 @@ def test_measure_interval_and_chunked_calls(eng):
     assert_same(g, o, "every=3 over three calls")
 
 
-def test_checkpoint_and_resume(eng):
+@pytest.mark.parametrize("layout", [INT8, BITPACK])
+def test_checkpoint_and_resume(eng, layout):
     dims, L, beta, seed = 2, 128, 0.44, 31
     full = gpu_run(eng, dims, L, beta, seed, HOT, 30, 1)
-    lat = eng.Lattice(dims, L, beta, seed)
+    lat = eng.Lattice(dims, L, beta, seed, layout=layout)
     lat.sweep(17, 1)
     E1, M1 = lat.observables()
     mid = lat.get_spins()
     lat.close()
-    lat2 = eng.Lattice(dims, L, beta, seed)
+    # resume in the other layout: the state is layout-free
+    lat2 = eng.Lattice(dims, L, beta, seed, layout=BITPACK if layout == INT8 else INT8)
     lat2.set_spins(mid, 17)
     assert lat2.info().sweeps_done == 17
     lat2.sweep(13, 1)
@@ -180,30 +208,35 @@ SCAN_BETAS = [round(0.30 + 0.02 * j, 10) for j in range(16)]
 
 
 def test_beta_scan_L512_full_runs(eng, pool):
-    """2D L=512, 16 betas in [0.30, 0.60], cold start, 2000 sweeps each."""
+    """2D L=512, 16 betas in [0.30, 0.60], cold start, 2000 sweeps each, both layouts."""
     futs = [pool.submit(jobs.run, 2, 512, b, 20031109 + j, COLD_UP, 2000, 1)
             for j, b in enumerate(SCAN_BETAS)]
     for j, b in enumerate(SCAN_BETAS):
-        g = gpu_run(eng, 2, 512, b, 20031109 + j, COLD_UP, 2000, 1)
-        assert_same(g, futs[j].result(), f"L=512 beta={b}")
+        want = futs[j].result()
+        for layout in (INT8, BITPACK):
+            g = gpu_run(eng, 2, 512, b, 20031109 + j, COLD_UP, 2000, 1, layout=layout)
+            assert_same(g, want, f"L=512 beta={b} layout={layout}")
 
 
 def test_beta_scan_L8192_first_20_sweeps(eng, pool):
-    """2D L=8192 (67M sites), 16 betas, cold start: the first 20 sweeps."""
+    """2D L=8192 (67M sites), 16 betas, cold start: the first 20 sweeps, both layouts."""
     futs = [pool.submit(jobs.run, 2, 8192, b, 20031109 + j, COLD_UP, 20, 1)
             for j, b in enumerate(SCAN_BETAS)]
     for j, b in enumerate(SCAN_BETAS):
-        g = gpu_run(eng, 2, 8192, b, 20031109 + j, COLD_UP, 20, 1)
-        assert_same(g, futs[j].result(), f"L=8192 beta={b}")
+        want = futs[j].result()
+        for layout in (INT8, BITPACK):
+            g = gpu_run(eng, 2, 8192, b, 20031109 + j, COLD_UP, 20, 1, layout=layout)
+            assert_same(g, want, f"L=8192 beta={b} layout={layout}")
 
 
-def test_3d_L256_near_critical(eng, pool):
+@pytest.mark.parametrize("layout", [INT8, BITPACK])
+def test_3d_L256_near_critical(eng, pool, layout):
     """3D L=256 at beta=0.2216544, hot start: the first 20 sweeps against the
     oracle in full; then sweeps 20..999 with E/M every 10, and the final
     sweep checked as a single oracle transition from the GPU's state."""
     dims, L, beta, seed = 3, 256, 0.2216544, 20031109
     fut = pool.submit(jobs.run, dims, L, beta, seed, HOT, 20, 1)
-    lat = eng.Lattice(dims, L, beta, seed)
+    lat = eng.Lattice(dims, L, beta, seed, layout=layout)
     lat.sweep(20, 1)
     E, M = lat.observables()
     s20 = lat.get_spins()
