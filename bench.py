@@ -391,6 +391,74 @@ def run_gpu(args, world, rank, local):
     return 0
 
 
+def run_batched_workload(args):
+    """2048 independent lattices (70% 2D L in [16,1024], 30% 3D L in [8,128],
+    log-uniform), 500 sweeps each: one persistent CUDA-graph launch (launch
+    shape from the autotuner) against one ising_sweep call per lattice."""
+    import torch
+    from paper_cs_0312006_gb300 import _build, autotune, batched, engine, workloads
+    _build.build()
+    engine.load_library()
+    specs = workloads.batched_mix(n=args.batch_lattices, sweeps=args.batch_sweeps)
+    if args.no_tune:
+        tuned = {"opts": dict(block_threads=256, cluster_size=8, big_sites=65536),
+                 "layout": "auto", "results": []}
+    else:
+        tuned = autotune.tune(specs, use_cache=not args.retune)
+    opts, layout = tuned["opts"], tuned["layout"]
+    batched.run_batched(batched.scaled(specs[:64], 2), opts, 1, layout)  # warm-up
+    res = batched.compare_forms(specs, opts, layout)
+    line = {"metric": "site updates/s", "value": res["batched_updates_per_s"],
+            "unit": "site updates/s", "n_gpus": 1, "higher_is_better": True,
+            "workload": f"batched: {res['lattices']} lattices, {args.batch_sweeps} sweeps each, "
+                        "70% 2D L log-uniform [16,1024], 30% 3D L log-uniform [8,128], E/M every "
+                        "10 sweeps",
+            "batched": res, "autotune": {"opts": opts, "layout": layout,
+                                         "candidates": len(tuned["results"])},
+            "device": torch.cuda.get_device_name()}
+    print(json.dumps(line), flush=True)
+    if res["mismatches"]:
+        raise SystemExit(f"batched and plain forms differ on {res['mismatches']} lattices")
+    return 0
+
+
+def run_serving_workload(args):
+    """Poisson job stream (200 jobs/s): dims in {2,3}; L log-uniform (2D
+    32-4096, 3D 16-256); beta within 0.05 of the critical point; sweeps
+    log-uniform 100-20000; E/M every 10 sweeps; HBM budget 120 GB.  Reports
+    aggregate site updates/s and p50/p99 job latency (arrival to completion),
+    the first tenth of the jobs excluded from the percentiles."""
+    import torch
+    from paper_cs_0312006_gb300 import _build, autotune, engine, serve, workloads
+    _build.build()
+    engine.load_library()
+    jobs = workloads.poisson_jobs(args.serve_jobs, rate_per_s=args.serve_rate)
+    warm = workloads.poisson_jobs(8, rate_per_s=1e6, seed=99, l2d=(32, 128), l3d=(16, 32),
+                                  sweeps=(10, 20))
+    serve.Server(round_s=args.round_s).run(warm)  # load and warm the kernels
+    srv = serve.Server(hbm_budget_bytes=int(args.hbm_budget_gb * 1e9),
+                       round_s=args.round_s, keep_spins=False,
+                       batch_opts=dict(cluster_size=8, big_sites=65536))
+    summ = srv.run(jobs)
+    skip = max(0, len(jobs) // 10)
+    pct = serve.percentile_summary(srv.results, skip)
+    plain = None
+    if not args.no_plain:
+        psum, pres = serve.run_plain_fifo(jobs)
+        plain = dict(psum, **serve.percentile_summary(pres, skip))
+    line = {"metric": "site updates/s", "value": summ["updates_per_s"],
+            "unit": "site updates/s", "n_gpus": 1, "higher_is_better": True,
+            "workload": f"serving: {len(jobs)} Poisson jobs at {args.serve_rate}/s, dims 2/3, "
+                        "L log-uniform (2D 32-4096, 3D 16-256), beta_c +- 0.05, sweeps "
+                        "log-uniform 100-20000, E/M every 10, HBM budget "
+                        f"{args.hbm_budget_gb} GB",
+            "serving": dict(summ, **pct), "plain_fifo": plain,
+            "offered_load_updates_per_s": serve.offered_load(jobs, args.serve_rate),
+            "device": torch.cuda.get_device_name()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,6 +467,19 @@ def main():
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--L", type=int, default=L_SCAN)
     ap.add_argument("--layout", choices=["both", "int8", "bitpack"], default="both")
+    ap.add_argument("--workload", choices=["scan", "batched", "serving"], default="scan",
+                    help="scan: the 2D L=8192 beta scan (default line); batched: 2048 "
+                         "lattices in one launch vs one launch per lattice; serving: Poisson "
+                         "job stream")
+    ap.add_argument("--batch-lattices", type=int, default=2048)
+    ap.add_argument("--batch-sweeps", type=int, default=500)
+    ap.add_argument("--retune", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="batched: fixed launch shape")
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--hbm-budget-gb", type=float, default=120.0)
+    ap.add_argument("--round-s", type=float, default=0.05)
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--lattices", type=int, default=N_BETA,
                     help="how many of the 16 betas to run (profiling uses fewer)")
     ap.add_argument("--time-every", type=int, default=1,
@@ -411,6 +492,10 @@ def main():
     if args.warmup < 3 and args.impl == "engine":
         raise SystemExit("bench.py: at least 3 warm-up steps are required")
     world, rank, local = dist_setup()
+    if args.workload == "batched" and args.impl != "reference":
+        return run_batched_workload(args)
+    if args.workload == "serving" and args.impl != "reference":
+        return run_serving_workload(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_gpu(args, world, rank, local)

@@ -150,6 +150,58 @@ int ising_synchronize(ising_lattice *lat);
 /* Free everything the handle owns.  NULL is accepted. */
 void ising_destroy(ising_lattice *lat);
 
+/*
+ * Batched form: many independent lattices (any mix of dims, L, layout, beta,
+ * seed) advanced by one persistent launch, with the same arithmetic and draws
+ * as ising_sweep, so each lattice ends bit-identical to running it alone.
+ * Lattices with at least huge_sites sites are advanced by the per-lattice
+ * pass kernels (each pass over the whole GPU) on the batch stream; the others
+ * are jobs of one persistent kernel, taken largest first from a device work
+ * queue: lattices with at least big_sites sites are run by a thread-block
+ * cluster of cluster_size CTAs (colour passes separated by the hardware
+ * cluster barrier), smaller ones by a single CTA each.  The launch is captured once
+ * in a CUDA graph and replayed; each launch advances lattice i by sweeps[i]
+ * sweeps and records E/M after sweep u iff (u + 1) % measure_every[i] == 0.
+ */
+typedef struct ising_batch ising_batch; /* opaque */
+
+typedef struct ising_batch_opts {
+    int block_threads;  /* threads per CTA: 128, 256 or 512 (0: 256) */
+    int cluster_size;   /* CTAs per cluster for large lattices, 1..8 (0: 4);
+                           1 runs every lattice on a single CTA */
+    int64_t big_sites;  /* size threshold of the cluster queue (0: 2^18) */
+    int use_graph;      /* >= 0: capture the persistent launch in a CUDA graph and
+                           replay it; < 0: plain launches */
+    int64_t huge_sites; /* lattices this large use the per-lattice kernels
+                           (0: 2^22; < 0: never) */
+} ising_batch_opts;
+
+/*
+ * Build a batch over n distinct lattices of the current device.  sweeps[i] >= 0
+ * sweeps per launch for lattice i; measure_every may be NULL (every sweep) or
+ * give a value >= 1 per lattice; opts may be NULL.  All lattices are moved to
+ * `stream` (as by ising_set_stream).  The batch borrows the handles: between
+ * ising_batch_launch and ising_batch_sync they must not be used directly, and
+ * they must outlive the batch.  Device memory: a job table (64 B per lattice).
+ */
+int ising_batch_create(ising_batch **out, ising_lattice *const *lats, int n,
+                       const int64_t *sweeps, const int *measure_every,
+                       const ising_batch_opts *opts, void *stream);
+
+/* Advance every lattice of the batch by its sweeps (asynchronous). */
+int ising_batch_launch(ising_batch *b);
+
+/* Wait for the batch's launches; afterwards the lattices may be used
+ * directly (ising_observables, ising_get_spins, ...). */
+int ising_batch_sync(ising_batch *b);
+
+/* Resident grid size, the number of jobs in the cluster / CTA queues and the
+ * number of lattices advanced by the per-lattice kernels. */
+int ising_batch_info(const ising_batch *b, int *grid, int *n_big, int *n_small, int *n_huge);
+
+/* Free the batch (not the lattices).  NULL is accepted. */
+void ising_batch_destroy(ising_batch *b);
+
 /* Static description of a status code. */
 const char *ising_strerror(int code);
 

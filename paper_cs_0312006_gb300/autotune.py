@@ -1,0 +1,101 @@
+"""Autotuner for the batched launch.
+
+Searches the launch shape of the persistent batched kernel -- threads per CTA,
+CTAs per cluster for large lattices, the size threshold of the cluster queue,
+and the spin layout policy -- on a scaled-down sample of the workload, and
+keeps the fastest.  Every candidate must produce bit-identical spins and E/M
+for every lattice (the draws are keyed by site, sweep and colour, so the
+launch shape never changes a result); a candidate that does not is an error,
+not a slower choice.  The winner is cached as JSON per device name and
+workload signature.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import numpy as np
+
+from . import batched
+
+CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_cs_0312006_gb300", "autotune.json")
+
+CANDIDATES = [
+    dict(block_threads=bt, cluster_size=cs, big_sites=bs)
+    for bt in (256, 512)
+    for cs in (1, 2, 4, 8)
+    for bs in ((1 << 16, 1 << 18, 1 << 20) if cs > 1 else (1 << 30,))
+]
+LAYOUTS = ("auto", "int8")
+
+
+def signature(specs) -> str:
+    h = hashlib.sha1()
+    for sp in specs:
+        h.update(f"{sp.dims},{sp.L},{sp.sweeps},{sp.measure_every};".encode())
+    return h.hexdigest()[:16]
+
+
+def _device_name() -> str:
+    import torch
+    return torch.cuda.get_device_name()
+
+
+def _fingerprint(lats):
+    out = []
+    for lat in lats:
+        E, M = lat.observables()
+        s = lat.get_spins()
+        out.append((hashlib.sha1(s.tobytes()).hexdigest(), E.tobytes(), M.tobytes()))
+        lat.close()
+    return out
+
+
+def tune(specs, sample_sweeps: int = 40, sample_lattices: int = 512, seed: int = 0,
+         use_cache: bool = True, verbose: bool = False) -> dict:
+    """Pick launch options for ``specs``; returns {"opts": ..., "layout": ...,
+    "results": [...]}."""
+    key = f"{_device_name()}|{signature(specs)}"
+    if use_cache and os.path.exists(CACHE):
+        try:
+            with open(CACHE) as f:
+                cache = json.load(f)
+            if key in cache:
+                return cache[key]
+        except (OSError, ValueError):
+            pass
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(specs), size=min(sample_lattices, len(specs)), replace=False)
+    sample = batched.scaled([specs[i] for i in sorted(idx)], sample_sweeps)
+    results = []
+    reference = None
+    for layout in LAYOUTS:
+        for opts in CANDIDATES:
+            batched.run_batched(sample, opts, 1, layout)[1]  # warm-up (graph capture)
+            dt, lats = batched.run_batched(sample, opts, 1, layout)
+            fp = _fingerprint(lats)
+            if reference is None:
+                reference = fp
+            elif fp != reference:
+                raise RuntimeError(f"autotune: candidate {opts} / {layout} changed a result")
+            results.append({"opts": opts, "layout": layout, "seconds": dt})
+            if verbose:
+                print(f"{layout:5s} {opts} {dt * 1e3:.2f} ms")
+    best = min(results, key=lambda r: r["seconds"])
+    entry = {"opts": best["opts"], "layout": best["layout"], "results": results,
+             "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+    if use_cache:
+        try:
+            os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+            cache = {}
+            if os.path.exists(CACHE):
+                with open(CACHE) as f:
+                    cache = json.load(f)
+            cache[key] = entry
+            with open(CACHE, "w") as f:
+                json.dump(cache, f, indent=1)
+        except (OSError, ValueError):
+            pass
+    return entry

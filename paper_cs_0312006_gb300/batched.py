@@ -1,0 +1,100 @@
+"""Batched workload driver: many independent lattices advanced by one
+persistent CUDA-graph launch (``Batch``) versus the plain form, one
+``ising_sweep`` call per lattice issued back to back on one stream.
+
+Both forms run identical arithmetic, so every lattice must end bit-identical;
+``compare_forms`` checks that for every lattice and reports aggregate site
+updates per second of each form.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import engine
+from .workloads import AUTO, INT8, LatticeSpec
+
+
+def make_lattices(specs, layout_policy: str = "auto", stream=None):
+    """Create one handle per spec (hot start).  ``layout_policy``: "auto"
+    (bit-packed where L % 64 == 0), "int8" or "bitpack"."""
+    lats = []
+    for sp in specs:
+        if layout_policy == "int8":
+            lay = INT8
+        elif layout_policy == "bitpack":
+            lay = engine.BITPACK if sp.L % 64 == 0 else INT8
+        else:
+            lay = AUTO
+        lats.append(engine.Lattice(sp.dims, sp.L, sp.beta, sp.seed, layout=lay, start=sp.start,
+                                   stream=stream))
+    return lats
+
+
+def total_updates(specs) -> int:
+    return int(sum(sp.sites * sp.sweeps for sp in specs))
+
+
+def run_batched(specs, opts: dict | None = None, launches: int = 1, layout_policy="auto",
+                stream=None, warm=True):
+    """Returns (seconds, lattices) for ``launches`` launches of one Batch."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    lats = make_lattices(specs, layout_policy, stream)
+    batch = engine.Batch(lats, [sp.sweeps for sp in specs], [sp.measure_every for sp in specs],
+                         stream=stream, **(opts or {}))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(launches):
+        batch.launch()
+    batch.sync()
+    dt = time.perf_counter() - t0
+    batch.close()
+    return dt, lats
+
+
+def run_plain(specs, launches: int = 1, layout_policy="auto", stream=None):
+    """One ising_sweep(sweeps, measure_every) per lattice, back to back."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    lats = make_lattices(specs, layout_policy, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(launches):
+        for sp, lat in zip(specs, lats):
+            lat.sweep(sp.sweeps, sp.measure_every)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, lats
+
+
+def lattice_result(lat):
+    E, M = lat.observables()
+    return lat.get_spins(), E, M
+
+
+def same_result(a, b) -> bool:
+    return all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def compare_forms(specs, opts=None, layout_policy="auto"):
+    """Run both forms on the same specs; returns a dict with both rates and
+    the number of lattices whose spins and E/M records differ (must be 0)."""
+    upd = total_updates(specs)
+    tb, lats_b = run_batched(specs, opts, 1, layout_policy)
+    tp, lats_p = run_plain(specs, 1, layout_policy)
+    mismatches = 0
+    for a, b in zip(lats_b, lats_p):
+        if not same_result(lattice_result(a), lattice_result(b)):
+            mismatches += 1
+        a.close()
+        b.close()
+    return {"lattices": len(specs), "site_updates": upd,
+            "batched_s": tb, "batched_updates_per_s": upd / tb,
+            "plain_s": tp, "plain_updates_per_s": upd / tp,
+            "batched_over_plain": tp / tb, "mismatches": mismatches}
+
+
+def scaled(specs, sweeps: int):
+    return [LatticeSpec(sp.dims, sp.L, sp.beta, sp.seed, sp.start, sweeps,
+                        min(sp.measure_every, sweeps), sp.layout) for sp in specs]

@@ -1,0 +1,443 @@
+// batch.cu -- many independent lattices of uneven size in one persistent
+// launch (the batched form of the checkerboard sweep; same arithmetic, same
+// draws, so each lattice's result is identical to running it alone).
+//
+// Lattices of at least huge_sites sites are advanced with the per-lattice
+// pass kernels (each pass spread over the whole GPU), issued on the batch's
+// stream ahead of the persistent launch; everything smaller goes through the
+// persistent kernel.
+//
+// Work queue: one job per lattice, holding everything its sweeps need (spin
+// arrays, thresholds, key, first sweep index, sweep count, measurement
+// interval, record slots).  Jobs are ordered by work (sites x sweeps),
+// largest first, and split in two queues at a size threshold:
+//   - large jobs are run by a thread-block cluster: the CTAs of the cluster
+//     share the job's words, and consecutive colour passes are separated by
+//     the hardware cluster barrier (release/acquire at cluster scope), with
+//     the other colour read through L2 so that words written by another CTA
+//     of the cluster are seen;
+//   - small jobs are run by one CTA each, passes separated by __syncthreads.
+// Each cluster (then each CTA) takes the next job with one atomicAdd on a
+// queue counter and runs all of the job's sweeps before taking another, so
+// there is no inter-CTA waiting other than the cluster barrier.  At the end of
+// a job its sweep index and record pointer advance in the job table, so
+// replaying the same launch (a CUDA graph) continues every lattice.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "engine_internal.h"
+#include "ising_device.cuh"
+#include "pass_bodies.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ising {
+
+struct BatchJob {
+    void* col0;
+    void* col1;
+    unsigned long long* obs;  // (E, M) slots of this launch's records; zeroed
+    uint32_t thr0, thr1, thr2, key0, key1;
+    uint32_t t0;              // index of the job's next sweep
+    int32_t dims, layout, L, W;
+    uint32_t rows, half;
+    int32_t nsweeps, measure_every;
+};
+
+namespace {
+
+constexpr int kModeCta = 0, kModeCluster = 1;
+
+template <int MODE>
+__device__ __forceinline__ void group_sync() {
+    if (MODE == kModeCluster)
+        cg::this_cluster().sync();
+    else
+        __syncthreads();
+}
+
+template <int DIMS, int LAYOUT, bool MEASURE, int NC>
+__device__ __forceinline__ void job_pass(const BatchJob& j, int c, uint32_t t, uint32_t rank,
+                                         uint32_t nthr, int& e_acc, int& m_acc) {
+    PassArgs a;
+    a.own = c == 0 ? j.col0 : j.col1;
+    a.other = c == 0 ? j.col1 : j.col0;
+    a.obs = nullptr;
+    a.rows = j.rows;
+    a.L = j.L;
+    a.W = j.W;
+    a.thr0 = j.thr0;
+    a.thr1 = j.thr1;
+    a.thr2 = j.thr2;
+    a.key0 = j.key0;
+    a.key1 = j.key1;
+    a.t = t;
+    a.c = c;
+    if (LAYOUT == ISING_INT8) {
+        WordGeom g;
+        g.W = (uint32_t)j.W;
+        g.L = (uint32_t)j.L;
+        g.rows = j.rows;
+        g.half = j.half;
+        const uint32_t vecs = (j.half + 15u) >> 4;
+        int m_neg = 0, n_sites = 0;
+        for (uint32_t v = rank; v < vecs; v += nthr)
+            int8_vec<DIMS, MEASURE, NC>(a, g, v, e_acc, m_neg, n_sites);
+        if (MEASURE) m_acc += n_sites - 2 * m_neg;
+    } else {
+        const uint32_t items = j.rows * ((uint32_t)j.W >> 5);
+        for (uint32_t it = rank; it < items; it += nthr)
+            packed_word<DIMS, MEASURE, NC>(a, it, e_acc, m_acc);
+    }
+}
+
+template <int DIMS, int LAYOUT, int MODE>
+__device__ void run_job(BatchJob* jp, uint32_t rank, uint32_t nthr, bool leader) {
+    constexpr int NC = MODE == kModeCluster ? 2 : 0;
+    const BatchJob j = *jp;
+    int rec = 0;
+    for (int s = 0; s < j.nsweeps; ++s) {
+        const uint32_t t = j.t0 + (uint32_t)s;
+        const bool measure = ((uint64_t)t + 1u) % (uint64_t)j.measure_every == 0u;
+        int e = 0, m = 0;
+        for (int c = 0; c < 2; ++c) {
+            if (measure)
+                job_pass<DIMS, LAYOUT, true, NC>(j, c, t, rank, nthr, e, m);
+            else
+                job_pass<DIMS, LAYOUT, false, NC>(j, c, t, rank, nthr, e, m);
+            group_sync<MODE>();  // this pass's writes before the next pass reads them
+        }
+        if (measure) {
+            block_reduce_add(e, m, j.obs + 2 * rec, true);
+            ++rec;
+        }
+    }
+    group_sync<MODE>();
+    if (leader) {  // continue from here at the next launch
+        jp->t0 = j.t0 + (uint32_t)j.nsweeps;
+        jp->obs = j.obs + 2 * rec;
+    }
+}
+
+template <int MODE>
+__device__ void dispatch_job(BatchJob* jp, uint32_t rank, uint32_t nthr, bool leader) {
+    const int dims = jp->dims, layout = jp->layout;
+    if (dims == 2) {
+        if (layout == ISING_BITPACK)
+            run_job<2, ISING_BITPACK, MODE>(jp, rank, nthr, leader);
+        else
+            run_job<2, ISING_INT8, MODE>(jp, rank, nthr, leader);
+    } else {
+        if (layout == ISING_BITPACK)
+            run_job<3, ISING_BITPACK, MODE>(jp, rank, nthr, leader);
+        else
+            run_job<3, ISING_INT8, MODE>(jp, rank, nthr, leader);
+    }
+}
+
+// counters[0] / counters[1]: next index into the large / small queue.
+__global__ void __launch_bounds__(512) batch_kernel(BatchJob* jobs, const int* order_big,
+                                                    int n_big, const int* order_small,
+                                                    int n_small, int* counters) {
+    __shared__ int s_job;
+    cg::cluster_group cl = cg::this_cluster();
+    // phase 1: large jobs, one cluster per job
+    const uint32_t crank = cl.block_rank() * blockDim.x + threadIdx.x;
+    const uint32_t cthreads = cl.num_blocks() * blockDim.x;
+    while (true) {
+        if (cl.block_rank() == 0 && threadIdx.x == 0) s_job = atomicAdd(&counters[0], 1);
+        cl.sync();
+        const int j = *cl.map_shared_rank(&s_job, 0);
+        cl.sync();
+        if (j >= n_big) break;
+        dispatch_job<kModeCluster>(&jobs[order_big[j]], crank, cthreads, crank == 0);
+    }
+    // phase 2: small jobs, one CTA per job
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_job = atomicAdd(&counters[1], 1);
+        __syncthreads();
+        const int j = s_job;
+        if (j >= n_small) break;
+        dispatch_job<kModeCta>(&jobs[order_small[j]], threadIdx.x, blockDim.x, threadIdx.x == 0);
+    }
+}
+
+}  // namespace
+
+}  // namespace ising
+
+using namespace ising;
+
+struct ising_batch {
+    std::vector<ising_lattice*> lats;
+    std::vector<int64_t> sweeps;
+    std::vector<int> every;
+    std::vector<int> huge;  // lattices advanced by the per-lattice kernels
+    std::vector<char> in_table;
+    ising_batch_opts opts{};
+    cudaStream_t stream = nullptr;
+    BatchJob* d_jobs = nullptr;
+    BatchJob* h_jobs = nullptr;  // pinned mirror
+    int* d_order = nullptr;      // [big..., small...]
+    int* d_counters = nullptr;
+    int n_big = 0, n_small = 0;
+    int grid = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t uploaded = nullptr;
+    bool table_valid = false;  // device table equals the host mirror's continuation
+    int64_t launches = 0;
+};
+
+namespace {
+
+int records_in(uint64_t t, int64_t n, int every) {
+    return (int)((t + (uint64_t)n) / (uint64_t)every - t / (uint64_t)every);
+}
+
+cudaError_t launch_batch_kernel(ising_batch* b, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)b->grid);
+    cfg.blockDim = dim3((unsigned)b->opts.block_threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)b->opts.cluster_size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_kernel, b->d_jobs, (const int*)b->d_order, b->n_big,
+                              (const int*)(b->d_order + b->n_big), b->n_small, b->d_counters);
+}
+
+void free_batch(ising_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->uploaded) cudaEventDestroy(b->uploaded);
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    if (b->d_order) cudaFree(b->d_order);
+    if (b->d_counters) cudaFree(b->d_counters);
+    if (b->h_jobs) cudaFreeHost(b->h_jobs);
+    delete b;
+}
+
+}  // namespace
+
+#define ISING_BCHECK(call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ising::cuda_fail(e_); \
+    } while (0)
+
+extern "C" {
+
+int ising_batch_create(ising_batch** out, ising_lattice* const* lats, int n,
+                       const int64_t* sweeps, const int* measure_every,
+                       const ising_batch_opts* opts, void* stream) {
+    if (!out) return ISING_EINVAL;
+    *out = nullptr;
+    if (!lats || n < 1 || !sweeps) return ISING_EINVAL;
+    ising_batch_opts o = {};
+    if (opts) o = *opts;
+    if (o.block_threads == 0) o.block_threads = 256;
+    if (o.cluster_size == 0) o.cluster_size = 4;
+    if (o.big_sites == 0) o.big_sites = 1 << 18;
+    if (o.huge_sites == 0) o.huge_sites = (int64_t)1 << 22;
+    if (o.block_threads != 128 && o.block_threads != 256 && o.block_threads != 512)
+        return ISING_EINVAL;
+    if (o.cluster_size < 1 || o.cluster_size > 8) return ISING_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!lats[i] || sweeps[i] < 0 || sweeps[i] > 0x7FFFFFFF) return ISING_EINVAL;
+        if (measure_every && measure_every[i] < 1) return ISING_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (lats[k] == lats[i]) return ISING_EINVAL;  // a lattice may appear once
+    }
+    ising_batch* b = new (std::nothrow) ising_batch();
+    if (!b) return ISING_ENOMEM;
+    b->lats.assign(lats, lats + n);
+    b->sweeps.assign(sweeps, sweeps + n);
+    b->every.resize(n);
+    for (int i = 0; i < n; ++i) b->every[i] = measure_every ? measure_every[i] : 1;
+    b->opts = o;
+    b->stream = static_cast<cudaStream_t>(stream);
+    int rc = ISING_OK;
+    for (int i = 0; i < n && rc == ISING_OK; ++i) rc = ising_set_stream(b->lats[i], stream);
+    if (rc != ISING_OK) {
+        free_batch(b);
+        return rc;
+    }
+
+    // queues: largest work first, split at the size thresholds
+    std::vector<int> big, small;
+    b->in_table.assign(n, 1);
+    for (int i = 0; i < n; ++i) {
+        if (o.huge_sites > 0 && b->lats[i]->sites >= o.huge_sites) {
+            b->huge.push_back(i);
+            b->in_table[i] = 0;
+        } else {
+            (b->lats[i]->sites >= o.big_sites ? big : small).push_back(i);
+        }
+    }
+    auto by_work = [&](int x, int y) {
+        return b->lats[x]->sites * b->sweeps[x] > b->lats[y]->sites * b->sweeps[y];
+    };
+    std::stable_sort(big.begin(), big.end(), by_work);
+    std::stable_sort(small.begin(), small.end(), by_work);
+    if (o.cluster_size == 1) {  // no cooperative phase: everything per CTA
+        small.insert(small.begin(), big.begin(), big.end());
+        std::stable_sort(small.begin(), small.end(), by_work);
+        big.clear();
+    }
+    b->n_big = (int)big.size();
+    b->n_small = (int)small.size();
+    std::vector<int> order(big);
+    order.insert(order.end(), small.begin(), small.end());
+
+    cudaError_t e = cudaMalloc(&b->d_jobs, sizeof(BatchJob) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_jobs, sizeof(BatchJob) * (size_t)n);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+    if (e == cudaSuccess && !order.empty())  // empty when every lattice is huge
+        e = cudaMemcpy(b->d_order, order.data(), sizeof(int) * order.size(),
+                       cudaMemcpyHostToDevice);
+    // persistent grid: as many clusters as can be resident
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3((unsigned)o.block_threads);
+        cfg.gridDim = dim3((unsigned)(o.cluster_size * 1024));
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)o.cluster_size;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&clusters, batch_kernel, &cfg);
+        if (e == cudaSuccess && clusters < 1) e = cudaErrorInvalidConfiguration;
+        b->grid = clusters * o.cluster_size;
+    }
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e);
+    }
+    *out = b;
+    return ISING_OK;
+}
+
+int ising_batch_launch(ising_batch* b) {
+    if (!b) return ISING_EINVAL;
+    const int n = (int)b->lats.size();
+    // host-side checks and record space, then the job table if it changed
+    bool moved = !b->table_valid;
+    for (int i = 0; i < n; ++i) {
+        ising_lattice* h = b->lats[i];
+        if (b->sweeps[i] > 0 && h->t + (uint64_t)b->sweeps[i] - 1 > kMaxSweep) return ISING_ERANGE;
+    }
+    // the largest lattices first, each pass over the whole GPU
+    for (int i : b->huge) {
+        const int rc = ising_sweep(b->lats[i], b->sweeps[i], b->every[i]);
+        if (rc != ISING_OK) return rc;
+    }
+    ISING_BCHECK(cudaEventSynchronize(b->uploaded));  // the mirror is free to change
+    for (int i = 0; i < n; ++i) {
+        if (!b->in_table[i]) continue;
+        ising_lattice* h = b->lats[i];
+        const int r = records_in(h->t, b->sweeps[i], b->every[i]);
+        unsigned long long* before = h->obs;
+        // keep room for several launches so that replays need no new table
+        int rc = ensure_records(h, h->n_rec + 8 * (int64_t)(r > 0 ? r : 0));
+        if (rc != ISING_OK) return rc;
+        if (h->obs != before) moved = true;
+        BatchJob& j = b->h_jobs[i];
+        j.col0 = h->col[0];
+        j.col1 = h->col[1];
+        j.obs = h->obs + 2 * h->n_rec;
+        j.thr0 = h->thr[0];
+        j.thr1 = h->thr[1];
+        j.thr2 = h->thr[2];
+        j.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
+        j.key1 = (uint32_t)(h->seed >> 32);
+        j.t0 = (uint32_t)h->t;
+        j.dims = h->dims;
+        j.layout = h->layout;
+        j.L = h->L;
+        j.W = h->W;
+        j.rows = (uint32_t)h->rows;
+        j.half = (uint32_t)h->half_sites;
+        j.nsweeps = (int32_t)b->sweeps[i];
+        j.measure_every = b->every[i];
+    }
+    // records reserved for later launches must stay inside the capacity: if the
+    // last reserve is about to run out, the table is rebuilt (moved == true)
+    if (moved) {
+        ISING_BCHECK(cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(BatchJob) * (size_t)n,
+                                     cudaMemcpyHostToDevice, b->stream));
+        ISING_BCHECK(cudaEventRecord(b->uploaded, b->stream));
+        b->table_valid = true;
+    }
+    if (b->opts.use_graph >= 0 && !b->exec && b->n_big + b->n_small > 0) {
+        // capture [reset queue counters, persistent kernel] once; replay it
+        cudaStream_t cap = nullptr;
+        ISING_BCHECK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = launch_batch_kernel(b, cap);
+            e = cudaStreamEndCapture(cap, &graph);
+            if (e == cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (b->n_big + b->n_small > 0) {
+        if (b->exec)
+            ISING_BCHECK(cudaGraphLaunch(b->exec, b->stream));
+        else
+            ISING_BCHECK(launch_batch_kernel(b, b->stream));
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!b->in_table[i]) continue;
+        ising_lattice* h = b->lats[i];
+        h->n_rec += records_in(h->t, b->sweeps[i], b->every[i]);
+        h->t += (uint64_t)b->sweeps[i];
+    }
+    // the device table now holds the continuation; it stays valid while no
+    // lattice's record buffer moves and nothing else touches the lattices
+    ++b->launches;
+    return ISING_OK;
+}
+
+int ising_batch_sync(ising_batch* b) {
+    if (!b) return ISING_EINVAL;
+    ISING_BCHECK(cudaStreamSynchronize(b->stream));
+    b->table_valid = false;  // lattices may now be used directly; rebuild next time
+    return ISING_OK;
+}
+
+void ising_batch_destroy(ising_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+}
+
+int ising_batch_info(const ising_batch* b, int* grid, int* n_big, int* n_small, int* n_huge) {
+    if (!b) return ISING_EINVAL;
+    if (grid) *grid = b->grid;
+    if (n_big) *n_big = b->n_big;
+    if (n_small) *n_small = b->n_small;
+    if (n_huge) *n_huge = (int)b->huge.size();
+    return ISING_OK;
+}
+
+}  // extern "C"

@@ -16,36 +16,23 @@
 using ising::DeviceProps;
 using ising::PassArgs;
 
-struct ising_lattice {
-    int dims = 0, L = 0, layout = ISING_INT8;
-    double beta = 0.0;
-    uint64_t seed = 0;
-    uint32_t thr[3] = {0, 0, 0};
-    int64_t sites = 0, half_sites = 0, rows = 0;
-    int W = 0;
-    void* col[2] = {nullptr, nullptr};  // colour 0 (black) and colour 1 (white) arrays
-    size_t col_bytes = 0;
-    uint64_t t = 0;                     // index of the next sweep
-    cudaStream_t stream = nullptr;
-    unsigned long long* obs = nullptr;  // (E, M) int64 pairs
-    int64_t obs_cap = 0, n_rec = 0;
-    const DeviceProps* dp = nullptr;
-};
-
 namespace {
 
-constexpr uint64_t kMaxSites = 1ull << 34;
-constexpr uint64_t kMaxSweep = 0xFFFFFFFFull;  // the sweep index is a 32-bit counter word
+constexpr uint64_t kMaxSites = 1ull << 32;  // 32-bit half indices in the kernels
 
 std::mutex g_props_mu;
 DeviceProps g_props[64];
 
+}  // namespace
+
+namespace ising {
+
 int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? ISING_ENOMEM : ISING_ECUDA; }
 
-#define ISING_CHECK(call)                          \
-    do {                                           \
-        cudaError_t e_ = (call);                   \
-        if (e_ != cudaSuccess) return cuda_fail(e_); \
+#define ISING_CHECK(call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ising::cuda_fail(e_); \
     } while (0)
 
 int device_props(const DeviceProps** out) {
@@ -169,7 +156,9 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     return ISING_OK;
 }
 
-}  // namespace
+}  // namespace ising
+
+using namespace ising;
 
 extern "C" {
 
@@ -222,10 +211,11 @@ int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t see
     h->W = L / 2;
     h->rows = dims == 2 ? L : (int64_t)L * L;
     h->dp = dp;
+    // 16 spare bytes: the word kernels may read one word past the last one
     if (use_layout == ISING_BITPACK)
-        h->col_bytes = (size_t)h->rows * (size_t)(L / 64) * sizeof(uint32_t);
+        h->col_bytes = (size_t)h->rows * (size_t)(L / 64) * sizeof(uint32_t) + 16;
     else
-        h->col_bytes = ((size_t)h->half_sites + 15) & ~(size_t)15;
+        h->col_bytes = (((size_t)h->half_sites + 15) & ~(size_t)15) + 16;
     for (int c = 0; c < 2; ++c) {
         cudaError_t e = cudaMalloc(&h->col[c], h->col_bytes);
         if (e != cudaSuccess) {

@@ -2,12 +2,37 @@
 // kernel translation units (not part of the public C ABI).
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "ising.h"
 
 namespace ising {
 
 struct PassArgs;
+struct DeviceProps;
+
+}  // namespace ising
+
+// A lattice handle (the opaque type of the C ABI).
+struct ising_lattice {
+    int dims = 0, L = 0, layout = ISING_INT8;
+    double beta = 0.0;
+    uint64_t seed = 0;
+    uint32_t thr[3] = {0, 0, 0};
+    int64_t sites = 0, half_sites = 0, rows = 0;
+    int W = 0;
+    void* col[2] = {nullptr, nullptr};  // colour 0 (black) and colour 1 (white) arrays
+    size_t col_bytes = 0;
+    uint64_t t = 0;                     // index of the next sweep
+    cudaStream_t stream = nullptr;
+    unsigned long long* obs = nullptr;  // (E, M) int64 pairs; slots >= n_rec are zero
+    int64_t obs_cap = 0, n_rec = 0;
+    const ising::DeviceProps* dp = nullptr;
+};
+
+namespace ising {
 
 struct DeviceProps {
     int device = -1;
@@ -15,6 +40,12 @@ struct DeviceProps {
     int blocks_per_sm_vec[2][2] = {{1, 1}, {1, 1}};    // int8 vector pass [dims-2][measure]
     int blocks_per_sm_packed[2][2] = {{1, 1}, {1, 1}}; // bit-packed pass [dims-2][measure]
 };
+
+// engine.cu helpers shared with batch.cu
+int cuda_fail(cudaError_t e);
+int device_props(const DeviceProps** out);
+int ensure_records(ising_lattice* h, int64_t need);
+constexpr uint64_t kMaxSweep = 0xFFFFFFFFull;  // the sweep index is a 32-bit counter word
 
 // int8 layout (sweep_int8.cu)
 cudaError_t int8_query_occupancy(DeviceProps& dp);

@@ -66,16 +66,6 @@ struct PassArgs {
     int strips;             // row strips per column, vector kernels only
 };
 
-// Number of thresholds a 32-bit draw u lies below.  The thresholds decrease
-// with k, so for k = 2(dims - d) (d = disagreeing neighbours, d < dims) the
-// Metropolis test u < thr[k] holds iff count(u) + d >= dims.
-template <int DIMS>
-__device__ __forceinline__ uint32_t below_count(uint32_t u, const PassArgs& a) {
-    uint32_t n = (u < a.thr0) + (u < a.thr1);
-    if (DIMS == 3) n += (u < a.thr2);
-    return n;
-}
-
 // Block-wide sum of two ints followed by one 64-bit atomic each into the
 // sweep's slot.  Integer addition is exact, so the order of the atomics does
 // not matter and the totals are bit-reproducible.

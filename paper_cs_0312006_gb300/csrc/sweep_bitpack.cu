@@ -21,153 +21,20 @@
 
 #include "engine_internal.h"
 #include "ising_device.cuh"
+#include "pass_bodies.cuh"
 
 namespace ising {
 
 namespace {
 
-__device__ __forceinline__ int wrap_prev(int v, int n) { return v == 0 ? n - 1 : v - 1; }
-__device__ __forceinline__ int wrap_next(int v, int n) { return v == n - 1 ? 0 : v + 1; }
-
-// Disagreement count masks for 32 sites.  For 2D (four neighbour xors
-// a, b, c, e): `always` = d >= 2, eq1 = d == 1, eq0 = d == 0.  For 3D (six):
-// `always` = d >= 3, eq2, eq1, eq0.
-struct Counts {
-    uint32_t always, eq0, eq1, eq2;
-};
-
-__device__ __forceinline__ Counts count2(uint32_t a, uint32_t b, uint32_t c, uint32_t e) {
-    const uint32_t s1 = a ^ b, c1 = a & b;
-    const uint32_t s2 = c ^ e, c2 = c & e;
-    const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
-    // d = b0 + 2 (c1 + c2 + c3); any carry means d >= 2
-    const uint32_t always = c1 | c2 | c3;
-    return Counts{always, ~(b0 | always), b0 & ~always, 0u};
-}
-
-__device__ __forceinline__ Counts count3(uint32_t a, uint32_t b, uint32_t c, uint32_t d,
-                                         uint32_t e, uint32_t f) {
-    // two full adders, then the weight-2 carries added in a third
-    const uint32_t s1 = a ^ b ^ c, k1 = (a & b) | (c & (a ^ b));
-    const uint32_t s2 = d ^ e ^ f, k2 = (d & e) | (f & (d ^ e));
-    const uint32_t bit0 = s1 ^ s2, k0 = s1 & s2;
-    const uint32_t bit1 = k1 ^ k2 ^ k0, bit2 = (k1 & k2) | (k0 & (k1 ^ k2));
-    // count = bit0 + 2 bit1 + 4 bit2; >= 3 iff bit2 or (bit1 and bit0)
-    const uint32_t always = bit2 | (bit1 & bit0);
-    const uint32_t low = ~(bit2 | bit1);  // count in {0, 1}
-    return Counts{always, low & ~bit0, low & bit0, bit1 & ~bit0 & ~bit2};
-}
-
-// Accept mask of the 4 sites of Philox group i (bits 4i..4i+3) with dE > 0.
-template <int DIMS>
-__device__ __forceinline__ uint32_t group_accept(const Counts& k, const Philox4& u, int i,
-                                                 const PassArgs& a) {
-    const uint32_t w[4] = {u.w0, u.w1, u.w2, u.w3};
-    uint32_t acc = 0u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int b = 4 * i + j;
-        uint32_t t;
-        if (DIMS == 2) {
-            t = (k.eq0 >> b) & 1u ? a.thr1 : a.thr0;
-        } else {
-            t = (k.eq0 >> b) & 1u ? a.thr2 : ((k.eq1 >> b) & 1u ? a.thr1 : a.thr0);
-        }
-        acc |= (w[j] < t ? 1u : 0u) << b;
-    }
-    return acc;
-}
-
+// One item = one 32-site word of the colour array (see packed_word()).
 template <int DIMS, bool MEASURE>
 __global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a) {
-    const int nq = a.W >> 5;  // words per half row
-    const int L = a.L;
-    const uint32_t items = (uint32_t)a.rows * (uint32_t)nq;
+    const uint32_t items = (uint32_t)a.rows * ((uint32_t)a.W >> 5);
     const uint32_t stride = gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    uint32_t* own = static_cast<uint32_t*>(a.own);
-    const uint32_t* other = static_cast<const uint32_t*>(a.other);
     int e_acc = 0, m_acc = 0;
-    // every lane runs the same number of trips so the shuffles see full warps
-    const uint32_t trips = (items + stride - 1) / stride;
-    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    for (uint32_t trip = 0; trip < trips; ++trip, g += stride) {
-        const bool valid = g < items;
-        const uint32_t gg = valid ? g : 0u;
-        const int r = (int)(gg / (uint32_t)nq);
-        const int q = (int)(gg - (uint32_t)r * nq);
-        int y, z;
-        if (DIMS == 2) {
-            y = r;
-            z = 0;
-        } else {
-            z = r / L;
-            y = r - z * L;
-        }
-        const int plane = z * L;
-        const uint32_t row = (uint32_t)r * nq;
-        const uint32_t o = __ldg(other + row + q);
-        const uint32_t oym = __ldg(other + (uint32_t)(plane + wrap_prev(y, L)) * nq + q);
-        const uint32_t oyp = __ldg(other + (uint32_t)(plane + wrap_next(y, L)) * nq + q);
-        uint32_t ozm = 0u, ozp = 0u;
-        if (DIMS == 3) {
-            ozm = __ldg(other + (uint32_t)(wrap_prev(z, L) * L + y) * nq + q);
-            ozp = __ldg(other + (uint32_t)(wrap_next(z, L) * L + y) * nq + q);
-        }
-        const uint32_t s = own[row + q];
-        uint32_t prev = __shfl_up_sync(0xffffffffu, o, 1);
-        uint32_t next = __shfl_down_sync(0xffffffffu, o, 1);
-        const int p = (a.c + y + z) & 1;
-        uint32_t sh;
-        if (p == 0) {
-            if (lane == 0 || q == 0) prev = __ldg(other + row + wrap_prev(q, nq));
-            sh = __funnelshift_l(prev, o, 1);  // bit b <- neighbour h' - 1
-        } else {
-            if (lane == 31 || q == nq - 1) next = __ldg(other + row + wrap_next(q, nq));
-            sh = __funnelshift_r(o, next, 1);  // bit b <- neighbour h' + 1
-        }
-        const uint32_t xa = s ^ o, xb = s ^ sh, xc = s ^ oym, xd = s ^ oyp;
-        Counts k;
-        if (DIMS == 2) {
-            k = count2(xa, xb, xc, xd);
-        } else {
-            k = count3(xa, xb, xc, xd, s ^ ozm, s ^ ozp);
-        }
-        uint32_t flip = k.always;
-        const uint32_t need = ~k.always;
-        const uint32_t g0 = (row + (uint32_t)q) * 8u;  // (r*W + 32q) / 4
-        if (valid && need) {
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                Philox4 u[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int gi = 4 * half + i;
-                    if ((need >> (4 * gi)) & 0xFu)
-                        u[i] = philox4x32_10(g0 + (uint32_t)gi, a.t, (uint32_t)a.c, kTagSweep,
-                                             a.key0, a.key1);
-                    else
-                        u[i] = Philox4{0u, 0u, 0u, 0u};
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) flip |= group_accept<DIMS>(k, u[i], 4 * half + i, a);
-            }
-        }
-        const uint32_t snew = s ^ (flip & (k.always | need));
-        if (valid) {
-            own[row + q] = snew;
-            if (MEASURE) {
-                m_acc += 2 * __popc(snew) - 32;
-                if (a.c == 1) {
-                    // E_white = sum over white sites of (2 d_new - 2 dims)
-                    int dsum = __popc(snew ^ o) + __popc(snew ^ sh) + __popc(snew ^ oym) +
-                               __popc(snew ^ oyp);
-                    if (DIMS == 3) dsum += __popc(snew ^ ozm) + __popc(snew ^ ozp);
-                    e_acc += 2 * dsum - 32 * 2 * DIMS;
-                }
-            }
-        }
-    }
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride)
+        packed_word<DIMS, MEASURE, 1>(a, g, e_acc, m_acc);
     if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
 }
 

@@ -25,101 +25,14 @@
 
 #include "engine_internal.h"
 #include "ising_device.cuh"
+#include "pass_bodies.cuh"
 
 namespace ising {
 
 namespace {
 
-constexpr uint32_t kBit1 = 0x02020202u;
-constexpr uint32_t kBit7 = 0x80808080u;
-constexpr uint32_t kOnes = 0x01010101u;
-
-// Byte mask 0xFE of each site whose flip is decided without a draw.  Byte j of
-// D is 2*d_j (d_j = disagreeing neighbours); bit 7 of D + bias is set iff
-// d_j >= dims, i.e. dE <= 0.  0x80 -> 0xFE by F | (F - (F >> 6)), borrow-free.
-template <int DIMS>
-__device__ __forceinline__ uint32_t downhill_mask(uint32_t D) {
-    constexpr uint32_t bias = (0x80u - 2u * DIMS) * kOnes;
-    const uint32_t F = (D + bias) & kBit7;
-    return F | (F - (F >> 6));
-}
-
-// Metropolis test of site j of a word with d_j < dims: u_j < thr[k], k = 2(dims - d_j).
-// The threshold is selected from d_j on the integer ALU; the result ORs 0xFE into
-// byte j of the xor mask.
-template <int DIMS>
-__device__ __forceinline__ uint32_t uphill_accept(uint32_t D, uint32_t u, int j,
-                                                  const PassArgs& a) {
-    const uint32_t dj = D & (0x0Eu << (8 * j));  // 2*d_j in place
-    uint32_t t;
-    if (DIMS == 2) {
-        t = dj == 0u ? a.thr1 : a.thr0;  // d = 0: k = 4; d = 1: k = 2
-    } else {
-        t = dj == 0u ? a.thr2 : (dj == (0x02u << (8 * j)) ? a.thr1 : a.thr0);
-    }
-    return u < t ? (0xFEu << (8 * j)) : 0u;
-}
-
-template <int DIMS>
-__device__ __forceinline__ uint32_t disagreements(uint32_t s, uint32_t n0, uint32_t n1,
-                                                  uint32_t n2, uint32_t n3, uint32_t n4,
-                                                  uint32_t n5) {
-    uint32_t D = ((s ^ n0) & kBit1) + ((s ^ n1) & kBit1) + ((s ^ n2) & kBit1) +
-                 ((s ^ n3) & kBit1);
-    if (DIMS == 3) D += ((s ^ n4) & kBit1) + ((s ^ n5) & kBit1);
-    return D;
-}
-
-// Update the 16 sites of one 16-byte vector (four Philox groups g0..g0+3).
-// The four Philox calls are independent and computed together when any of
-// the 16 sites needs its draw.  Accumulates the number of -1 spins (m_neg)
-// and, in the white pass, sum_j 2*d_new_j (e_acc).
-template <int DIMS, bool MEASURE>
-__device__ __forceinline__ uint4 update_vec(const uint4& s, const uint4& x, const uint4& xs,
-                                            const uint4& ym, const uint4& yp, const uint4& zm,
-                                            const uint4& zp, uint32_t g0, const PassArgs& a,
-                                            int& e_acc, int& m_neg) {
-    const uint32_t sv[4] = {s.x, s.y, s.z, s.w};
-    uint32_t D[4], X[4];
-    D[0] = disagreements<DIMS>(s.x, x.x, xs.x, ym.x, yp.x, zm.x, zp.x);
-    D[1] = disagreements<DIMS>(s.y, x.y, xs.y, ym.y, yp.y, zm.y, zp.y);
-    D[2] = disagreements<DIMS>(s.z, x.z, xs.z, ym.z, yp.z, zm.z, zp.z);
-    D[3] = disagreements<DIMS>(s.w, x.w, xs.w, ym.w, yp.w, zm.w, zp.w);
-    bool need = false;
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        X[w] = downhill_mask<DIMS>(D[w]);
-        need |= X[w] != 0xFEFEFEFEu;
-    }
-    if (need) {
-        Philox4 u[4];
-#pragma unroll
-        for (int w = 0; w < 4; ++w)
-            u[w] = philox4x32_10(g0 + (uint32_t)w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            X[w] |= uphill_accept<DIMS>(D[w], u[w].w0, 0, a) |
-                    uphill_accept<DIMS>(D[w], u[w].w1, 1, a) |
-                    uphill_accept<DIMS>(D[w], u[w].w2, 2, a) |
-                    uphill_accept<DIMS>(D[w], u[w].w3, 3, a);
-        }
-    }
-    uint32_t out[4];
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        out[w] = sv[w] ^ X[w];  // 0x01 <-> 0xFF where flipped
-        if (MEASURE) {
-            m_neg += __popc(out[w] & kBit7);
-            if (a.c == 1) {
-                // 2*d_new = 2*(2 dims) - 2*d where flipped; X covers bits 1..7 there
-                constexpr uint32_t q2 = 4u * DIMS * kOnes;
-                const uint32_t Dn = (D[w] & ~X[w]) | ((q2 - D[w]) & X[w]);
-                e_acc = __dp4a((int)Dn, (int)kOnes, e_acc);
-            }
-        }
-    }
-    return make_uint4(out[0], out[1], out[2], out[3]);
-}
+constexpr uint32_t kBit7 = kByteBit7;
+constexpr uint32_t kOnes = kByteOnes;
 
 __device__ __forceinline__ int wrap_prev(int v, int n) { return v == 0 ? n - 1 : v - 1; }
 __device__ __forceinline__ int wrap_next(int v, int n) { return v == n - 1 ? 0 : v + 1; }
@@ -238,80 +151,16 @@ __global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 2) pass_int8_strip(PassAr
     }
 }
 
-// General kernel: any even L.  One item = one 32-bit word (four consecutive
-// half indices, one Philox group); each site finds its neighbours from its
-// coordinates, so half rows need not align with words.
+// General kernel: any even L.  One item = one 16-byte vector of the colour
+// array (16 consecutive half indices, four Philox groups); see int8_vec().
 template <int DIMS, bool MEASURE>
-__global__ void __launch_bounds__(256) pass_int8_any(PassArgs a, int64_t half_sites) {
-    const int64_t words = (half_sites + 3) >> 2;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int L = a.L, W = a.W;
-    int8_t* own = static_cast<int8_t*>(a.own);
-    const int8_t* other = static_cast<const int8_t*>(a.other);
-    int e_acc = 0, m_acc = 0;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += stride) {
-        int s_val[4], d_val[4];
-        bool valid[4], need_draw = false;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t h = 4 * w + j;
-            valid[j] = h < half_sites;
-            s_val[j] = 1;
-            d_val[j] = DIMS;
-            if (!valid[j]) continue;
-            const int64_t r = h / W;
-            const int xh = (int)(h - r * W);
-            int y, z;
-            if (DIMS == 2) {
-                y = (int)r;
-                z = 0;
-            } else {
-                z = (int)(r / L);
-                y = (int)(r - (int64_t)z * L);
-            }
-            const int p = (a.c + y + z) & 1;
-            const int x = 2 * xh + p;
-            const int xm = (x == 0 ? L - 1 : x - 1) >> 1, xp = (x == L - 1 ? 0 : x + 1) >> 1;
-            const int64_t plane = (int64_t)z * L;
-            const int64_t rym = plane + (y == 0 ? L - 1 : y - 1);
-            const int64_t ryp = plane + (y == L - 1 ? 0 : y + 1);
-            const int s = own[h];
-            int hsum = other[r * W + xm] + other[r * W + xp] + other[rym * W + xh] +
-                       other[ryp * W + xh];
-            if (DIMS == 3) {
-                const int64_t rzm = (int64_t)(z == 0 ? L - 1 : z - 1) * L + y;
-                const int64_t rzp = (int64_t)(z == L - 1 ? 0 : z + 1) * L + y;
-                hsum += other[rzm * W + xh] + other[rzp * W + xh];
-            }
-            s_val[j] = s;
-            d_val[j] = (2 * DIMS - s * hsum) >> 1;  // k = s*h = 2*(dims - d)
-            if (d_val[j] < DIMS) need_draw = true;
-        }
-        uint32_t u[4] = {0u, 0u, 0u, 0u};
-        if (need_draw) {
-            const Philox4 q = philox4x32_10((uint32_t)w, a.t, (uint32_t)a.c, kTagSweep, a.key0,
-                                            a.key1);
-            u[0] = q.w0;
-            u[1] = q.w1;
-            u[2] = q.w2;
-            u[3] = q.w3;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!valid[j]) continue;
-            const bool flip = (int)below_count<DIMS>(u[j], a) + d_val[j] >= DIMS;
-            const int sn = flip ? -s_val[j] : s_val[j];
-            if (flip) own[4 * w + j] = (int8_t)sn;
-            if (MEASURE) {
-                m_acc += sn;
-                if (a.c == 1) {
-                    const int dn = flip ? 2 * DIMS - d_val[j] : d_val[j];
-                    e_acc += 2 * dn - 2 * DIMS;
-                }
-            }
-        }
-    }
-    if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
+__global__ void __launch_bounds__(256) pass_int8_vecs(PassArgs a, WordGeom g) {
+    const uint32_t vecs = (g.half + 15u) >> 4;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    int e_acc = 0, m_neg = 0, n_sites = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < vecs; v += stride)
+        int8_vec<DIMS, MEASURE, 1>(a, g, v, e_acc, m_neg, n_sites);
+    if (MEASURE) block_reduce_add(e_acc, n_sites - 2 * m_neg, a.obs, a.c == 1);
 }
 
 // Canonical <-> layout conversion and initial states.  Item = one canonical
@@ -372,12 +221,17 @@ cudaError_t launch_pass_t(const PassArgs& a0, int64_t half_sites, bool vec, cons
         const int64_t blocks = (strips * a.nv + threads - 1) / threads;
         pass_int8_strip<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a);
     } else {
-        const int64_t words = (half_sites + 3) >> 2;
-        int64_t blocks = (words + threads - 1) / threads;
+        const int64_t vecs = (half_sites + 15) >> 4;
+        int64_t blocks = (vecs + threads - 1) / threads;
         const int64_t cap = (int64_t)dp.sm_count * 8;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        pass_int8_any<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a0, half_sites);
+        WordGeom g;
+        g.W = (uint32_t)a0.W;
+        g.L = (uint32_t)a0.L;
+        g.rows = (uint32_t)a0.rows;
+        g.half = (uint32_t)half_sites;
+        pass_int8_vecs<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a0, g);
     }
     return cudaGetLastError();
 }

@@ -33,6 +33,12 @@ class IsingError(RuntimeError):
         super().__init__(f"{what}: {msg} ({code})")
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int), ("cluster_size", ctypes.c_int),
+                ("big_sites", ctypes.c_int64), ("use_graph", ctypes.c_int),
+                ("huge_sites", ctypes.c_int64)]
+
+
 class IsingInfo(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int), ("L", ctypes.c_int), ("layout", ctypes.c_int),
                 ("reserved", ctypes.c_int), ("beta", ctypes.c_double),
@@ -75,6 +81,15 @@ def load_library():
             "ising_get_info": ([P, ctypes.POINTER(IsingInfo)], ctypes.c_int),
             "ising_synchronize": ([P], ctypes.c_int),
             "ising_destroy": ([P], None),
+            "ising_batch_create": ([ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int, i64p,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(BatchOpts), P],
+                                   ctypes.c_int),
+            "ising_batch_launch": ([P], ctypes.c_int),
+            "ising_batch_sync": ([P], ctypes.c_int),
+            "ising_batch_info": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                                 ctypes.c_int),
+            "ising_batch_destroy": ([P], None),
             "ising_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "ising_version": ([], ctypes.c_char_p),
         }
@@ -197,3 +212,62 @@ class Lattice:
     @property
     def handle(self) -> int:
         return int(self._h.value or 0)
+
+
+class Batch:
+    """Many lattices advanced by one persistent launch (``ising_batch_*``).
+
+    ``sweeps`` and ``measure_every`` are per lattice (sequences) or scalars.
+    While a launch is in flight the lattices must not be used directly; call
+    ``sync()`` first.
+    """
+
+    def __init__(self, lattices, sweeps, measure_every=1, block_threads=0, cluster_size=0,
+                 big_sites=0, use_graph=True, huge_sites=0, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.lattices = list(lattices)
+        n = len(self.lattices)
+        sw = np.asarray(np.broadcast_to(np.asarray(sweeps, dtype=np.int64), (n,)),
+                        dtype=np.int64).copy()
+        ev = np.asarray(np.broadcast_to(np.asarray(measure_every, dtype=np.int32), (n,)),
+                        dtype=np.int32).copy()
+        handles = (ctypes.c_void_p * n)(*[lat.handle for lat in self.lattices])
+        opts = BatchOpts(block_threads, cluster_size, big_sites, 0 if use_graph else -1,
+                         huge_sites)
+        raw = getattr(stream, "cuda_stream", stream)
+        self._h = ctypes.c_void_p()
+        _check(lib.ising_batch_create(ctypes.byref(self._h), handles, n,
+                                      sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      ctypes.byref(opts), ctypes.c_void_p(int(raw) if raw else 0)),
+               "ising_batch_create")
+
+    def launch(self) -> None:
+        _check(self._lib.ising_batch_launch(self._h), "ising_batch_launch")
+
+    def sync(self) -> None:
+        _check(self._lib.ising_batch_sync(self._h), "ising_batch_sync")
+
+    def info(self) -> dict:
+        g, nb, ns, nh = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.ising_batch_info(self._h, ctypes.byref(g), ctypes.byref(nb),
+                                          ctypes.byref(ns), ctypes.byref(nh)), "ising_batch_info")
+        return {"grid": g.value, "n_big": nb.value, "n_small": ns.value, "n_huge": nh.value}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.ising_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -64,7 +64,7 @@ def batched_mix(n: int = 2048, sweeps: int = 500, seed: int = 0) -> list:
     """Independent lattices: 70% 2D with L log-uniform in [16, 1024] and beta
     uniform in [0.2, 0.6]; 30% 3D with L log-uniform in [8, 128] and beta
     uniform in [0.15, 0.30]; L rounded to the nearest even integer; hot start;
-    seeds 1000 + j."""
+    seeds 1000 + j; E/M recorded every 10 sweeps."""
     rng = np.random.default_rng(seed)
     out = []
     for j in range(n):
@@ -76,7 +76,7 @@ def batched_mix(n: int = 2048, sweeps: int = 500, seed: int = 0) -> list:
             L = _even_round(math.exp(rng.uniform(math.log(8), math.log(128))))
             beta = float(rng.uniform(0.15, 0.30))
             dims = 3
-        out.append(LatticeSpec(dims, L, beta, 1000 + j, HOT, sweeps, sweeps, AUTO))
+        out.append(LatticeSpec(dims, L, beta, 1000 + j, HOT, sweeps, 10, AUTO))
     return out
 
 

@@ -1,0 +1,144 @@
+"""Scheduling logic of the serving loop on the CPU, with stand-ins for the
+lattice and batch objects (no GPU): admission by arrival time, slots and the
+memory budget without overtaking, processor-sharing quanta, the bookkeeping
+of records and latencies, and the workload generators."""
+import numpy as np
+import pytest
+
+from paper_cs_0312006_gb300 import serve, workloads
+
+
+class FakeLattice:
+    live = 0
+
+    def __init__(self, dims, L, beta, seed, layout=0, start=0, stream=None):
+        self.dims, self.L, self.t, self.n_rec = dims, L, 0, 0
+        self.E, self.M = [], []
+        FakeLattice.live += 1
+        self.closed = False
+
+    def observables(self):
+        E, M = np.array(self.E, dtype=np.int64), np.array(self.M, dtype=np.int64)
+        self.E, self.M = [], []
+        return E, M
+
+    def get_spins(self):
+        return np.full(self.L ** self.dims, 1, dtype=np.int8)
+
+    def close(self):
+        assert not self.closed
+        self.closed = True
+        FakeLattice.live -= 1
+
+
+class FakeBatch:
+    calls = []
+
+    def __init__(self, lats, sweeps, every, use_graph=True, stream=None, **kw):
+        self.lats, self.sweeps, self.every = lats, list(sweeps), list(every)
+        FakeBatch.calls.append(list(sweeps))
+
+    def launch(self):
+        for lat, n, ev in zip(self.lats, self.sweeps, self.every):
+            for _ in range(n):
+                lat.t += 1
+                if lat.t % ev == 0:  # record after sweep t-1 iff (t-1)+1 divisible
+                    lat.E.append(lat.t)
+                    lat.M.append(-lat.t)
+
+    def sync(self):
+        pass
+
+    def close(self):
+        pass
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 0.001  # each query advances the clock by 1 ms
+        return self.t
+
+
+def jobs_of(specs, gap=0.0):
+    return [workloads.Job(i, i * gap, sp) for i, sp in enumerate(specs)]
+
+
+def spec(L, sweeps, every=10, dims=2):
+    return workloads.LatticeSpec(dims, L, 0.44, 7, 0, sweeps, every, 0)
+
+
+def make_server(**kw):
+    FakeBatch.calls.clear()
+    return serve.Server(lattice_factory=FakeLattice, batch_factory=FakeBatch, clock=Clock(), **kw)
+
+
+def test_all_jobs_complete_with_their_records():
+    srv = make_server(round_s=1e-4)
+    specs = [spec(32, 100), spec(64, 250, 5), spec(16, 30, 3)]
+    summ = srv.run(jobs_of(specs))
+    assert summ["jobs"] == 3 and FakeLattice.live == 0
+    for j, sp in enumerate(specs):
+        r = srv.results[j]
+        want = [t for t in range(1, sp.sweeps + 1) if t % sp.measure_every == 0]
+        assert r.E.tolist() == want and r.M.tolist() == [-t for t in want]
+        assert r.sweeps == sp.sweeps and r.latency_s > 0
+    assert summ["site_updates"] == sum(sp.sites * sp.sweeps for sp in specs)
+
+
+def test_memory_budget_limits_residency_and_keeps_order():
+    one = serve.job_bytes(spec(64, 100))
+    srv = make_server(hbm_budget_bytes=2 * one + 10, round_s=1e-5)
+    specs = [spec(64, 100) for _ in range(5)]
+    srv.run(jobs_of(specs))
+    assert srv.peak_bytes <= 2 * one + 10
+    assert all(len(c) <= 2 for c in FakeBatch.calls)
+    admits = [srv.results[j].admit_s for j in range(5)]
+    assert admits == sorted(admits)  # first come, first admitted
+
+
+def test_slots_limit_and_job_too_big():
+    srv = make_server(max_resident=1, round_s=1.0)
+    srv.run(jobs_of([spec(32, 10), spec(32, 10)]))
+    assert all(len(c) == 1 for c in FakeBatch.calls)
+    small = make_server(hbm_budget_bytes=1000)
+    with pytest.raises(ValueError):
+        small.submit(workloads.Job(0, 0.0, spec(256, 10)))
+
+
+def test_time_sharing_quanta():
+    srv = make_server(round_s=0.01)
+    big = serve.Server.RATE_CLUSTER
+    srv.big_sites = 64 * 64  # 64x64 runs on a cluster, 16x16 on one CTA
+    srv.run(jobs_of([spec(64, 100000), spec(16, 100000), spec(2048, 100000)]))
+    first = FakeBatch.calls[0]
+    assert first[0] == int(0.01 * big // (64 * 64)) // 10 * 10
+    assert first[1] == int(0.01 * serve.Server.RATE_CTA // 256) // 10 * 10
+    huge = int(0.01 * serve.Server.RATE_FULL // (2048 * 2048))
+    assert first[2] == (huge - huge % 10 if huge > 10 else huge)
+
+
+def test_arrivals_respected():
+    srv = make_server(round_s=1.0)
+    jobs = [workloads.Job(0, 0.0, spec(16, 10)), workloads.Job(1, 0.5, spec(16, 10))]
+    srv.run(jobs)
+    assert srv.results[1].admit_s >= 0.5
+
+
+def test_workload_generators():
+    mix = workloads.batched_mix(2048)
+    assert len(mix) == 2048
+    d2 = [s for s in mix if s.dims == 2]
+    assert 0.65 < len(d2) / 2048 < 0.75
+    assert all(s.L % 2 == 0 for s in mix)
+    assert min(s.L for s in d2) >= 16 and max(s.L for s in d2) <= 1024
+    d3 = [s for s in mix if s.dims == 3]
+    assert min(s.L for s in d3) >= 8 and max(s.L for s in d3) <= 128
+    jobs = workloads.poisson_jobs(2000)
+    gaps = np.diff([j.arrival_s for j in jobs])
+    assert abs(gaps.mean() - 1 / 200) < 0.15 / 200
+    assert all(100 <= j.spec.sweeps <= 20000 for j in jobs)
+    scan = workloads.beta_scan_2d()
+    assert [round(s.beta, 2) for s in scan] == [round(0.30 + 0.02 * j, 2) for j in range(16)]
