@@ -41,8 +41,9 @@ typedef struct ising_lattice ising_lattice; /* opaque, owned by the library */
 enum {
     ISING_INT8 = 0,    /* one int8 per site, one array per colour (the two-lattice
                           checkerboard of Sec. 5), row-major half rows */
-    ISING_BITPACK = 1, /* 32 same-colour sites per uint32 word; L % 64 == 0 */
-    ISING_AUTO = 2     /* the engine picks; never changes results */
+    ISING_BITPACK = 1, /* 32 same-colour sites per uint32 word, each half row
+                          padded to whole words */
+    ISING_AUTO = 2     /* the engine picks (bit-packed); never changes results */
 };
 
 /* Initial states (Sec. 2.2: spins up with probability p). */
@@ -81,8 +82,7 @@ typedef struct ising_info_t {
  *   out    receives the handle (set to NULL on failure).
  *   dims   2 or 3.
  *   L      even, >= 2 (odd L has no valid checkerboard on a torus: the wrap
- *          bond would join two sites of one colour); ISING_BITPACK needs
- *          L % 64 == 0; L^dims <= 2^34.
+ *          bond would join two sites of one colour); L^dims <= 2^32.
  *   beta   > 0 (may be +inf for a zero-temperature quench).  The thresholds
  *          floor(exp(-2 beta k) 2^32), k = 2..2*dims, are built on the host;
  *          a beta whose exact value lies within 2^-24 of an integer boundary

@@ -18,13 +18,13 @@ from .workloads import AUTO, INT8, LatticeSpec
 
 def make_lattices(specs, layout_policy: str = "auto", stream=None):
     """Create one handle per spec (hot start).  ``layout_policy``: "auto"
-    (bit-packed where L % 64 == 0), "int8" or "bitpack"."""
+    (the engine's choice, bit-packed), "int8" or "bitpack"."""
     lats = []
     for sp in specs:
         if layout_policy == "int8":
             lay = INT8
         elif layout_policy == "bitpack":
-            lay = engine.BITPACK if sp.L % 64 == 0 else INT8
+            lay = engine.BITPACK
         else:
             lay = AUTO
         lats.append(engine.Lattice(sp.dims, sp.L, sp.beta, sp.seed, layout=lay, start=sp.start,

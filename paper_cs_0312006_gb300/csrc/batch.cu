@@ -89,7 +89,7 @@ __device__ __forceinline__ void job_pass(const BatchJob& j, int c, uint32_t t, u
             int8_vec<DIMS, MEASURE, NC>(a, g, v, e_acc, m_neg, n_sites);
         if (MEASURE) m_acc += n_sites - 2 * m_neg;
     } else {
-        const uint32_t items = j.rows * ((uint32_t)j.W >> 5);
+        const uint32_t items = j.rows * (((uint32_t)j.W + 31u) >> 5);
         for (uint32_t it = rank; it < items; it += nthr)
             packed_word<DIMS, MEASURE, NC>(a, it, e_acc, m_acc);
     }

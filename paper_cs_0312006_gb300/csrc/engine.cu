@@ -186,11 +186,9 @@ int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t see
         return ISING_EINVAL;
     const uint64_t sites = dims == 2 ? (uint64_t)L * L : (uint64_t)L * L * L;
     if ((uint64_t)L > (1u << 20) || sites > kMaxSites) return ISING_EINVAL;
-    if (layout == ISING_BITPACK && L % 64 != 0) return ISING_EINVAL;
-    // ISING_AUTO: the bit-packed layout whenever its shape rule allows (results
-    // are identical in both layouts)
-    const int use_layout = layout == ISING_AUTO ? (L % 64 == 0 ? ISING_BITPACK : ISING_INT8)
-                                                : layout;
+    // ISING_AUTO: the bit-packed layout, the faster of the two on this GPU
+    // (results are identical in both layouts)
+    const int use_layout = layout == ISING_AUTO ? ISING_BITPACK : layout;
     uint32_t thr[3];
     int rc = build_thresholds(dims, beta, thr);
     if (rc != ISING_OK) return rc;
@@ -213,7 +211,7 @@ int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t see
     h->dp = dp;
     // 16 spare bytes: the word kernels may read one word past the last one
     if (use_layout == ISING_BITPACK)
-        h->col_bytes = (size_t)h->rows * (size_t)(L / 64) * sizeof(uint32_t) + 16;
+        h->col_bytes = (size_t)h->rows * (size_t)((L / 2 + 31) / 32) * sizeof(uint32_t) + 16;
     else
         h->col_bytes = (((size_t)h->half_sites + 15) & ~(size_t)15) + 16;
     for (int c = 0; c < 2; ++c) {

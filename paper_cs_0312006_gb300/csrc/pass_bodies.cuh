@@ -340,8 +340,8 @@ __device__ __forceinline__ void int8_vec(const PassArgs& a, const WordGeom& g, u
 }
 
 // ----------------------------------------------------------------------------
-// Bit-packed body (L % 64 == 0): one 32-site word per call; see sweep_bitpack.cu
-// for the layout.
+// Bit-packed body: one 32-site word per call; see sweep_bitpack.cu for the
+// layout.
 // ----------------------------------------------------------------------------
 struct Counts {
     uint32_t always, eq0, eq1, eq2;
@@ -385,52 +385,19 @@ __device__ __forceinline__ uint32_t group_accept(const Counts& k, const Philox4&
     return acc;
 }
 
-// Update word (r, q) of the packed colour array.  `prev`/`next` are the other
-// colour's words q-1 / q+1 of the same row (with wrap) when the caller has
-// them; pass have_nb = false to load them here.
-template <int DIMS, bool MEASURE, int NC>
-__device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, int& e_acc,
-                                            int& m_acc) {
-    const uint32_t nq = (uint32_t)a.W >> 5;
-    const uint32_t L = (uint32_t)a.L;
-    uint32_t* own = static_cast<uint32_t*>(a.own);
-    const uint32_t* other = static_cast<const uint32_t*>(a.other);
-    const uint32_t r = item / nq, q = item - r * nq;
-    uint32_t y = r, z = 0;
-    if (DIMS == 3) {
-        z = r / L;
-        y = r - z * L;
-    }
-    const uint32_t plane = z * L;
-    const uint32_t row = r * nq;
-    const uint32_t o = load_other<NC>(other + row + q);
-    const uint32_t oym = load_other<NC>(other + (plane + (y == 0u ? L - 1u : y - 1u)) * nq + q);
-    const uint32_t oyp = load_other<NC>(other + (plane + (y + 1u == L ? 0u : y + 1u)) * nq + q);
-    uint32_t ozm = 0u, ozp = 0u;
-    if (DIMS == 3) {
-        ozm = load_other<NC>(other + ((z == 0u ? L - 1u : z - 1u) * L + y) * nq + q);
-        ozp = load_other<NC>(other + ((z + 1u == L ? 0u : z + 1u) * L + y) * nq + q);
-    }
-    const uint32_t s = own[row + q];
-    const int p = (a.c + (int)y + (int)z) & 1;
-    uint32_t sh;
-    if (p == 0) {
-        const uint32_t prev = load_other<NC>(other + row + (q == 0u ? nq - 1u : q - 1u));
-        sh = __funnelshift_l(prev, o, 1);  // bit b <- neighbour h' - 1
-    } else {
-        const uint32_t next = load_other<NC>(other + row + (q + 1u == nq ? 0u : q + 1u));
-        sh = __funnelshift_r(o, next, 1);  // bit b <- neighbour h' + 1
-    }
-    Counts k;
-    if (DIMS == 2) {
-        k = count2(s ^ o, s ^ sh, s ^ oym, s ^ oyp);
-    } else {
-        k = count3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
-    }
-    uint32_t flip = k.always;
-    const uint32_t need = ~k.always;
-    if (need) {
-        const uint32_t g0 = (row + q) * 8u;  // (r*W + 32q) / 4
+// Accept mask of the sites with dE > 0 among the `need` bits of a packed word
+// whose 32 bits are the half indices hb = hbase + b (b = 0..31).  Bit b's draw
+// is word (hb & 3) of Philox group hb >> 2.  When hbase is a multiple of 4 the
+// eight groups are the word's nibbles and are computed four at a time; when a
+// row starts inside a group (W not a multiple of 4) the word spans nine
+// groups, taken one at a time (measured faster here than interleaving them,
+// which raises register pressure in the batched kernel).
+template <int DIMS>
+__device__ __forceinline__ uint32_t packed_accept(const Counts& k, uint32_t need, uint32_t hbase,
+                                                  const PassArgs& a) {
+    uint32_t acc = 0u;
+    const uint32_t m = hbase & 3u, g0 = hbase >> 2;
+    if (m == 0u) {
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             Philox4 u[4];
@@ -444,18 +411,104 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
                     u[i] = Philox4{0u, 0u, 0u, 0u};
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) flip |= group_accept<DIMS>(k, u[i], 4 * half + i, a);
+            for (int i = 0; i < 4; ++i) acc |= group_accept<DIMS>(k, u[i], 4 * half + i, a);
+        }
+        return acc;
+    }
+#pragma unroll 1
+    for (int g = 0; g < 9; ++g) {
+        const int lo = 4 * g - (int)m;  // bit of the group's word 0 (may be < 0)
+        const uint32_t gmask = lo >= 0 ? (0xFu << lo) : (0xFu >> (-lo));
+        if (!(need & gmask)) continue;
+        const Philox4 u = philox4x32_10(g0 + (uint32_t)g, a.t, (uint32_t)a.c, kTagSweep, a.key0,
+                                        a.key1);
+        const uint32_t w[4] = {u.w0, u.w1, u.w2, u.w3};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int b = lo + j;
+            if (b < 0 || b > 31) continue;
+            uint32_t t;
+            if (DIMS == 2) {
+                t = (k.eq0 >> b) & 1u ? a.thr1 : a.thr0;
+            } else {
+                t = (k.eq0 >> b) & 1u ? a.thr2 : ((k.eq1 >> b) & 1u ? a.thr1 : a.thr0);
+            }
+            acc |= (w[j] < t ? 1u : 0u) << b;
         }
     }
-    const uint32_t snew = s ^ flip;
+    return acc;
+}
+
+// Update word (r, q) of the packed colour array.  A half row of W sites takes
+// nq = ceil(W / 32) words; bit b of word q is half column xh = 32q + b (valid
+// when xh < W; the other bits of a row's last word stay 0 and never flip).
+// The x-neighbour wrap at the row ends comes from the row's last valid bit
+// (p = 0, first word) or first bit (p = 1, last word).
+template <int DIMS, bool MEASURE, int NC>
+__device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, int& e_acc,
+                                            int& m_acc) {
+    const uint32_t W = (uint32_t)a.W;
+    const uint32_t nq = (W + 31u) >> 5;
+    const uint32_t L = (uint32_t)a.L;
+    uint32_t* own = static_cast<uint32_t*>(a.own);
+    const uint32_t* other = static_cast<const uint32_t*>(a.other);
+    const uint32_t r = item / nq, q = item - r * nq;
+    uint32_t y = r, z = 0;
+    if (DIMS == 3) {
+        z = r / L;
+        y = r - z * L;
+    }
+    const uint32_t nb = W - 32u * q < 32u ? W - 32u * q : 32u;  // valid bits
+    const uint32_t valid = nb == 32u ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+    const uint32_t plane = z * L;
+    const uint32_t row = r * nq;
+    const uint32_t o = load_other<NC>(other + row + q);
+    const uint32_t oym = load_other<NC>(other + (plane + (y == 0u ? L - 1u : y - 1u)) * nq + q);
+    const uint32_t oyp = load_other<NC>(other + (plane + (y + 1u == L ? 0u : y + 1u)) * nq + q);
+    uint32_t ozm = 0u, ozp = 0u;
+    if (DIMS == 3) {
+        ozm = load_other<NC>(other + ((z == 0u ? L - 1u : z - 1u) * L + y) * nq + q);
+        ozp = load_other<NC>(other + ((z + 1u == L ? 0u : z + 1u) * L + y) * nq + q);
+    }
+    const uint32_t s = own[row + q];
+    const int p = (a.c + (int)y + (int)z) & 1;
+    uint32_t sh;
+    if (p == 0) {  // bit b <- neighbour xh - 1
+        uint32_t prev;
+        if (q == 0u) {  // wrap: the row's last site, moved to bit 31
+            const uint32_t last = load_other<NC>(other + row + nq - 1u);
+            prev = last << (31u - ((W - 1u) & 31u));
+        } else {
+            prev = load_other<NC>(other + row + q - 1u);
+        }
+        sh = __funnelshift_l(prev, o, 1);
+    } else {       // bit b <- neighbour xh + 1
+        if (q + 1u == nq) {  // wrap: bit nb - 1 takes the row's first site
+            const uint32_t first = q == 0u ? o : load_other<NC>(other + row);
+            const uint32_t top = 1u << (nb - 1u);
+            sh = ((o >> 1) & ~top) | ((first & 1u) ? top : 0u);
+        } else {
+            sh = __funnelshift_r(o, load_other<NC>(other + row + q + 1u), 1);
+        }
+    }
+    Counts k;
+    if (DIMS == 2) {
+        k = count2(s ^ o, s ^ sh, s ^ oym, s ^ oyp);
+    } else {
+        k = count3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
+    }
+    uint32_t flip = k.always;
+    const uint32_t need = ~k.always & valid;
+    if (need) flip |= packed_accept<DIMS>(k, need, r * W + 32u * q, a);
+    const uint32_t snew = s ^ (flip & valid);
     own[row + q] = snew;
     if (MEASURE) {
-        m_acc += 2 * __popc(snew) - 32;
+        m_acc += 2 * __popc(snew & valid) - (int)nb;
         if (a.c == 1) {
-            int dsum = __popc(snew ^ o) + __popc(snew ^ sh) + __popc(snew ^ oym) +
-                       __popc(snew ^ oyp);
-            if (DIMS == 3) dsum += __popc(snew ^ ozm) + __popc(snew ^ ozp);
-            e_acc += 2 * dsum - 32 * 2 * DIMS;
+            int dsum = __popc((snew ^ o) & valid) + __popc((snew ^ sh) & valid) +
+                       __popc((snew ^ oym) & valid) + __popc((snew ^ oyp) & valid);
+            if (DIMS == 3) dsum += __popc((snew ^ ozm) & valid) + __popc((snew ^ ozp) & valid);
+            e_acc += 2 * dsum - (int)nb * 2 * DIMS;
         }
     }
 }

@@ -1,13 +1,14 @@
 // sweep_bitpack.cu -- colour pass of the checkerboard Metropolis sweep on the
 // bit-packed ("multispin") layout, with the E and M reductions fused in.
 //
-// Layout: colour c's sites in half index order h = i >> 1 (canonical site
-// i = x + L*y (+ L*L*z)), 32 sites per uint32 word, site h at bit (h mod 32) of
-// word h / 32; bit 1 means spin +1.  With L % 64 == 0 every half row of W = L/2
-// sites is a whole number nq = W/32 of words, so word q of half row r holds the
-// sites h = r*W + 32q + b, b = 0..31, and row r's x-neighbour word of the other
-// colour lines up bit for bit (h' = h), with the second x-neighbour one bit to
-// the right (p = 0: h' - 1) or left (p = 1: h' + 1), p = (c + y + z) & 1.
+// Layout: each half row r of colour c (its W = L/2 sites, half column
+// xh = 0..W-1, half index h = r*W + xh) takes nq = ceil(W/32) uint32 words;
+// site xh is bit (xh mod 32) of word r*nq + xh/32, bit 1 meaning spin +1.  The
+// bits past W in a row's last word are padding: zero, never read as spins,
+// never flipped.  Row r's word q of the other colour lines up with the site
+// word bit for bit (same half column), the second x-neighbour is one bit to
+// the right (p = 0: xh - 1) or left (p = 1: xh + 1), p = (c + y + z) & 1, and
+// the y- and z-neighbour words are the same word of the neighbouring rows.
 //
 // The Metropolis rule (Sec. 2.2) is evaluated for 32 sites at once: the
 // per-site count d of disagreeing neighbours is formed by bit-sliced adders
@@ -15,8 +16,7 @@
 // the mask of sites with dE <= 0 (d >= dims; they flip) and, for the others,
 // the mask of sites with each d < dims, selecting the threshold
 // floor(exp(-2 beta k) 2^32), k = 2(dims - d).  Draws are identical to the
-// int8 layout: site h uses word h & 3 of Philox(seed; h >> 2, t, c, 0), so the
-// eight Philox groups of a word are g0 .. g0 + 7 with g0 = (r*W + 32q) / 4.
+// int8 layout: site h uses word h & 3 of Philox(seed; h >> 2, t, c, 0).
 #include <cstdint>
 
 #include "engine_internal.h"
@@ -30,7 +30,7 @@ namespace {
 // One item = one 32-site word of the colour array (see packed_word()).
 template <int DIMS, bool MEASURE>
 __global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a) {
-    const uint32_t items = (uint32_t)a.rows * ((uint32_t)a.W >> 5);
+    const uint32_t items = (uint32_t)a.rows * (((uint32_t)a.W + 31u) >> 5);
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_acc = 0;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride)
@@ -39,10 +39,11 @@ __global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a) {
 }
 
 // Initial state written straight into the packed layout: one thread per word
-// of one colour; bit b of word (r, q) is canonical site i = L*r + 64q + 2b + p.
+// of one colour; bit b of word (r, q) is half column xh = 32q + b, i.e. the
+// canonical site i = L*r + 2*xh + p.
 __global__ void init_packed(uint32_t* col0, uint32_t* col1, int L, int dims, int64_t rows,
                             int start, uint32_t key0, uint32_t key1) {
-    const int nq = L / 64;
+    const int W = L / 2, nq = (W + 31) / 32;
     const int64_t words = rows * nq;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t w2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w2 < 2 * words;
@@ -51,21 +52,19 @@ __global__ void init_packed(uint32_t* col0, uint32_t* col1, int L, int dims, int
         const int64_t w = w2 - (int64_t)c * words;
         const int64_t r = w / nq;
         const int q = (int)(w - r * nq);
-        uint32_t bits;
+        const int nb = W - 32 * q < 32 ? W - 32 * q : 32;
+        uint32_t bits = 0u;
         if (start == 0) {
             const int64_t y = r % L, z = dims == 3 ? r / L : 0;
             const int p = (int)((c + y + z) & 1);
-            bits = 0u;
-            for (int m = 0; m < 16; ++m) {  // sites b = 2m, 2m+1 share Philox group i >> 2
-                const int64_t i0 = (int64_t)L * r + 64 * q + 4 * m;  // canonical group base
-                const Philox4 u = philox4x32_10((uint32_t)(i0 >> 2), 0u, 0u, kTagInit, key0, key1);
+            for (int b = 0; b < nb; ++b) {
+                const int64_t i = (int64_t)L * r + 2 * (32 * q + b) + p;
+                const Philox4 u = philox4x32_10((uint32_t)(i >> 2), 0u, 0u, kTagInit, key0, key1);
                 const uint32_t wd[4] = {u.w0, u.w1, u.w2, u.w3};
-                // canonical word (2b + p) & 3 = 2*(b & 1) + p
-                if (wd[p] < 0x80000000u) bits |= 1u << (2 * m);
-                if (wd[2 + p] < 0x80000000u) bits |= 1u << (2 * m + 1);
+                if (wd[i & 3] < 0x80000000u) bits |= 1u << b;
             }
-        } else {
-            bits = start == 1 ? 0xFFFFFFFFu : 0u;
+        } else if (start == 1) {
+            bits = nb == 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u);
         }
         (c == 0 ? col0 : col1)[w] = bits;
     }
@@ -73,20 +72,21 @@ __global__ void init_packed(uint32_t* col0, uint32_t* col1, int L, int dims, int
 
 __global__ void export_packed(const uint32_t* col0, const uint32_t* col1, int8_t* out, int L,
                               int dims, int64_t sites) {
+    const int nq = (L / 2 + 31) / 32;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sites; i += stride) {
-        const int64_t x = i % L, rest = i / L;
-        const int64_t y = rest % L, z = dims == 3 ? rest / L : 0;
-        const int64_t h = i >> 1;
-        const uint32_t word = (((x + y + z) & 1) == 0 ? col0 : col1)[h >> 5];
-        out[i] = ((word >> (h & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
+        const int64_t x = i % L, r = i / L;
+        const int64_t y = r % L, z = dims == 3 ? r / L : 0;
+        const int64_t xh = x >> 1;
+        const uint32_t word = (((x + y + z) & 1) == 0 ? col0 : col1)[r * nq + (xh >> 5)];
+        out[i] = ((word >> (xh & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
     }
 }
 
-// One thread per packed word: gather its 32 canonical bytes.
+// One thread per packed word: gather its canonical bytes.
 __global__ void import_packed(uint32_t* col0, uint32_t* col1, const int8_t* in, int L, int dims,
                               int64_t rows) {
-    const int nq = L / 64;
+    const int W = L / 2, nq = (W + 31) / 32;
     const int64_t words = rows * nq;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t w2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w2 < 2 * words;
@@ -97,9 +97,10 @@ __global__ void import_packed(uint32_t* col0, uint32_t* col1, const int8_t* in, 
         const int q = (int)(w - r * nq);
         const int64_t y = r % L, z = dims == 3 ? r / L : 0;
         const int p = (int)((c + y + z) & 1);
+        const int nb = W - 32 * q < 32 ? W - 32 * q : 32;
         uint32_t bits = 0u;
-        for (int b = 0; b < 32; ++b)
-            if (in[(int64_t)L * r + 64 * q + 2 * b + p] > 0) bits |= 1u << b;
+        for (int b = 0; b < nb; ++b)
+            if (in[(int64_t)L * r + 2 * (32 * q + b) + p] > 0) bits |= 1u << b;
         (c == 0 ? col0 : col1)[w] = bits;
     }
 }
@@ -113,7 +114,7 @@ unsigned grid_for(int64_t n, const DeviceProps& dp) {
 
 template <int DIMS, bool MEASURE>
 cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream_t st) {
-    const int64_t items = a.rows * (a.W >> 5);
+    const int64_t items = a.rows * ((a.W + 31) >> 5);
     int64_t blocks = (items + 255) / 256;
     const int64_t cap = (int64_t)dp.sm_count * dp.blocks_per_sm_packed[DIMS - 2][MEASURE];
     if (blocks > cap) blocks = cap;
@@ -147,8 +148,8 @@ cudaError_t packed_pass(const PassArgs& a, int dims, bool measure, const DeviceP
 
 cudaError_t packed_init(uint32_t* col0, uint32_t* col1, int L, int dims, int64_t rows, int start,
                         uint32_t key0, uint32_t key1, const DeviceProps& dp, cudaStream_t st) {
-    init_packed<<<grid_for(2 * rows * (L / 64), dp), 256, 0, st>>>(col0, col1, L, dims, rows,
-                                                                    start, key0, key1);
+    init_packed<<<grid_for(2 * rows * ((L / 2 + 31) / 32), dp), 256, 0, st>>>(
+        col0, col1, L, dims, rows, start, key0, key1);
     return cudaGetLastError();
 }
 
@@ -160,8 +161,8 @@ cudaError_t packed_export(const uint32_t* col0, const uint32_t* col1, int8_t* ou
 
 cudaError_t packed_import(uint32_t* col0, uint32_t* col1, const int8_t* in, int L, int dims,
                           int64_t rows, const DeviceProps& dp, cudaStream_t st) {
-    import_packed<<<grid_for(2 * rows * (L / 64), dp), 256, 0, st>>>(col0, col1, in, L, dims,
-                                                                      rows);
+    import_packed<<<grid_for(2 * rows * ((L / 2 + 31) / 32), dp), 256, 0, st>>>(col0, col1, in,
+                                                                                 L, dims, rows);
     return cudaGetLastError();
 }
 

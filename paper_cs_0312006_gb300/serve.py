@@ -61,8 +61,9 @@ class _Resident:
 
 def job_bytes(spec) -> int:
     """Device bytes a job holds: two colour arrays and its E/M records."""
-    if spec.layout == engine.BITPACK or (spec.layout == engine.AUTO and spec.L % 64 == 0):
-        per_colour = spec.sites // 16 + 16  # 1 bit per site, half the sites per colour
+    if spec.layout in (engine.BITPACK, engine.AUTO):
+        rows = spec.L ** (spec.dims - 1)
+        per_colour = rows * ((spec.L // 2 + 31) // 32) * 4 + 16  # padded rows of words
     else:
         per_colour = ((spec.sites // 2 + 15) // 16) * 16 + 16
     records = 16 * (spec.sweeps // spec.measure_every + 64)

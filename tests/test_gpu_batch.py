@@ -32,7 +32,7 @@ def mix_specs(seed=0, n=48):
         dims = 2 if j % 3 else 3
         L = int(rng.choice(sizes2 if dims == 2 else sizes3))
         beta = float(rng.uniform(0.2, 0.6) if dims == 2 else rng.uniform(0.15, 0.3))
-        layout = BITPACK if (L % 64 == 0 and j % 2 == 0) else INT8
+        layout = BITPACK if j % 2 == 0 else INT8
         sweeps = int(rng.integers(3, 25))
         every = int(rng.choice([1, 3, 10]))
         specs.append((dims, L, beta, 1000 + j, layout, sweeps, every))
@@ -80,7 +80,8 @@ def test_batch_equals_alone(eng):
 
 def test_batch_against_oracle(eng):
     specs = [(2, 34, 0.44, 7, INT8, 9, 1), (3, 6, 0.22, 8, INT8, 9, 3),
-             (2, 128, 0.5, 9, BITPACK, 9, 1), (2, 200, 0.3, 10, INT8, 9, 2)]
+             (2, 128, 0.5, 9, BITPACK, 9, 1), (2, 200, 0.3, 10, INT8, 9, 2),
+             (2, 70, 0.4, 11, BITPACK, 9, 1), (3, 10, 0.2, 12, BITPACK, 9, 2)]
     got = run_batch(eng, specs, launches=1, cluster_size=2, big_sites=2000)
     for (d, L, b, sd, _, sw, ev), g in zip(specs, got):
         o = oracle.run(d, L, b, sd, sw, measure_every=ev)
