@@ -202,6 +202,43 @@ int ising_batch_info(const ising_batch *b, int *grid, int *n_big, int *n_small, 
 /* Free the batch (not the lattices).  NULL is accepted. */
 void ising_batch_destroy(ising_batch *b);
 
+/*
+ * ising_batch_run_static -- the batched launch for callers that cannot
+ * allocate device memory while they run.  (An engine facility; the paper has
+ * no counterpart.)  Some callers must not allocate once running: a real-time
+ * or latency-bound loop where cudaMalloc would stall the device, code that
+ * owns a fixed memory pool, or a host that has reserved all device memory for
+ * its lattices up front.  This call advances lattice i by sweeps[i] sweeps in
+ * one persistent launch on `stream`, like ising_batch_create + launch, but
+ * allocates nothing: its work queue (job table, queue order, counters) lives
+ * in one file-scope device array of fixed size, at most 2048 lattices per
+ * call (more gives ISING_ERANGE before any work is issued); every GPU that
+ * loads the library holds that array, about 168 KiB, until the process exits.
+ *
+ *   lats, n        n distinct lattices of the current device (1 <= n <= 2048).
+ *   sweeps         n sweep counts (>= 0).
+ *   measure_every  NULL (every sweep) or n intervals (>= 1): E/M is recorded
+ *                  after sweep u iff (u + 1) % measure_every[i] == 0.
+ *   records        caller-owned DEVICE buffer of (E, M) int64 pairs.  Lattice
+ *                  i's records follow those of lattices 0..i-1, in sweep
+ *                  order.  The call zeroes and fills only the pairs it
+ *                  writes; records_cap is the number of pairs available and
+ *                  must cover them all (else ISING_ERANGE, nothing issued).
+ *                  The handles' own record buffers are not touched.
+ *   opts           block_threads, cluster_size and big_sites as for
+ *                  ising_batch_create (NULL: defaults); every lattice runs in
+ *                  the persistent kernel (huge_sites and use_graph are ignored).
+ * The spins and sweep counters of the handles advance as with ising_sweep.
+ * The first call on a device looks up the array's device address and the
+ * resident grid size; make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents, so
+ * calls whose work overlaps on the GPU (e.g. issued on two streams without
+ * ordering) race: order them on one stream or synchronise between them.
+ */
+int ising_batch_run_static(ising_lattice *const *lats, int n, const int64_t *sweeps,
+                           const int *measure_every, int64_t *records, int64_t records_cap,
+                           const ising_batch_opts *opts, void *stream);
+
 /* Static description of a status code. */
 const char *ising_strerror(int code);
 

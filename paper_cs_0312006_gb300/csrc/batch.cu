@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -437,6 +438,189 @@ int ising_batch_info(const ising_batch* b, int* grid, int* n_big, int* n_small, 
     if (n_big) *n_big = b->n_big;
     if (n_small) *n_small = b->n_small;
     if (n_huge) *n_huge = (int)b->huge.size();
+    return ISING_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// The batched launch without allocation.  For callers that must not allocate
+// device memory once they are running (a real-time loop, a process that owns
+// a fixed memory pool, code that runs where cudaMalloc would synchronise or
+// fail), the job table, the queue order and the queue counters live in one
+// file-scope device array of fixed size instead of in memory the library
+// allocates; the caller's lattices and record buffer are the only other
+// memory touched.
+// ----------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticMaxJobs = 2048;
+constexpr size_t kStaticTableBytes = sizeof(BatchJob) * kStaticMaxJobs;
+constexpr size_t kStaticOrderBytes = sizeof(int) * kStaticMaxJobs;
+
+// job table | order | queue counters; every GPU that loads the library holds
+// it (about 168 KiB) until the process exits
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticTableBytes +
+                                                                  kStaticOrderBytes + 256];
+
+struct StaticSetup {
+    bool ready = false;
+    unsigned char* scratch = nullptr;  // device address of g_static_scratch
+    int clusters[3][9] = {};           // resident clusters per [block size][cluster size]
+};
+std::mutex g_static_mu;
+StaticSetup g_static[64];
+
+int block_index(int threads) { return threads == 128 ? 0 : (threads == 256 ? 1 : 2); }
+
+// Once per device, with that device current: the device address of the
+// scratch array (its host-side name is only a stand-in for it) and, once per
+// launch shape, the resident grid size.  Neither call allocates.
+int static_setup(int threads, int cluster, unsigned char** scratch, int* grid) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= 64) return ISING_ECUDA;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    StaticSetup& st = g_static[dev];
+    if (!st.ready) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e);
+        st.scratch = static_cast<unsigned char*>(ptr);
+        st.ready = true;
+    }
+    int& c = st.clusters[block_index(threads)][cluster];
+    if (c < 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.gridDim = dim3((unsigned)(cluster * 1024));
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        e = cudaOccupancyMaxActiveClusters(&nc, batch_kernel, &cfg);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (nc < 1) return ISING_ECUDA;
+        c = nc;
+    }
+    *scratch = st.scratch;
+    *grid = c * cluster;
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ising_batch_run_static(ising_lattice* const* lats, int n, const int64_t* sweeps,
+                           const int* measure_every, int64_t* records, int64_t records_cap,
+                           const ising_batch_opts* opts, void* stream) {
+    if (!lats || !sweeps || n < 1) return ISING_EINVAL;
+    if (n > kStaticMaxJobs) return ISING_ERANGE;  // more lattices than the fixed job table holds
+    ising_batch_opts o = {};
+    if (opts) o = *opts;
+    if (o.block_threads == 0) o.block_threads = 256;
+    if (o.cluster_size == 0) o.cluster_size = 4;
+    if (o.big_sites == 0) o.big_sites = 1 << 18;
+    if (o.block_threads != 128 && o.block_threads != 256 && o.block_threads != 512)
+        return ISING_EINVAL;
+    if (o.cluster_size < 1 || o.cluster_size > 8) return ISING_EINVAL;
+    // validate everything and count the records before touching the GPU
+    int64_t total_rec = 0;
+    for (int i = 0; i < n; ++i) {
+        const ising_lattice* h = lats[i];
+        if (!h || sweeps[i] < 0 || sweeps[i] > 0x7FFFFFFF) return ISING_EINVAL;
+        const int every = measure_every ? measure_every[i] : 1;
+        if (every < 1) return ISING_EINVAL;
+        if (sweeps[i] > 0 && h->t + (uint64_t)sweeps[i] - 1 > kMaxSweep) return ISING_ERANGE;
+        for (int k = 0; k < i; ++k)
+            if (lats[k] == h) return ISING_EINVAL;
+        total_rec += records_in(h->t, sweeps[i], every);
+    }
+    if (total_rec > 0 && (!records || records_cap < total_rec)) return ISING_ERANGE;
+    unsigned char* scratch = nullptr;
+    int grid = 0;
+    int rc = static_setup(o.block_threads, o.cluster_size, &scratch, &grid);
+    if (rc != ISING_OK) return rc;
+    cudaStream_t sm = static_cast<cudaStream_t>(stream);
+    BatchJob* d_jobs = reinterpret_cast<BatchJob*>(scratch);
+    int* d_order = reinterpret_cast<int*>(scratch + kStaticTableBytes);
+    int* d_counters = reinterpret_cast<int*>(scratch + kStaticTableBytes + kStaticOrderBytes);
+
+    // queues, largest work first: cluster-cooperative jobs, then per-CTA jobs
+    int order[kStaticMaxJobs];
+    int n_big = 0;
+    for (int i = 0; i < n; ++i)
+        if (o.cluster_size > 1 && lats[i]->sites >= o.big_sites) order[n_big++] = i;
+    int n_all = n_big;
+    for (int i = 0; i < n; ++i)
+        if (!(o.cluster_size > 1 && lats[i]->sites >= o.big_sites)) order[n_all++] = i;
+    auto work = [&](int i) { return lats[i]->sites * sweeps[i]; };
+    std::stable_sort(order, order + n_big, [&](int x, int y) { return work(x) > work(y); });
+    std::stable_sort(order + n_big, order + n, [&](int x, int y) { return work(x) > work(y); });
+
+    cudaError_t e = cudaSuccess;
+    if (total_rec > 0)  // the fused reductions add into zeroed record slots
+        e = cudaMemsetAsync(records, 0, (size_t)total_rec * 16, sm);
+    // job table, staged through a small host buffer (copies from pageable
+    // memory are complete as far as the source is concerned on return)
+    constexpr int kChunk = 32;
+    BatchJob chunk[kChunk];
+    int64_t rec_off = 0;
+    for (int base = 0; base < n && e == cudaSuccess; base += kChunk) {
+        const int m = n - base < kChunk ? n - base : kChunk;
+        for (int q = 0; q < m; ++q) {
+            const int i = base + q;
+            const ising_lattice* h = lats[i];
+            const int every = measure_every ? measure_every[i] : 1;
+            BatchJob& j = chunk[q];
+            j.col0 = h->col[0];
+            j.col1 = h->col[1];
+            j.obs = reinterpret_cast<unsigned long long*>(records) + 2 * rec_off;
+            j.thr0 = h->thr[0];
+            j.thr1 = h->thr[1];
+            j.thr2 = h->thr[2];
+            j.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
+            j.key1 = (uint32_t)(h->seed >> 32);
+            j.t0 = (uint32_t)h->t;
+            j.dims = h->dims;
+            j.layout = h->layout;
+            j.L = h->L;
+            j.W = h->W;
+            j.rows = (uint32_t)h->rows;
+            j.half = (uint32_t)h->half_sites;
+            j.nsweeps = (int32_t)sweeps[i];
+            j.measure_every = every;
+            rec_off += records_in(h->t, sweeps[i], every);
+        }
+        e = cudaMemcpyAsync(d_jobs + base, chunk, sizeof(BatchJob) * (size_t)m,
+                            cudaMemcpyHostToDevice, sm);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_order, order, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), sm);
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3((unsigned)o.block_threads);
+        cfg.stream = sm;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)o.cluster_size;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, batch_kernel, d_jobs, (const int*)d_order, n_big,
+                               (const int*)(d_order + n_big), n - n_big, d_counters);
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int i = 0; i < n; ++i) lats[i]->t += (uint64_t)sweeps[i];
     return ISING_OK;
 }
 

@@ -31,9 +31,6 @@ namespace ising {
 
 namespace {
 
-constexpr uint32_t kBit7 = kByteBit7;
-constexpr uint32_t kOnes = kByteOnes;
-
 __device__ __forceinline__ int wrap_prev(int v, int n) { return v == 0 ? n - 1 : v - 1; }
 __device__ __forceinline__ int wrap_next(int v, int n) { return v == n - 1 ? 0 : v + 1; }
 

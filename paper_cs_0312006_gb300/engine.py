@@ -90,6 +90,9 @@ def load_library():
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                                  ctypes.c_int),
             "ising_batch_destroy": ([P], None),
+            "ising_batch_run_static": ([ctypes.POINTER(P), ctypes.c_int, i64p,
+                                        ctypes.POINTER(ctypes.c_int), P, ctypes.c_int64,
+                                        ctypes.POINTER(BatchOpts), P], ctypes.c_int),
             "ising_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "ising_version": ([], ctypes.c_char_p),
         }
@@ -271,3 +274,27 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def batch_run_static(lattices, sweeps, measure_every, records_ptr: int, records_cap: int,
+                     block_threads=0, cluster_size=0, big_sites=0, stream=None) -> None:
+    """``ising_batch_run_static``: one persistent launch over ``lattices`` that
+    allocates nothing; E/M records go to the caller's device buffer at
+    ``records_ptr`` ((E, M) int64 pairs, ``records_cap`` pairs, lattice by
+    lattice in order)."""
+    lib = load_library()
+    n = len(lattices)
+    sw = np.asarray(np.broadcast_to(np.asarray(sweeps, dtype=np.int64), (n,)),
+                    dtype=np.int64).copy()
+    ev = np.asarray(np.broadcast_to(np.asarray(measure_every, dtype=np.int32), (n,)),
+                    dtype=np.int32).copy()
+    handles = (ctypes.c_void_p * n)(*[lat.handle for lat in lattices])
+    opts = BatchOpts(block_threads, cluster_size, big_sites, 0, 0)
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib.ising_batch_run_static(handles, n,
+                                      sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      ctypes.c_void_p(records_ptr), int(records_cap),
+                                      ctypes.byref(opts),
+                                      ctypes.c_void_p(int(raw) if raw else 0)),
+           "ising_batch_run_static")
