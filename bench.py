@@ -227,8 +227,9 @@ def run_gpu(args, world, rank, local):
     if args.layout != "both":
         layouts = [x for x in layouts if x[0] == args.layout]
     stream = torch.cuda.current_stream()
+    int8_kernel = {"strip": engine.KERNEL_STRIP, "tma": engine.KERNEL_TMA}[args.int8_kernel]
     sets = {name: [engine.Lattice(2, L, b, BASE_SEED + 16 * rank + j, layout=lay,
-                                  start=engine.COLD_UP, stream=stream)
+                                  start=engine.COLD_UP, stream=stream, kernel=int8_kernel)
                    for j, b in enumerate(betas)] for name, lay in layouts}
 
     def barrier():
@@ -305,7 +306,9 @@ def run_gpu(args, world, rank, local):
         if name == "int8":
             bytes_per_pass = BYTES_PER_UPDATE_INT8 * updates_per_pass
             achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
-            rooflines[name] = {"kernel": "pass_int8_strip<2,measure>", "bound": "hbm",
+            kname = "pass_int8_tma<2,measure>" if args.int8_kernel == "tma" else \
+                "pass_int8_strip<2,measure>"
+            rooflines[name] = {"kernel": kname, "bound": "hbm",
                                "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                                "frac": achieved / peak_hbm, "traffic": None,
                                "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
@@ -467,6 +470,9 @@ def main():
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--L", type=int, default=L_SCAN)
     ap.add_argument("--layout", choices=["both", "int8", "bitpack"], default="both")
+    ap.add_argument("--int8-kernel", choices=["strip", "tma"], default="tma",
+                    help="int8 pass: register-window strips or shared-memory tiles staged by "
+                         "bulk (TMA) copies")
     ap.add_argument("--workload", choices=["scan", "batched", "serving"], default="scan",
                     help="scan: the 2D L=8192 beta scan (default line); batched: 2048 "
                          "lattices in one launch vs one launch per lattice; serving: Poisson "

@@ -46,6 +46,13 @@ enum {
     ISING_AUTO = 2     /* the engine picks (bit-packed); never changes results */
 };
 
+/* Kernels for the int8 colour pass (same results; see ising_set_kernel). */
+enum {
+    ISING_KERNEL_AUTO = 0,  /* the staged kernel where it applies (measured faster) */
+    ISING_KERNEL_STRIP = 1, /* per-thread row strips, neighbour rows in registers */
+    ISING_KERNEL_TMA = 2    /* tiles staged in shared memory by bulk (TMA) copies */
+};
+
 /* Initial states (Sec. 2.2: spins up with probability p). */
 enum {
     ISING_HOT = 0,       /* p = 1/2: s_i = +1 iff Philox(seed; i>>2, 0, 0, 1)[i&3] < 2^31 */
@@ -128,6 +135,19 @@ int ising_set_spins(ising_lattice *lat, const int8_t *host_in, uint64_t t);
  * (L^dims bytes).  Asynchronous on the handle's stream. */
 int ising_export_device(ising_lattice *lat, int8_t *dev_out);
 
+/* Choose the int8 pass kernel of a lattice (ISING_KERNEL_*).  The staged
+ * kernel needs L % 32 == 0 and tiles that fit in shared memory; otherwise, and
+ * for the bit-packed layout, the choice is recorded but the general kernels
+ * run.  Results never depend on it. */
+int ising_set_kernel(ising_lattice *lat, int kernel);
+
+/* Test hook for the bounded waits: while `on` is nonzero, every staged (TMA)
+ * pass expects more bytes on its first tile than are ever copied, so its wait
+ * runs out after about a second, the kernel returns early and the next
+ * ising_synchronize / ising_observables reports ISING_ETIMEOUT.  The spins of
+ * such a pass are not defined.  Off by default. */
+int ising_test_inject_timeout(int on);
+
 /* Use this CUDA stream (a cudaStream_t, may be NULL = legacy default stream)
  * for all later work of the handle.  The caller keeps ownership. */
 int ising_set_stream(ising_lattice *lat, void *stream);
@@ -144,7 +164,8 @@ int ising_compute_thresholds(int dims, double beta, uint32_t out[3]);
 /* Describe the handle. */
 int ising_get_info(const ising_lattice *lat, ising_info_t *out);
 
-/* Block until the handle's stream is idle. */
+/* Block until the handle's stream is idle; ISING_ETIMEOUT if a kernel gave up
+ * on a bounded wait since the last check (the flag is then cleared). */
 int ising_synchronize(ising_lattice *lat);
 
 /* Free everything the handle owns.  NULL is accepted. */

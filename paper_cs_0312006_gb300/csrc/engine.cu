@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -47,6 +48,8 @@ int device_props(const DeviceProps** out) {
         ISING_CHECK(cudaDeviceGetAttribute(&q.sm_count, cudaDevAttrMultiProcessorCount, dev));
         ISING_CHECK(ising::int8_query_occupancy(q));
         ISING_CHECK(ising::packed_query_occupancy(q));
+        ISING_CHECK(cudaMalloc(reinterpret_cast<void**>(&q.d_err), sizeof(int)));
+        ISING_CHECK(cudaMemset(q.d_err, 0, sizeof(int)));
         p = q;
     }
     *out = &p;
@@ -133,6 +136,17 @@ int clear_records(ising_lattice* h) {
     return ISING_OK;
 }
 
+std::atomic<int> g_inject_timeout{0};
+
+// Read and clear the device's bounded-wait flag.
+int check_timeout(ising_lattice* h) {
+    int flag = 0;
+    ISING_CHECK(cudaMemcpy(&flag, h->dp->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag == 0) return ISING_OK;
+    ISING_CHECK(cudaMemset(h->dp->d_err, 0, sizeof(int)));
+    return ISING_ETIMEOUT;
+}
+
 int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     PassArgs a;
     a.own = h->col[c];
@@ -150,6 +164,9 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     a.c = c;
     if (h->layout == ISING_BITPACK)
         ISING_CHECK(ising::packed_pass(a, h->dims, slot != nullptr, *h->dp, h->stream));
+    else if (h->kernel != ISING_KERNEL_STRIP && ising::int8_tma_ok(h->dims, h->L))
+        ISING_CHECK(ising::int8_pass_tma(a, h->dims, slot != nullptr, *h->dp, h->dp->d_err,
+                                         g_inject_timeout.load() ? 16u : 0u, h->stream));
     else
         ISING_CHECK(ising::int8_pass(a, h->dims, h->half_sites, slot != nullptr, *h->dp,
                                      h->stream));
@@ -276,6 +293,8 @@ int ising_sweep(ising_lattice* h, int64_t n, int measure_every) {
 int ising_observables(ising_lattice* h, int64_t* E, int64_t* M, int64_t cap, int64_t* count) {
     if (!h) return ISING_EINVAL;
     ISING_CHECK(cudaStreamSynchronize(h->stream));
+    const int trc = check_timeout(h);
+    if (trc != ISING_OK) return trc;
     if (count) *count = h->n_rec;
     if (!E || !M) return ISING_OK;
     if (cap < h->n_rec) return ISING_ERANGE;
@@ -386,6 +405,19 @@ int ising_get_info(const ising_lattice* h, ising_info_t* out) {
 int ising_synchronize(ising_lattice* h) {
     if (!h) return ISING_EINVAL;
     ISING_CHECK(cudaStreamSynchronize(h->stream));
+    return check_timeout(h);
+}
+
+int ising_set_kernel(ising_lattice* h, int kernel) {
+    if (!h) return ISING_EINVAL;
+    if (kernel != ISING_KERNEL_AUTO && kernel != ISING_KERNEL_STRIP && kernel != ISING_KERNEL_TMA)
+        return ISING_EINVAL;
+    h->kernel = kernel;
+    return ISING_OK;
+}
+
+int ising_test_inject_timeout(int on) {
+    g_inject_timeout.store(on ? 1 : 0);
     return ISING_OK;
 }
 

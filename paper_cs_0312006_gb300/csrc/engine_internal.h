@@ -30,6 +30,7 @@ struct ising_lattice {
     unsigned long long* obs = nullptr;  // (E, M) int64 pairs; slots >= n_rec are zero
     int64_t obs_cap = 0, n_rec = 0;
     const ising::DeviceProps* dp = nullptr;
+    int kernel = ISING_KERNEL_AUTO;     // int8 pass kernel choice
 };
 
 namespace ising {
@@ -39,6 +40,7 @@ struct DeviceProps {
     int sm_count = 0;
     int blocks_per_sm_vec[2][2] = {{1, 1}, {1, 1}};    // int8 vector pass [dims-2][measure]
     int blocks_per_sm_packed[2][2] = {{1, 1}, {1, 1}}; // bit-packed pass [dims-2][measure]
+    int* d_err = nullptr;  // raised by a kernel whose bounded wait ran out
 };
 
 // engine.cu helpers shared with batch.cu
@@ -58,6 +60,11 @@ cudaError_t int8_export(const int8_t* col0, const int8_t* col1, int8_t* out, int
                         int64_t sites, const DeviceProps& dp, cudaStream_t st);
 cudaError_t int8_import(int8_t* col0, int8_t* col1, const int8_t* in, int L, int dims,
                         int64_t sites, const DeviceProps& dp, cudaStream_t st);
+
+// int8 layout, inputs staged by bulk copies (sweep_int8_tma.cu)
+bool int8_tma_ok(int dims, int L);
+cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
+                          int* err, uint32_t extra_tx, cudaStream_t st);
 
 // bit-packed layout (sweep_bitpack.cu)
 cudaError_t packed_query_occupancy(DeviceProps& dp);

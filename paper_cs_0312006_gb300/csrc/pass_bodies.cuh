@@ -62,6 +62,25 @@ __device__ __forceinline__ uint32_t uphill_accept(uint32_t D, uint32_t u, int j,
     return u < t ? (0xFEu << (8 * j)) : 0u;
 }
 
+// The same test for four sites by counting: byte j gains 2 for every threshold
+// u_j lies below; since the thresholds fall with k, site j (d_j < dims) flips
+// iff 2*(count_j + d_j) >= 2*dims, read off bit 7 after the bias.
+template <int DIMS>
+__device__ __forceinline__ uint32_t uphill_count(uint32_t D, const Philox4& u, const PassArgs& a) {
+    constexpr uint32_t bias = (0x80u - 2u * DIMS) * kByteOnes;
+    uint32_t acc = D + bias;
+    acc += (u.w0 < a.thr0 ? 0x00000002u : 0u) + (u.w0 < a.thr1 ? 0x00000002u : 0u);
+    acc += (u.w1 < a.thr0 ? 0x00000200u : 0u) + (u.w1 < a.thr1 ? 0x00000200u : 0u);
+    acc += (u.w2 < a.thr0 ? 0x00020000u : 0u) + (u.w2 < a.thr1 ? 0x00020000u : 0u);
+    acc += (u.w3 < a.thr0 ? 0x02000000u : 0u) + (u.w3 < a.thr1 ? 0x02000000u : 0u);
+    if (DIMS == 3) {
+        acc += (u.w0 < a.thr2 ? 0x00000002u : 0u) + (u.w1 < a.thr2 ? 0x00000200u : 0u);
+        acc += (u.w2 < a.thr2 ? 0x00020000u : 0u) + (u.w3 < a.thr2 ? 0x02000000u : 0u);
+    }
+    const uint32_t F = acc & kByteBit7;
+    return F | (F - (F >> 6));
+}
+
 template <int DIMS>
 __device__ __forceinline__ uint32_t disagreements(uint32_t s, uint32_t n0, uint32_t n1,
                                                   uint32_t n2, uint32_t n3, uint32_t n4,
@@ -236,13 +255,11 @@ __device__ __forceinline__ uint4 update_vec(const uint4& s, const uint4& x, cons
 #pragma unroll
         for (int w = 0; w < 4; ++w)
             u[w] = philox4x32_10(g0 + (uint32_t)w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
+        // counting thresholds below each draw measured a little faster here
+        // than selecting one threshold per site (uphill_accept): it spreads the
+        // work over the integer ALU and the multiply-add pipe
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            X[w] |= uphill_accept<DIMS>(D[w], u[w].w0, 0, a) |
-                    uphill_accept<DIMS>(D[w], u[w].w1, 1, a) |
-                    uphill_accept<DIMS>(D[w], u[w].w2, 2, a) |
-                    uphill_accept<DIMS>(D[w], u[w].w3, 3, a);
-        }
+        for (int w = 0; w < 4; ++w) X[w] |= uphill_count<DIMS>(D[w], u[w], a);
     }
     uint32_t out[4];
 #pragma unroll

@@ -1,0 +1,278 @@
+// sweep_int8_tma.cu -- the int8 colour pass with its inputs staged in shared
+// memory by the Tensor Memory Accelerator (bulk asynchronous copies).
+//
+// Same arithmetic and draws as the register-window strip kernel
+// (sweep_int8.cu, update_vec in pass_bodies.cuh); only the data movement
+// differs.  A tile is a band of R consecutive half rows of one plane (full
+// width W = L/2 bytes, W % 16 == 0).  For each tile one thread issues
+// cp.async.bulk copies of
+//   - the tile's own-colour rows (R*W contiguous bytes),
+//   - the other colour's rows y0-1 .. y0+R (the band plus one halo row on
+//     each side; the halo rows wrap around the plane, so they are separate
+//     copies),
+//   - for 3D, the other colour's bands in planes z-1 and z+1,
+// into one of S pipeline stages, completing on that stage's mbarrier.
+// Persistent CTAs walk their tiles while the copies for the next S-1 tiles
+// are in flight.  Every thread owns 16-byte columns of the band and slides
+// down them, reading its neighbour rows from shared memory (x-neighbour edge
+// bytes from the adjacent column in shared memory, so no shuffles), and
+// writes its updated vectors straight to global memory.
+//
+// Waits on an mbarrier are bounded: if a phase does not complete within the
+// limit the kernel raises the error flag, waits (bounded again) for its own
+// copies still in flight, and returns; the host reports ISING_ETIMEOUT.
+#include <cstdint>
+
+#include "engine_internal.h"
+#include "ising_device.cuh"
+#include "pass_bodies.cuh"
+
+namespace ising {
+
+namespace {
+
+constexpr int kStages = 2;
+constexpr int kTileRows = 2;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // give up on a phase after ~1 s
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t done;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return done != 0u;
+}
+
+// Bounded wait for `phase` of `bar`: false once ~1 s of wall time has passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+    if (mbar_try_wait(bar, phase)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+// One bulk copy global -> shared, completing `bytes` on `bar`.  Both addresses
+// are 16-byte aligned and bytes is a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+struct TmaGeom {
+    int R;          // rows per tile
+    int tiles;      // tiles in the lattice
+    int bands;      // tiles per plane: L / R
+    uint32_t stage_bytes;
+    uint32_t extra_tx;  // test hook: bytes expected on the first tile that never arrive
+};
+
+// Offsets inside one stage: own rows [0, R*W), other rows y0-1..y0+R at
+// [R*W, (2R+2)*W), 3D: other band of plane z-1, then z+1.
+template <int DIMS>
+__device__ __forceinline__ void issue_tile(const PassArgs& a, const TmaGeom& tg, int tile,
+                                           unsigned char* stage, uint64_t* bar,
+                                           uint32_t extra_tx) {
+    const uint32_t W = (uint32_t)a.W, L = (uint32_t)a.L, R = (uint32_t)tg.R;
+    const uint32_t z = DIMS == 3 ? (uint32_t)tile / (uint32_t)tg.bands : 0u;
+    const uint32_t y0 = ((uint32_t)tile - z * (uint32_t)tg.bands) * R;
+    const uint32_t plane = z * L;
+    const unsigned char* own = static_cast<const unsigned char*>(a.own);
+    const unsigned char* oth = static_cast<const unsigned char*>(a.other);
+    mbar_expect_tx(bar, tg.stage_bytes + extra_tx);
+    bulk_g2s(stage, own + (size_t)(plane + y0) * W, R * W, bar);
+    unsigned char* o = stage + R * W;
+    const uint32_t ym = y0 == 0u ? L - 1u : y0 - 1u;
+    const uint32_t yp = y0 + R == L ? 0u : y0 + R;
+    bulk_g2s(o, oth + (size_t)(plane + ym) * W, W, bar);
+    bulk_g2s(o + W, oth + (size_t)(plane + y0) * W, R * W, bar);
+    bulk_g2s(o + (R + 1u) * W, oth + (size_t)(plane + yp) * W, W, bar);
+    if (DIMS == 3) {
+        const uint32_t zm = z == 0u ? L - 1u : z - 1u, zp = z + 1u == L ? 0u : z + 1u;
+        unsigned char* zb = o + (R + 2u) * W;
+        bulk_g2s(zb, oth + (size_t)(zm * L + y0) * W, R * W, bar);
+        bulk_g2s(zb + R * W, oth + (size_t)(zp * L + y0) * W, R * W, bar);
+    }
+}
+
+template <int DIMS, bool MEASURE>
+__global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[kStages];
+    const uint32_t W = (uint32_t)a.W, R = (uint32_t)tg.R;
+    const uint32_t nv = W >> 4;
+    // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int first = blockIdx.x;
+    const int my_tiles = first < tg.tiles ? (tg.tiles - 1 - first) / (int)gridDim.x + 1 : 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kStages && k < my_tiles; ++k)
+            issue_tile<DIMS>(a, tg, first + k * gridDim.x, smem + k * tg.stage_bytes, &bars[k],
+                             k == 0 ? tg.extra_tx : 0u);
+
+    int e_acc = 0, m_neg = 0, n_vec = 0;
+    uint4* own_g = static_cast<uint4*>(a.own);
+    for (int k = 0; k < my_tiles; ++k) {
+        const int s = k % kStages;
+        const uint32_t phase = (uint32_t)(k / kStages) & 1u;
+        const bool ok = mbar_wait(&bars[s], phase);
+        if (__syncthreads_or(!ok)) {
+            // a phase never completed: raise the flag, let this CTA's copies in
+            // flight land (bounded), and leave without a reduction
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                for (int k2 = k; k2 < my_tiles && k2 < k + kStages; ++k2)
+                    (void)mbar_wait(&bars[k2 % kStages], (uint32_t)(k2 / kStages) & 1u);
+            }
+            return;
+        }
+        const int tile = first + k * gridDim.x;
+        const uint32_t z = DIMS == 3 ? (uint32_t)tile / (uint32_t)tg.bands : 0u;
+        const uint32_t y0 = ((uint32_t)tile - z * (uint32_t)tg.bands) * R;
+        const unsigned char* st = smem + s * tg.stage_bytes;
+        const uint4* own_s = reinterpret_cast<const uint4*>(st);
+        const unsigned char* oth = st + R * W;  // row slot j holds y0 - 1 + j
+        const uint4* oth16 = reinterpret_cast<const uint4*>(oth);
+        const uint4* zm16 = reinterpret_cast<const uint4*>(oth + (R + 2u) * W);
+        const uint4* zp16 = zm16 + R * nv;
+        for (uint32_t i = 0; i < R; ++i) {
+            const uint32_t y = y0 + i;
+            const int p = (a.c + (int)y + (int)z) & 1;
+            const uint32_t* row32 = reinterpret_cast<const uint32_t*>(oth + (i + 1u) * W);
+            // columns fastest across the threads: a warp reads contiguous shared memory
+            for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
+                const uint4 oc = oth16[(i + 1u) * nv + v];
+                const uint4 om = oth16[i * nv + v];
+                const uint4 op = oth16[(i + 2u) * nv + v];
+                uint4 zm = make_uint4(0u, 0u, 0u, 0u), zp = zm;
+                if (DIMS == 3) {
+                    zm = zm16[i * nv + v];
+                    zp = zp16[i * nv + v];
+                }
+                uint4 sh;
+                if (p == 0) {  // byte j <- byte j - 1 (wrapping to the row's last byte)
+                    const uint32_t prev = row32[(v == 0u ? nv - 1u : v - 1u) * 4u + 3u];
+                    sh = make_uint4(__funnelshift_l(prev, oc.x, 8), __funnelshift_l(oc.x, oc.y, 8),
+                                    __funnelshift_l(oc.y, oc.z, 8), __funnelshift_l(oc.z, oc.w, 8));
+                } else {       // byte j <- byte j + 1 (wrapping to the row's first byte)
+                    const uint32_t next = row32[(v + 1u == nv ? 0u : v + 1u) * 4u];
+                    sh = make_uint4(__funnelshift_r(oc.x, oc.y, 8), __funnelshift_r(oc.y, oc.z, 8),
+                                    __funnelshift_r(oc.z, oc.w, 8), __funnelshift_r(oc.w, next, 8));
+                }
+                const uint32_t row = (z * (uint32_t)a.L + y) * nv + v;  // global vector index
+                int e_vec = 0;
+                own_g[row] = update_vec<DIMS, MEASURE>(own_s[i * nv + v], oc, sh, om, op, zm, zp,
+                                                       row * 4u, a, e_vec, m_neg);
+                e_acc += e_vec;
+                ++n_vec;
+            }
+        }
+        __syncthreads();  // every thread is done with stage s
+        if (threadIdx.x == 0 && k + kStages < my_tiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_tile<DIMS>(a, tg, first + (k + kStages) * gridDim.x, smem + s * tg.stage_bytes,
+                             &bars[s], 0u);
+        }
+    }
+    if (MEASURE) {
+        if (a.c == 1) e_acc -= n_vec * 16 * 2 * DIMS;  // E_white = sum (2 d_new - 2 dims)
+        block_reduce_add(e_acc, n_vec * 16 - 2 * m_neg, a.obs, a.c == 1);
+    }
+}
+
+template <int DIMS, bool MEASURE>
+cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uint32_t extra_tx,
+                         cudaStream_t st) {
+    TmaGeom tg;
+    tg.extra_tx = extra_tx;
+    const int planes = DIMS == 3 ? a.L : 1;
+    // two rows per tile and 256 threads measured best on GB300 (2D L=8192:
+    // 44.7 us per pass, against 49 us with four rows and 55 us with eight)
+    int R = kTileRows;
+    const int threads = 256;
+    while (R > 1 && (a.L % R != 0)) R >>= 1;
+    tg.R = R;
+    tg.bands = a.L / R;
+    tg.tiles = tg.bands * planes;
+    const uint32_t W = (uint32_t)a.W;
+    tg.stage_bytes = (uint32_t)(2 * R + 2) * W + (DIMS == 3 ? 2u * R * W : 0u);
+    const size_t smem = (size_t)kStages * tg.stage_bytes;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    static int attr_set = 0;  // largest dynamic shared memory opted into so far
+    cudaError_t e = cudaSuccess;
+    if ((int)smem > attr_set) {
+        e = cudaFuncSetAttribute(pass_int8_tma<DIMS, MEASURE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = 200 * 1024;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_int8_tma<DIMS, MEASURE>,
+                                                      threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid = dp.sm_count * per_sm;
+    if (grid > tg.tiles) grid = tg.tiles;
+    pass_int8_tma<DIMS, MEASURE><<<grid, threads, smem, st>>>(a, tg, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// The staged kernel needs W % 16 == 0 and its stages (2 x (2R+2) half rows,
+// plus 2 x 2R for 3D) to fit in shared memory.
+bool int8_tma_ok(int dims, int L) {
+    const int W = L / 2;
+    if (W % 16 != 0) return false;
+    int R = kTileRows;
+    while (R > 1 && (L % R != 0)) R >>= 1;
+    const size_t stage = (size_t)(2 * R + 2) * W + (dims == 3 ? 2u * R * W : 0u);
+    return (size_t)kStages * stage <= 200 * 1024;
+}
+
+cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
+                          int* err, uint32_t extra_tx, cudaStream_t st) {
+    if (dims == 2)
+        return measure ? launch_tma_t<2, true>(a, dp, err, extra_tx, st)
+                       : launch_tma_t<2, false>(a, dp, err, extra_tx, st);
+    return measure ? launch_tma_t<3, true>(a, dp, err, extra_tx, st)
+                   : launch_tma_t<3, false>(a, dp, err, extra_tx, st);
+}
+
+}  // namespace ising

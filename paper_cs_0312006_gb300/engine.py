@@ -19,6 +19,7 @@ from . import _build
 
 INT8, BITPACK, AUTO = 0, 1, 2
 HOT, COLD_UP, COLD_DOWN = 0, 1, 2
+KERNEL_AUTO, KERNEL_STRIP, KERNEL_TMA = 0, 1, 2
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, ERANGE = 0, -1, -2, -3, -4, -5, -6
 
@@ -80,6 +81,8 @@ def load_library():
             "ising_compute_thresholds": ([ctypes.c_int, ctypes.c_double, u32p], ctypes.c_int),
             "ising_get_info": ([P, ctypes.POINTER(IsingInfo)], ctypes.c_int),
             "ising_synchronize": ([P], ctypes.c_int),
+            "ising_set_kernel": ([P, ctypes.c_int], ctypes.c_int),
+            "ising_test_inject_timeout": ([ctypes.c_int], ctypes.c_int),
             "ising_destroy": ([P], None),
             "ising_batch_create": ([ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int, i64p,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(BatchOpts), P],
@@ -109,6 +112,11 @@ def _check(rc: int, what: str) -> None:
         raise IsingError(rc, what)
 
 
+def test_inject_timeout(on: bool) -> None:
+    """Test hook: make every staged (TMA) pass's bounded wait run out."""
+    _check(load_library().ising_test_inject_timeout(1 if on else 0), "ising_test_inject_timeout")
+
+
 def compute_thresholds(dims: int, beta: float) -> np.ndarray:
     """``ising_compute_thresholds``: the engine's host-side threshold table."""
     out = np.zeros(3, dtype=np.uint32)
@@ -122,7 +130,7 @@ class Lattice:
     """One lattice on the current CUDA device (``ising_create``)."""
 
     def __init__(self, dims: int, L: int, beta: float, seed: int, layout: int = INT8,
-                 start: int = HOT, stream=None):
+                 start: int = HOT, stream=None, kernel: int = KERNEL_AUTO):
         lib = load_library()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -131,6 +139,8 @@ class Lattice:
                f"ising_create(dims={dims}, L={L}, beta={beta})")
         if stream is not None:
             self.set_stream(stream)
+        if kernel != KERNEL_AUTO:
+            self.set_kernel(kernel)
         if start != HOT:
             self.init(start)
 
@@ -211,6 +221,10 @@ class Lattice:
 
     def synchronize(self) -> None:
         _check(self._lib.ising_synchronize(self._h), "ising_synchronize")
+
+    def set_kernel(self, kernel: int) -> None:
+        """int8 pass kernel: KERNEL_AUTO, KERNEL_STRIP or KERNEL_TMA."""
+        _check(self._lib.ising_set_kernel(self._h, int(kernel)), "ising_set_kernel")
 
     @property
     def handle(self) -> int:

@@ -47,8 +47,8 @@ def eng():
     return engine
 
 
-def gpu_run(eng, dims, L, beta, seed, start, nsweeps, every, chunks=None, layout=0):
-    lat = eng.Lattice(dims, L, beta, seed, layout=layout, start=start)
+def gpu_run(eng, dims, L, beta, seed, start, nsweeps, every, chunks=None, layout=0, kernel=0):
+    lat = eng.Lattice(dims, L, beta, seed, layout=layout, start=start, kernel=kernel)
     if chunks is None:
         chunks = [nsweeps]
     assert sum(chunks) == nsweeps
@@ -105,6 +105,17 @@ def test_sweeps_match_oracle_3d(eng, L, beta):
     for layout in layouts_for(L):
         g = gpu_run(eng, 3, L, beta, 99 + L, HOT, n, 1, layout=layout)
         assert_same(g, o, f"3D L={L} beta={beta} layout={layout}")
+
+
+@pytest.mark.parametrize("dims,L", [(2, 32), (2, 64), (2, 96), (2, 160), (2, 1024), (3, 32),
+                                    (3, 64), (3, 96)])
+def test_tma_staged_kernel_matches_oracle(eng, dims, L):
+    """The int8 pass with its rows staged in shared memory by bulk copies."""
+    n = 8 if dims == 2 else 4
+    beta = 0.4406868 if dims == 2 else 0.2216544
+    o = oracle.run(dims, L, beta, 5 + L, n, measure_every=1, start=HOT)
+    g = gpu_run(eng, dims, L, beta, 5 + L, HOT, n, 1, layout=INT8, kernel=eng.KERNEL_TMA)
+    assert_same(g, o, f"TMA {dims}D L={L}")
 
 
 def test_auto_layout_choice_and_identity(eng):
@@ -220,9 +231,10 @@ def test_beta_scan_L8192_first_20_sweeps(eng, pool):
             for j, b in enumerate(SCAN_BETAS)]
     for j, b in enumerate(SCAN_BETAS):
         want = futs[j].result()
-        for layout in (INT8, BITPACK):
-            g = gpu_run(eng, 2, 8192, b, 20031109 + j, COLD_UP, 20, 1, layout=layout)
-            assert_same(g, want, f"L=8192 beta={b} layout={layout}")
+        for layout, kernel in ((INT8, 1), (INT8, 2), (BITPACK, 0)):
+            g = gpu_run(eng, 2, 8192, b, 20031109 + j, COLD_UP, 20, 1, layout=layout,
+                        kernel=kernel)
+            assert_same(g, want, f"L=8192 beta={b} layout={layout} kernel={kernel}")
 
 
 @pytest.mark.parametrize("layout", [INT8, BITPACK])
