@@ -462,6 +462,37 @@ def run_serving_workload(args):
     return 0
 
 
+def run_philox_workload(args):
+    """Throughput of the device generator alone (ising_philox_fill): the
+    ceiling that the Metropolis draws put on any pass kernel."""
+    import torch
+    from paper_cs_0312006_gb300 import _build, engine
+    _build.build()
+    engine.load_library()
+    # 2^22 calls per launch: the 64 MiB of output stays in L2, so the launches
+    # measure the generator's arithmetic, not HBM stores
+    n = 1 << 22
+    out = torch.empty(4 * n, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        engine.philox_fill(out.data_ptr(), n, 5, 1, 0, BASE_SEED)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    reps = 200
+    for _ in range(reps):
+        engine.philox_fill(out.data_ptr(), n, 5, 1, 0, BASE_SEED)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    line = {"metric": "Philox4x32-10 calls/s", "value": n / (ms / 1e3), "unit": "calls/s",
+            "draws_per_s": 4 * n / (ms / 1e3), "ms_per_launch": ms, "calls": n,
+            "store_GB_per_s": 16 * n / (ms / 1e3) / 1e9, "sm_count": sm,
+            "device": torch.cuda.get_device_name()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -473,7 +504,8 @@ def main():
     ap.add_argument("--int8-kernel", choices=["strip", "tma"], default="tma",
                     help="int8 pass: register-window strips or shared-memory tiles staged by "
                          "bulk (TMA) copies")
-    ap.add_argument("--workload", choices=["scan", "batched", "serving"], default="scan",
+    ap.add_argument("--workload", choices=["scan", "batched", "serving", "philox"],
+                    default="scan",
                     help="scan: the 2D L=8192 beta scan (default line); batched: 2048 "
                          "lattices in one launch vs one launch per lattice; serving: Poisson "
                          "job stream")
@@ -502,6 +534,8 @@ def main():
         return run_batched_workload(args)
     if args.workload == "serving" and args.impl != "reference":
         return run_serving_workload(args)
+    if args.workload == "philox" and args.impl != "reference":
+        return run_philox_workload(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_gpu(args, world, rank, local)

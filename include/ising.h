@@ -141,6 +141,14 @@ int ising_export_device(ising_lattice *lat, int8_t *dev_out);
  * run.  Results never depend on it. */
 int ising_set_kernel(ising_lattice *lat, int kernel);
 
+/* The engine's counter-based generator on the device: for c0 = 0..n-1,
+ * dev_out[4*c0 + j] = word j of Philox4x32-10(key = seed; counter =
+ * (c0, c1, c2, c3)) (Salmon et al., SC'11), the same function every kernel
+ * draws from.  dev_out: caller-owned device memory of 4n uint32.  Asynchronous
+ * on `stream`.  For checking the generator and measuring its throughput. */
+int ising_philox_fill(uint32_t *dev_out, uint32_t n, uint32_t c1, uint32_t c2, uint32_t c3,
+                      uint64_t seed, void *stream);
+
 /* Test hook for the bounded waits: while `on` is nonzero, every staged (TMA)
  * pass expects more bytes on its first tile than are ever copied, so its wait
  * runs out after about a second, the kernel returns early and the next

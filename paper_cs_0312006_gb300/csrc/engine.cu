@@ -416,6 +416,18 @@ int ising_set_kernel(ising_lattice* h, int kernel) {
     return ISING_OK;
 }
 
+int ising_philox_fill(uint32_t* dev_out, uint32_t n, uint32_t c1, uint32_t c2, uint32_t c3,
+                      uint64_t seed, void* stream) {
+    if (!dev_out && n > 0) return ISING_EINVAL;
+    if (n == 0) return ISING_OK;
+    const DeviceProps* dp = nullptr;
+    const int rc = device_props(&dp);
+    if (rc != ISING_OK) return rc;
+    ISING_CHECK(ising::philox_fill(dev_out, n, c1, c2, c3, (uint32_t)(seed & 0xFFFFFFFFu),
+                                   (uint32_t)(seed >> 32), *dp, static_cast<cudaStream_t>(stream)));
+    return ISING_OK;
+}
+
 int ising_test_inject_timeout(int on) {
     g_inject_timeout.store(on ? 1 : 0);
     return ISING_OK;

@@ -52,6 +52,8 @@ constexpr uint64_t kMaxSweep = 0xFFFFFFFFull;  // the sweep index is a 32-bit co
 // int8 layout (sweep_int8.cu)
 cudaError_t int8_query_occupancy(DeviceProps& dp);
 bool int8_vec_ok(int L);
+cudaError_t philox_fill(uint32_t* out, uint32_t n, uint32_t c1, uint32_t c2, uint32_t c3,
+                        uint32_t key0, uint32_t key1, const DeviceProps& dp, cudaStream_t st);
 cudaError_t int8_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure,
                       const DeviceProps& dp, cudaStream_t st);
 cudaError_t int8_init(int8_t* col0, int8_t* col1, int L, int dims, int64_t sites, int start,

@@ -235,6 +235,18 @@ cudaError_t launch_pass_t(const PassArgs& a0, int64_t half_sites, bool vec, cons
 
 }  // namespace
 
+// Philox4x32-10 blocks for counters (c0, c1, c2, c3), c0 = 0..n-1 under key
+// (key0, key1): out[4 c0 + j] = word j.  Used to pin the device generator and
+// to measure its throughput.
+__global__ void philox_fill_kernel(uint4* out, uint32_t n, uint32_t c1, uint32_t c2, uint32_t c3,
+                                   uint32_t key0, uint32_t key1) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const Philox4 u = philox4x32_10(i, c1, c2, c3, key0, key1);
+        out[i] = make_uint4(u.w0, u.w1, u.w2, u.w3);
+    }
+}
+
 cudaError_t int8_query_occupancy(DeviceProps& dp) {
     cudaError_t e;
 #define ISING_OCC(D, M)                                                                      \
@@ -250,6 +262,17 @@ cudaError_t int8_query_occupancy(DeviceProps& dp) {
 }
 
 bool int8_vec_ok(int L) { return (L / 2) % 16 == 0; }
+
+cudaError_t philox_fill(uint32_t* out, uint32_t n, uint32_t c1, uint32_t c2, uint32_t c3,
+                        uint32_t key0, uint32_t key1, const DeviceProps& dp, cudaStream_t st) {
+    int64_t blocks = ((int64_t)n + 255) / 256;
+    const int64_t cap = (int64_t)dp.sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    philox_fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<uint4*>(out), n, c1, c2,
+                                                          c3, key0, key1);
+    return cudaGetLastError();
+}
 
 cudaError_t int8_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure,
                       const DeviceProps& dp, cudaStream_t st) {

@@ -83,6 +83,8 @@ def load_library():
             "ising_synchronize": ([P], ctypes.c_int),
             "ising_set_kernel": ([P, ctypes.c_int], ctypes.c_int),
             "ising_test_inject_timeout": ([ctypes.c_int], ctypes.c_int),
+            "ising_philox_fill": ([P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.c_uint32, ctypes.c_uint64, P], ctypes.c_int),
             "ising_destroy": ([P], None),
             "ising_batch_create": ([ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int, i64p,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(BatchOpts), P],
@@ -110,6 +112,15 @@ def load_library():
 def _check(rc: int, what: str) -> None:
     if rc != OK:
         raise IsingError(rc, what)
+
+
+def philox_fill(dev_ptr: int, n: int, c1: int, c2: int, c3: int, seed: int, stream=None) -> None:
+    """``ising_philox_fill``: 4n uint32 of Philox4x32-10 at ``dev_ptr``."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(load_library().ising_philox_fill(ctypes.c_void_p(dev_ptr), n, c1, c2, c3,
+                                            ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                                            ctypes.c_void_p(int(raw) if raw else 0)),
+           "ising_philox_fill")
 
 
 def test_inject_timeout(on: bool) -> None:

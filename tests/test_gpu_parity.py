@@ -263,3 +263,19 @@ def test_3d_L256_near_critical(eng, pool, layout):
     s_o, e_o, m_o = step.result()
     assert np.array_equal(s_o, s1000), "sweep 999 transition"
     assert (E_last[0], M_last[0]) == (e_o, m_o) == e_chk.result()
+
+
+def test_device_philox_matches_oracle(eng):
+    """The device generator (every kernel's draws) against the oracle's Philox
+    (itself pinned to Triton's library implementation)."""
+    import torch
+    rng = np.random.default_rng(4)
+    for seed, (c1, c2, c3) in [(20031109, (0, 0, 0)), (0xFFFFFFFFFFFFFFFF, (7, 1, 0)),
+                               (12345, (2 ** 32 - 1, 1, 2))]:
+        n = 4096
+        out = torch.zeros(4 * n, dtype=torch.int32, device="cuda")
+        eng.philox_fill(out.data_ptr(), n, c1, c2, c3, seed)
+        got = out.cpu().numpy().view(np.uint32).reshape(n, 4)
+        key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
+        for i in list(rng.integers(0, n, size=64)) + [0, n - 1]:
+            assert got[i].tolist() == oracle.philox4x32_10([i, c1, c2, c3], key).tolist()
