@@ -49,6 +49,46 @@ BASE_SEED = 20031109
 BYTES_PER_UPDATE_INT8 = 3  # per colour pass: read own N/2, read other N/2, write own N/2
 
 
+# DRAM bytes per site update of the two pass kernels on this workload, from one
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` capture of the
+# bench's own run (profiles/dram_traffic_bench_scan_L8192.md).  They describe
+# the kernel sources whose hash is recorded; any change to those sources makes
+# the bench report "traffic": null until the capture is redone.
+TRAFFIC = {
+    "int8": {"bytes_per_update": 1.9656, "sha1": "593903d67fa083d7bf84ff7ab3b969c5774fbb62",
+             "sources": ["sweep_int8_tma.cu", "pass_bodies.cuh", "ising_device.cuh"]},
+    "bitpack": {"bytes_per_update": 0.2230, "sha1": "7eaa6f9995ad8b6cc3269ccc2ec50aaa3a3cf8b8",
+                "sources": ["sweep_bitpack.cu", "pass_bodies.cuh", "ising_device.cuh"]},
+}
+
+
+def kernel_sources_sha1(names) -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_cs_0312006_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(layout: str, updates_per_launch: int):
+    t = TRAFFIC[layout]
+    if t["bytes_per_update"] is None or kernel_sources_sha1(t["sources"]) != t["sha1"]:
+        return None
+    return t["bytes_per_update"] * updates_per_launch
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def scan_betas():
     return [round(0.30 + 0.02 * j, 10) for j in range(N_BETA)]
 
@@ -279,12 +319,7 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    ms = start.elapsed_time(stop)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(stop), world, device="cuda")
     per_layout_updates = world * len(betas) * n_sites * args.steps
     value = per_layout_updates * len(sets) / (ms / 1e3)
     for lats in sets.values():  # every step recorded one (E, M) per lattice
@@ -310,7 +345,8 @@ def run_gpu(args, world, rank, local):
                 "pass_int8_strip<2,measure>"
             rooflines[name] = {"kernel": kname, "bound": "hbm",
                                "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
-                               "frac": achieved / peak_hbm, "traffic": None,
+                               "frac": achieved / peak_hbm,
+                               "traffic": measured_traffic("int8", updates_per_pass),
                                "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
                                "peak_source": f"{peak_kind} hbm_gbs (copy)"}
         else:
@@ -318,7 +354,8 @@ def run_gpu(args, world, rank, local):
             achieved = updates_per_pass / (pass_ms / 1e3)
             rooflines[name] = {"kernel": "pass_packed<2,measure>", "bound": "alu",
                                "achieved": achieved, "peak": peak, "unit": "site updates/s",
-                               "frac": achieved / peak, "traffic": None,
+                               "frac": achieved / peak,
+                               "traffic": measured_traffic("bitpack", updates_per_pass),
                                "launch_ms": pass_ms,
                                "peak_source": "derived: SMs x 32 wide multiplies/clk / 18 per "
                                               "Philox call x 4 sites x median SM clock"}
@@ -346,12 +383,7 @@ def run_gpu(args, world, rank, local):
                 lat.get_spins(host_out)  # D2H of the final configuration
                 d2h += n_sites
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
         h2d_total = len(sets) * len(betas) * n_sites
         e2e = {"value": world * len(sets) * len(betas) * n_sites * e2e_steps / dt,
                "unit": "site updates/s", "h2d_bytes_per_step": h2d_total / e2e_steps,
@@ -462,6 +494,43 @@ def run_serving_workload(args):
     return 0
 
 
+def run_small_workload(args):
+    """The small critical run: 2D L=64 at beta_c, hot start, seed 20031109,
+    1000 sweeps with E/M every sweep, checked against the oracle."""
+    import numpy as np
+    import torch
+    from paper_cs_0312006_gb300 import _build, engine
+    _build.build()
+    engine.load_library()
+    L, beta, n = 64, 0.4406868, 1000
+    lat = engine.Lattice(2, L, beta, BASE_SEED)
+    lat.sweep(n, 1)  # warm-up run
+    lat.observables()
+    times = []
+    for _ in range(5):
+        lat.init(engine.HOT)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lat.sweep(n, 1)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    E, M = lat.observables()
+    s = lat.get_spins()
+    lat.close()
+    import oracle
+    s_o, E_o, M_o = oracle.run(2, L, beta, BASE_SEED, n, measure_every=1)
+    exact = bool(np.array_equal(s, s_o) and np.array_equal(E, E_o) and np.array_equal(M, M_o))
+    ms = sorted(times)[len(times) // 2]
+    line = {"metric": "site updates/s", "value": L * L * n / (ms / 1e3), "unit": "site updates/s",
+            "workload": "2D L=64, beta 0.4406868, hot start, 1000 sweeps, E/M every sweep",
+            "us_per_sweep": ms * 1e3 / n, "median_ms": ms, "bit_exact_vs_oracle": exact,
+            "device": torch.cuda.get_device_name()}
+    print(json.dumps(line), flush=True)
+    return 0 if exact else 1
+
+
 def run_philox_workload(args):
     """Throughput of the device generator alone (ising_philox_fill): the
     ceiling that the Metropolis draws put on any pass kernel."""
@@ -504,7 +573,7 @@ def main():
     ap.add_argument("--int8-kernel", choices=["strip", "tma"], default="tma",
                     help="int8 pass: register-window strips or shared-memory tiles staged by "
                          "bulk (TMA) copies")
-    ap.add_argument("--workload", choices=["scan", "batched", "serving", "philox"],
+    ap.add_argument("--workload", choices=["scan", "batched", "serving", "philox", "small"],
                     default="scan",
                     help="scan: the 2D L=8192 beta scan (default line); batched: 2048 "
                          "lattices in one launch vs one launch per lattice; serving: Poisson "
@@ -536,6 +605,8 @@ def main():
         return run_serving_workload(args)
     if args.workload == "philox" and args.impl != "reference":
         return run_philox_workload(args)
+    if args.workload == "small" and args.impl != "reference":
+        return run_small_workload(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_gpu(args, world, rank, local)

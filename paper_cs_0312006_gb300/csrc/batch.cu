@@ -86,8 +86,14 @@ __device__ __forceinline__ void job_pass(const BatchJob& j, int c, uint32_t t, u
         g.half = j.half;
         const uint32_t vecs = (j.half + 15u) >> 4;
         int m_neg = 0, n_sites = 0;
-        for (uint32_t v = rank; v < vecs; v += nthr)
-            int8_vec<DIMS, MEASURE, NC>(a, g, v, e_acc, m_neg, n_sites);
+        if (j.W >= 64 && vecs >= nthr) {
+            for (uint32_t v = rank; v < vecs; v += nthr)
+                int8_vec<DIMS, MEASURE, NC>(a, g, v, e_acc, m_neg, n_sites);
+        } else {  // short rows or few vectors: four sites per item spread further
+            const uint32_t words = (j.half + 3u) >> 2;
+            for (uint32_t w = rank; w < words; w += nthr)
+                int8_word<DIMS, MEASURE, NC>(a, g, w, e_acc, m_neg, n_sites);
+        }
         if (MEASURE) m_acc += n_sites - 2 * m_neg;
     } else {
         const uint32_t items = j.rows * (((uint32_t)j.W + 31u) >> 5);
@@ -625,3 +631,48 @@ int ising_batch_run_static(ising_lattice* const* lats, int n, const int64_t* swe
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Small lattices through ising_sweep: with a few thousand sites a colour pass
+// lasts less than its launch, so n sweeps run as one job on a single CTA (the
+// same arithmetic and draws; passes separated by __syncthreads) instead of 2n
+// launches.  The job travels by value and lives in shared memory.
+// ----------------------------------------------------------------------------
+namespace ising {
+
+namespace {
+
+__global__ void __launch_bounds__(256, 1) small_job_kernel(BatchJob job) {
+    __shared__ BatchJob sj;
+    if (threadIdx.x == 0) sj = job;
+    __syncthreads();
+    dispatch_job<kModeCta>(&sj, threadIdx.x, blockDim.x, threadIdx.x == 0);
+}
+
+}  // namespace
+
+int small_sweep(ising_lattice* h, int64_t n, int every, unsigned long long* slots) {
+    BatchJob j;
+    j.col0 = h->col[0];
+    j.col1 = h->col[1];
+    j.obs = slots;
+    j.thr0 = h->thr[0];
+    j.thr1 = h->thr[1];
+    j.thr2 = h->thr[2];
+    j.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
+    j.key1 = (uint32_t)(h->seed >> 32);
+    j.t0 = (uint32_t)h->t;
+    j.dims = h->dims;
+    j.layout = h->layout;
+    j.L = h->L;
+    j.W = h->W;
+    j.rows = (uint32_t)h->rows;
+    j.half = (uint32_t)h->half_sites;
+    j.nsweeps = (int32_t)n;
+    j.measure_every = every;
+    small_job_kernel<<<1, 256, 0, h->stream>>>(j);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e);
+}
+
+}  // namespace ising

@@ -107,6 +107,7 @@ void free_device(ising_lattice* h) {
     if (h->obs) cudaFree(h->obs);
     h->obs = nullptr;
     h->obs_cap = 0;
+
 }
 
 // Record slots at index >= n_rec are kept zero, so a sweep call never needs
@@ -277,6 +278,13 @@ int ising_sweep(ising_lattice* h, int64_t n, int measure_every) {
         if (rc != ISING_OK) return rc;
     }
     int64_t rec = h->n_rec;
+    if (h->sites <= kSmallSites && n >= 2 && n <= 0x7FFFFFFF) {
+        const int rc = small_sweep(h, n, measure_every, h->obs ? h->obs + 2 * rec : nullptr);
+        if (rc != ISING_OK) return rc;
+        h->t += (uint64_t)n;
+        h->n_rec = rec + new_rec;
+        return ISING_OK;
+    }
     for (int64_t s = 0; s < n; ++s) {
         const uint64_t t = h->t + (uint64_t)s;
         unsigned long long* slot = nullptr;

@@ -47,6 +47,9 @@ struct DeviceProps {
 int cuda_fail(cudaError_t e);
 int device_props(const DeviceProps** out);
 int ensure_records(ising_lattice* h, int64_t need);
+// n sweeps of a small lattice in one persistent single-CTA launch (batch.cu)
+int small_sweep(ising_lattice* h, int64_t n, int every, unsigned long long* slots);
+constexpr int64_t kSmallSites = 16384;  // at or below: the single-launch path
 constexpr uint64_t kMaxSweep = 0xFFFFFFFFull;  // the sweep index is a 32-bit counter word
 
 // int8 layout (sweep_int8.cu)

@@ -1,0 +1,48 @@
+"""The bench's multi-rank logic on the CPU with two gloo ranks: every rank
+learns the slowest rank's time (the whole job's time), and the ranks' lattice
+seeds do not collide (independent replicas, no data-path collective)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t = bench.max_over_ranks(1.5 + rank, world)  # rank 1 is the slow one
+    seeds = [bench.BASE_SEED + 16 * rank + j for j in range(16)]
+    out.put((rank, t, seeds))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_the_slowest_time():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert sorted(t for _, t, _ in got) == [2.5, 2.5]
+    seeds = [s for _, _, ss in got for s in ss]
+    assert len(set(seeds)) == len(seeds) == 32
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(3.25, 1) == 3.25
+    assert bench.measured_traffic("int8", 10) in (None, pytest.approx(
+        bench.TRAFFIC["int8"]["bytes_per_update"] * 10 if bench.TRAFFIC["int8"]["bytes_per_update"] else 0))
