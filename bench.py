@@ -531,6 +531,40 @@ def run_small_workload(args):
     return 0 if exact else 1
 
 
+def run_cubic_workload(args):
+    """3D cubic L=256 (16.8 M sites) at beta 0.2216544, hot start, seed
+    20031109, 1000 sweeps with E/M every 10 sweeps, in both layouts."""
+    import torch
+    from paper_cs_0312006_gb300 import _build, engine
+    _build.build()
+    engine.load_library()
+    L, beta, n = args.cubic_L, 0.2216544, args.cubic_sweeps
+    sites = L ** 3
+    out = {}
+    for name, lay in (("int8", engine.INT8), ("bitpack", engine.BITPACK)):
+        lat = engine.Lattice(3, L, beta, BASE_SEED, layout=lay)
+        lat.sweep(3, 10)  # warm-up
+        torch.cuda.synchronize()
+        lat.init(engine.HOT)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lat.sweep(n, 10)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        E, M = lat.observables()
+        lat.close()
+        out[name] = {"value": sites * n / (ms / 1e3), "ms": ms, "records": len(E),
+                     "us_per_sweep": ms * 1e3 / n}
+    total = 2 * sites * n / ((out["int8"]["ms"] + out["bitpack"]["ms"]) / 1e3)
+    line = {"metric": "site updates/s", "value": total, "unit": "site updates/s",
+            "workload": f"3D cubic L={L}, beta 0.2216544, hot start, {n} sweeps, E/M every 10 "
+                        "sweeps, int8 and bit-packed layouts",
+            "layouts": out, "device": torch.cuda.get_device_name()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_philox_workload(args):
     """Throughput of the device generator alone (ising_philox_fill): the
     ceiling that the Metropolis draws put on any pass kernel."""
@@ -573,7 +607,8 @@ def main():
     ap.add_argument("--int8-kernel", choices=["strip", "tma"], default="tma",
                     help="int8 pass: register-window strips or shared-memory tiles staged by "
                          "bulk (TMA) copies")
-    ap.add_argument("--workload", choices=["scan", "batched", "serving", "philox", "small"],
+    ap.add_argument("--workload", choices=["scan", "batched", "serving", "philox", "small",
+                                           "cubic"],
                     default="scan",
                     help="scan: the 2D L=8192 beta scan (default line); batched: 2048 "
                          "lattices in one launch vs one launch per lattice; serving: Poisson "
@@ -582,6 +617,8 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=500)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batched: fixed launch shape")
+    ap.add_argument("--cubic-L", type=int, default=256)
+    ap.add_argument("--cubic-sweeps", type=int, default=1000)
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--hbm-budget-gb", type=float, default=120.0)
@@ -607,6 +644,8 @@ def main():
         return run_philox_workload(args)
     if args.workload == "small" and args.impl != "reference":
         return run_small_workload(args)
+    if args.workload == "cubic" and args.impl != "reference":
+        return run_cubic_workload(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_gpu(args, world, rank, local)

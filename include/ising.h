@@ -48,7 +48,7 @@ enum {
 
 /* Kernels for the int8 colour pass (same results; see ising_set_kernel). */
 enum {
-    ISING_KERNEL_AUTO = 0,  /* the staged kernel where it applies (measured faster) */
+    ISING_KERNEL_AUTO = 0,  /* staged for 2D with L >= 4096, strip otherwise (measured) */
     ISING_KERNEL_STRIP = 1, /* per-thread row strips, neighbour rows in registers */
     ISING_KERNEL_TMA = 2    /* tiles staged in shared memory by bulk (TMA) copies */
 };

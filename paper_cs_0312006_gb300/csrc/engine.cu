@@ -165,7 +165,12 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     a.c = c;
     if (h->layout == ISING_BITPACK)
         ISING_CHECK(ising::packed_pass(a, h->dims, slot != nullptr, *h->dp, h->stream));
-    else if (h->kernel != ISING_KERNEL_STRIP && ising::int8_tma_ok(h->dims, h->L))
+    else if (ising::int8_tma_ok(h->dims, h->L) &&
+             (h->kernel == ISING_KERNEL_TMA ||
+              // AUTO: the staged kernel where it measured faster (2D, long rows);
+              // with short rows (3D, small 2D) its tiles hold about one vector
+              // per thread and barriers dominate, so the strip kernel runs
+              (h->kernel == ISING_KERNEL_AUTO && h->dims == 2 && h->L >= 4096)))
         ISING_CHECK(ising::int8_pass_tma(a, h->dims, slot != nullptr, *h->dp, h->dp->d_err,
                                          g_inject_timeout.load() ? 16u : 0u, h->stream));
     else

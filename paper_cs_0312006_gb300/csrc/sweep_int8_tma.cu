@@ -32,7 +32,17 @@ namespace ising {
 namespace {
 
 constexpr int kStages = 2;
-constexpr int kTileRows = 2;
+
+// Rows per tile: about 8 KiB of own-colour rows (two rows of a 2D L = 8192
+// lattice, which measured best there against 1, 4 and 8), at least 2 and at
+// most 32 rows, a power of two that divides L.
+__host__ __device__ inline int tile_rows(int L) {
+    const int W = L / 2;
+    int R = 2;
+    while (R < 32 && 2 * R * W <= 8192 && L % (2 * R) == 0) R *= 2;
+    while (R > 1 && L % R != 0) R >>= 1;
+    return R;
+}
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // give up on a phase after ~1 s
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -222,11 +232,10 @@ cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uin
     TmaGeom tg;
     tg.extra_tx = extra_tx;
     const int planes = DIMS == 3 ? a.L : 1;
-    // two rows per tile and 256 threads measured best on GB300 (2D L=8192:
-    // 44.7 us per pass, against 49 us with four rows and 55 us with eight)
-    int R = kTileRows;
+    // tile_rows() and 256 threads measured best on GB300 (2D L=8192: 44.7 us
+    // per pass with two rows, against 49 us with four and 55 us with eight)
+    const int R = tile_rows(a.L);
     const int threads = 256;
-    while (R > 1 && (a.L % R != 0)) R >>= 1;
     tg.R = R;
     tg.bands = a.L / R;
     tg.tiles = tg.bands * planes;
@@ -260,8 +269,7 @@ cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uin
 bool int8_tma_ok(int dims, int L) {
     const int W = L / 2;
     if (W % 16 != 0) return false;
-    int R = kTileRows;
-    while (R > 1 && (L % R != 0)) R >>= 1;
+    const int R = tile_rows(L);
     const size_t stage = (size_t)(2 * R + 2) * W + (dims == 3 ? 2u * R * W : 0u);
     return (size_t)kStages * stage <= 200 * 1024;
 }
