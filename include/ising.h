@@ -195,7 +195,7 @@ void ising_destroy(ising_lattice *lat);
 typedef struct ising_batch ising_batch; /* opaque */
 
 typedef struct ising_batch_opts {
-    int block_threads;  /* threads per CTA: 128, 256 or 512 (0: 256) */
+    int block_threads;  /* threads per CTA: 128 or 256 (0: 256) */
     int cluster_size;   /* CTAs per cluster for large lattices, 1..8 (0: 4);
                            1 runs every lattice on a single CTA */
     int64_t big_sites;  /* size threshold of the cluster queue (0: 2^18) */

