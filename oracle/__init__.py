@@ -30,7 +30,8 @@ _lock = threading.Lock()
 _lib = None
 
 HOT, COLD_UP, COLD_DOWN = 0, 1, 2
-CHECKERBOARD, SEQUENTIAL = 0, 1
+CHECKERBOARD, SEQUENTIAL, HEATBATH = 0, 1, 2
+METROPOLIS_RULE, HEATBATH_RULE = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -71,6 +72,11 @@ def _load():
                                        ctypes.c_uint64, u32p, ctypes.c_uint32,
                                        ctypes.c_int]
         lib.orc_half_sweep.restype = ctypes.c_int
+        lib.orc_half_sweep_rule.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64,
+                                            u32p, ctypes.c_uint32, ctypes.c_int, ctypes.c_int]
+        lib.orc_half_sweep_rule.restype = ctypes.c_int
+        lib.orc_thresholds_heatbath.argtypes = [ctypes.c_int, ctypes.c_double, u32p]
+        lib.orc_thresholds_heatbath.restype = ctypes.c_int
         lib.orc_sweep.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64,
                                   u32p, ctypes.c_uint32]
         lib.orc_sweep.restype = ctypes.c_int
@@ -114,6 +120,16 @@ def thresholds(dims: int, beta: float) -> np.ndarray:
     return thr
 
 
+def thresholds_heatbath(dims: int, beta: float) -> np.ndarray:
+    """Heat-bath flip thresholds thb[d] = floor(2^32 / (1 + exp(4 beta (dims - d))))
+    for d = 0..2*dims disagreeing neighbours (7 entries, unused ones 0)."""
+    thb = np.zeros(7, dtype=np.uint32)
+    rc = _load().orc_thresholds_heatbath(dims, float(beta), _ptr(thb, ctypes.c_uint32))
+    if rc != 0:
+        raise ValueError(f"orc_thresholds_heatbath(dims={dims}, beta={beta!r}) -> {rc}")
+    return thb
+
+
 def init(dims: int, L: int, seed: int, start: int = HOT) -> np.ndarray:
     """Initial state in canonical order (x fastest), int8 +-1."""
     s = np.zeros(n_sites(dims, L), dtype=np.int8)
@@ -134,12 +150,15 @@ def magnetization(dims: int, L: int, s: np.ndarray) -> int:
 
 
 def half_sweep(dims: int, L: int, s: np.ndarray, seed: int, thr: np.ndarray,
-               t: int, c: int) -> None:
-    """One colour pass, in place on the canonical int8 array ``s``."""
+               t: int, c: int, rule: int = METROPOLIS_RULE) -> None:
+    """One colour pass, in place on the canonical int8 array ``s`` (``thr``:
+    Metropolis thresholds, or heat-bath thresholds with rule=HEATBATH_RULE)."""
     assert s.dtype == np.int8 and s.flags.c_contiguous
-    thr = np.ascontiguousarray(thr, dtype=np.uint32)
-    rc = _load().orc_half_sweep(dims, L, _ptr(s, ctypes.c_int8), seed,
-                                _ptr(thr, ctypes.c_uint32), t, c)
+    src = np.asarray(thr, dtype=np.uint32).ravel()
+    tab = np.zeros(7, dtype=np.uint32)
+    tab[:min(7, src.size)] = src[:7]
+    rc = _load().orc_half_sweep_rule(dims, L, _ptr(s, ctypes.c_int8), seed,
+                                     _ptr(tab, ctypes.c_uint32), t, c, rule)
     if rc != 0:
         raise ValueError(f"orc_half_sweep -> {rc}")
 
@@ -157,8 +176,9 @@ def sweep(dims: int, L: int, s: np.ndarray, seed: int, thr: np.ndarray,
 
 def run(dims: int, L: int, beta: float, seed: int, nsweeps: int,
         measure_every: int = 1, start: int = HOT, s: np.ndarray | None = None,
-        t0: int = 0, sequential: bool = False):
-    """Run ``nsweeps`` sweeps numbered t0, t0+1, ...
+        t0: int = 0, sequential: bool = False, heatbath: bool = False):
+    """Run ``nsweeps`` sweeps numbered t0, t0+1, ... (checkerboard Metropolis,
+    sequential Metropolis, or checkerboard heat bath).
 
     Returns (s, E, M): the final canonical state and the int64 energy and
     magnetisation recorded after every sweep t with (t+1) % measure_every == 0.
@@ -171,8 +191,9 @@ def run(dims: int, L: int, beta: float, seed: int, nsweeps: int,
     E = np.zeros(cap, dtype=np.int64)
     M = np.zeros(cap, dtype=np.int64)
     n = _load().orc_run(dims, L, float(beta), seed, _ptr(s, ctypes.c_int8), t0,
-                        nsweeps, measure_every, SEQUENTIAL if sequential else
-                        CHECKERBOARD, _ptr(E, ctypes.c_int64),
+                        nsweeps, measure_every,
+                        HEATBATH if heatbath else (SEQUENTIAL if sequential else CHECKERBOARD),
+                        _ptr(E, ctypes.c_int64),
                         _ptr(M, ctypes.c_int64), cap)
     if n < 0:
         raise ValueError(f"orc_run -> {n}")

@@ -149,12 +149,15 @@ def state_energy(s, nb_fwd) -> int:
     return -int(sum(s[i] * sum(s[j] for j in nb_fwd[i]) for i in range(len(s))))
 
 
-def half_sweep_matrix(dims: int, L: int, thr, colour: int) -> np.ndarray:
+def half_sweep_matrix(dims: int, L: int, thr, colour: int,
+                      heatbath: bool = False) -> np.ndarray:
     """P[a, b] = probability that one colour pass maps state a to state b.
 
     Each site of the colour flips independently (its neighbours all have the
-    other colour) with probability 1 if k <= 0 and thr[k/2 - 1] / 2^32 if
-    k > 0, k = s_i * (sum of its 2*dims neighbours).
+    other colour).  Metropolis: with probability 1 if k <= 0 and
+    thr[k/2 - 1] / 2^32 if k > 0, k = s_i * (sum of its 2*dims neighbours).
+    Heat bath: with probability thr[d] / 2^32, d = (2*dims - k)/2 the number
+    of disagreeing neighbours.
     """
     n = L ** dims
     coords = _coords(dims, L)
@@ -166,7 +169,10 @@ def half_sweep_matrix(dims: int, L: int, thr, colour: int) -> np.ndarray:
         probs = []
         for i in sites:
             k = int(s[i] * sum(s[j] for j in nb[i]))
-            probs.append(1.0 if k <= 0 else float(thr[k // 2 - 1]) / 2.0 ** 32)
+            if heatbath:
+                probs.append(float(thr[(2 * dims - k) // 2]) / 2.0 ** 32)
+            else:
+                probs.append(1.0 if k <= 0 else float(thr[k // 2 - 1]) / 2.0 ** 32)
         for mask in range(2 ** len(sites)):
             b, pr = a, 1.0
             for bit, i in enumerate(sites):
@@ -226,3 +232,16 @@ def exact_thresholds(dims: int, beta: float, dps: int = 50) -> list:
         for k in range(2, 2 * dims + 1, 2):
             out.append(int(mpmath.floor(mpmath.exp(-2 * b * k) * mpmath.mpf(2) ** 32)))
     return out
+
+
+def exact_thresholds_heatbath(dims: int, beta: float, dps: int = 50) -> list:
+    """floor(2^32 / (1 + exp(2 beta k))) for d = 0, .., 2*dims disagreeing
+    neighbours, k = 2(dims - d) the energy-change numerator (dE = 2k), padded
+    with zeros to 7 entries; beta is the exact binary value of the double."""
+    out = []
+    with mpmath.workdps(dps):
+        b = mpmath.mpf(beta)
+        for d in range(2 * dims + 1):
+            k = 2 * (dims - d)
+            out.append(int(mpmath.floor(mpmath.mpf(2) ** 32 / (1 + mpmath.exp(2 * b * k)))))
+    return out + [0] * (7 - len(out))

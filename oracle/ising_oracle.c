@@ -125,6 +125,63 @@ int orc_thresholds(int dims, double beta, uint32_t thr[3])
 }
 
 /* ------------------------------------------------------------------------ */
+/* Heat-bath thresholds (the alternative acceptance rule: each visited spin */
+/* takes its conditional Boltzmann distribution given its neighbours, so    */
+/* it flips with probability 1 / (1 + exp(beta dE)) = 1/(1 + exp(2 beta k))). */
+/* Indexed by the number d = 0..2*dims of disagreeing neighbours, with      */
+/* k = 2(dims - d): thb[d] = floor(2^32 / (1 + exp(4 beta (dims - d)))).     */
+/* thb[dims] = 2^31 exactly.  Same exact-floor safeguards as above.         */
+/* ------------------------------------------------------------------------ */
+/* Two exact forms of the same number are used, each where it keeps full    */
+/* relative precision: with x = 4 beta |dims - d| > 0,                      */
+/*   2^32 / (1 + e^{+-x}) = 2^31 -+ delta,  delta = 2^31 tanh(x / 2),        */
+/*   and for large x the small side 2^32 / (1 + e^x) directly.              */
+static int heatbath_floor(int m, long double x, int wide, uint32_t *out)
+{
+    /* m > 0: floor(2^31 - delta); m < 0: floor(2^31 + delta)               */
+    long double delta = wide ? ldexpl(tanhl(x / 2.0L), 31)
+                             : (long double)ldexp(tanh((double)x / 2.0), 31);
+    if (delta < 1073741824.0L) {           /* delta < 2^30: use delta      */
+        if (delta < 1.0L) { *out = m > 0 ? 0x7FFFFFFFu : 0x80000000u; return 0; }
+        long double f = delta - floorl(delta);
+        if (f < (wide ? 0x1p-24L : 0x1p-16L) || f > 1.0L - (wide ? 0x1p-24L : 0x1p-16L))
+            return 1;
+        uint32_t fl = (uint32_t)floorl(delta);   /* delta not an integer    */
+        *out = m > 0 ? 0x80000000u - fl - 1u : 0x80000000u + fl;
+        return 0;
+    }
+    long double small = wide ? ldexpl(1.0L / (1.0L + expl(x)), 32)
+                             : (long double)ldexp(1.0 / (1.0 + exp((double)x)), 32);
+    if (small < 1.0L) { *out = m > 0 ? 0u : 0xFFFFFFFFu; return 0; }
+    long double f = small - floorl(small);
+    if (f < (wide ? 0x1p-24L : 0x1p-16L) || f > 1.0L - (wide ? 0x1p-24L : 0x1p-16L))
+        return 1;
+    uint32_t fl = (uint32_t)floorl(small);       /* small not an integer    */
+    *out = m > 0 ? fl : 0xFFFFFFFFu - fl;        /* floor(2^32 - small)     */
+    return 0;
+}
+
+int orc_thresholds_heatbath(int dims, double beta, uint32_t thb[7])
+{
+    if (dims != 2 && dims != 3) return -1;
+    if (!(beta > 0.0)) return -1;
+    for (int d = 0; d < 7; ++d) thb[d] = 0;
+    for (int d = 0; d <= 2 * dims; ++d) {
+        int m = dims - d; /* k / 2 */
+        if (m == 0) { thb[d] = 0x80000000u; continue; }
+        int am = m > 0 ? m : -m;
+        if (isinf(beta) || 4.0 * beta * am > 800.0) {
+            thb[d] = m > 0 ? 0u : 0xFFFFFFFFu;
+            continue;
+        }
+        long double x = 4.0L * (long double)beta * (long double)am;
+        if (heatbath_floor(m, x, 0, &thb[d]) == 0) continue;
+        if (heatbath_floor(m, x, 1, &thb[d]) != 0) return -2;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Lattice geometry                                                         */
 /* ------------------------------------------------------------------------ */
 
@@ -221,6 +278,18 @@ static int accept_flip(int k, const uint32_t thr[3], uint64_t seed,
     return u < thr[k / 2 - 1];
 }
 
+/* The heat-bath decision: every visited site draws; it flips iff its draw  */
+/* is below thb[d], d = (2*dims - k) / 2 the number of disagreeing          */
+/* neighbours.                                                              */
+static int heatbath_flip(int dims, int k, const uint32_t thb[7], uint64_t seed,
+                         uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                         unsigned w)
+{
+    int d = (2 * dims - k) / 2;
+    uint32_t u = draw_word(seed, c0, c1, c2, c3, w);
+    return u < thb[d];
+}
+
 /* ------------------------------------------------------------------------ */
 /* One colour pass (Sec. 2.2: "a pass through all white or all black        */
 /* sites").  Every site i of colour c is visited; it reads only sites of    */
@@ -228,8 +297,8 @@ static int accept_flip(int k, const uint32_t thr[3], uint64_t seed,
 /* Draw for site i in sweep t: Philox(seed; hh>>2, t, c, TAG_SWEEP)[hh & 3] */
 /* with hh = i >> 1 (the site's index within its colour).  Requires L even. */
 /* ------------------------------------------------------------------------ */
-int orc_half_sweep(int dims, int L, int8_t *s, uint64_t seed,
-                   const uint32_t thr[3], uint32_t t, int c)
+int orc_half_sweep_rule(int dims, int L, int8_t *s, uint64_t seed,
+                        const uint32_t *thr, uint32_t t, int c, int rule)
 {
     if (dims != 2 && dims != 3) return -1;
     if (L < 2 || (L & 1)) return -1;
@@ -244,20 +313,36 @@ int orc_half_sweep(int dims, int L, int8_t *s, uint64_t seed,
                 int h = neighbour_sum(dims, L, s, x, y, z);
                 int k = s[i] * h;
                 int64_t hh = i >> 1;
-                if (accept_flip(k, thr, seed, (uint32_t)(hh >> 2), t,
-                                (uint32_t)c, TAG_SWEEP, (unsigned)(hh & 3)))
-                    s[i] = (int8_t)-s[i];
+                int flip = rule == 0
+                    ? accept_flip(k, thr, seed, (uint32_t)(hh >> 2), t, (uint32_t)c,
+                                  TAG_SWEEP, (unsigned)(hh & 3))
+                    : heatbath_flip(dims, k, thr, seed, (uint32_t)(hh >> 2), t,
+                                    (uint32_t)c, TAG_SWEEP, (unsigned)(hh & 3));
+                if (flip) s[i] = (int8_t)-s[i];
             }
     return 0;
 }
 
+/* Metropolis colour pass (rule 0). */
+int orc_half_sweep(int dims, int L, int8_t *s, uint64_t seed,
+                   const uint32_t thr[3], uint32_t t, int c)
+{
+    return orc_half_sweep_rule(dims, L, s, seed, thr, t, c, 0);
+}
+
 /* One sweep = black pass (colour 0) then white pass (colour 1). */
+int orc_sweep_rule(int dims, int L, int8_t *s, uint64_t seed,
+                   const uint32_t *thr, uint32_t t, int rule)
+{
+    int rc = orc_half_sweep_rule(dims, L, s, seed, thr, t, 0, rule);
+    if (rc) return rc;
+    return orc_half_sweep_rule(dims, L, s, seed, thr, t, 1, rule);
+}
+
 int orc_sweep(int dims, int L, int8_t *s, uint64_t seed,
               const uint32_t thr[3], uint32_t t)
 {
-    int rc = orc_half_sweep(dims, L, s, seed, thr, t, 0);
-    if (rc) return rc;
-    return orc_half_sweep(dims, L, s, seed, thr, t, 1);
+    return orc_sweep_rule(dims, L, s, seed, thr, t, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -291,21 +376,24 @@ int orc_sweep_sequential(int dims, int L, int8_t *s, uint64_t seed,
 /* and magnetisation (recomputed from scratch) are recorded iff             */
 /* (t + 1) % measure_every == 0.  Writes at most cap records and returns    */
 /* their number (or a negative error).  mode 0 = checkerboard, 1 =          */
-/* sequential.  The state s is updated in place.                            */
+/* sequential, 2 = checkerboard heat bath.  The state s is updated in place. */
 /* ------------------------------------------------------------------------ */
 int64_t orc_run(int dims, int L, double beta, uint64_t seed, int8_t *s,
                 uint32_t t0, int64_t nsweeps, int measure_every, int mode,
                 int64_t *E, int64_t *M, int64_t cap)
 {
-    uint32_t thr[3];
-    int rc = orc_thresholds(dims, beta, thr);
+    /* mode 0: checkerboard Metropolis; 1: sequential Metropolis;
+       2: checkerboard heat bath */
+    uint32_t thr[7];
+    int rc = mode == 2 ? orc_thresholds_heatbath(dims, beta, thr)
+                       : orc_thresholds(dims, beta, thr);
     if (rc) return rc;
     if (measure_every < 1 || nsweeps < 0) return -1;
     int64_t nrec = 0;
     for (int64_t n = 0; n < nsweeps; ++n) {
         uint32_t t = t0 + (uint32_t)n;
-        rc = mode == 0 ? orc_sweep(dims, L, s, seed, thr, t)
-                       : orc_sweep_sequential(dims, L, s, seed, thr, t);
+        rc = mode == 1 ? orc_sweep_sequential(dims, L, s, seed, thr, t)
+                       : orc_sweep_rule(dims, L, s, seed, thr, t, mode == 2 ? 1 : 0);
         if (rc) return rc;
         if (((uint64_t)t + 1) % (uint64_t)measure_every == 0) {
             if (nrec < cap) {
