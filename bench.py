@@ -27,6 +27,10 @@ Arms
 
 Multi-GPU (torchrun): every rank runs its own 16 independent lattices (seeds
 offset by 16 * rank), no collective on the data path; scaling "weak".
+
+--rule heatbath runs the same workload with the heat-bath update rule (every
+site draws; flip iff u < floor(2^32 / (1 + exp(beta dE)))) instead of the
+Metropolis rule, in the engine and in the oracle arms alike.
 """
 from __future__ import annotations
 
@@ -71,8 +75,10 @@ def kernel_sources_sha1(names) -> str:
     return h.hexdigest()
 
 
-def measured_traffic(layout: str, updates_per_launch: int):
+def measured_traffic(layout: str, updates_per_launch: int, rule: str = "metropolis"):
     t = TRAFFIC[layout]
+    if rule != "metropolis":  # the capture covers the Metropolis instances only
+        return None
     if t["bytes_per_update"] is None or kernel_sources_sha1(t["sources"]) != t["sha1"]:
         return None
     return t["bytes_per_update"] * updates_per_launch
@@ -93,10 +99,13 @@ def scan_betas():
     return [round(0.30 + 0.02 * j, 10) for j in range(N_BETA)]
 
 
-def workload_config(L: int, steps: int, lattices: int = N_BETA) -> dict:
-    return {"workload": f"2D Ising beta scan: L={L} square lattice, 16 betas evenly spaced in "
-                        f"[0.30,0.60], cold start, {steps} sweeps, E/M every sweep, int8 and "
-                        f"bit-packed layouts",
+def workload_config(L: int, steps: int, lattices: int = N_BETA,
+                    rule: str = "metropolis") -> dict:
+    name = "checkerboard Metropolis" if rule == "metropolis" else "checkerboard heat-bath"
+    return {"workload": f"2D Ising beta scan ({name}): L={L} square lattice, 16 betas evenly "
+                        f"spaced in [0.30,0.60], cold start, {steps} sweeps, E/M every sweep, "
+                        f"int8 and bit-packed layouts",
+            "rule": rule,
             "lattices_per_gpu": lattices,
             "l2": f"inputs larger than L2: a step touches {lattices} x L^2 bytes of int8 spins",
             "step": "one sweep (black pass, white pass, fused E/M) of each lattice"}
@@ -177,7 +186,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(budget_s: float, L: int, betas, n_lattices: int):
+def oracle_sample_rate(budget_s: float, L: int, betas, n_lattices: int, heatbath: bool = False):
     """Time the oracle (as it stands) sweeping cold-started lattices of size L
     with E/M recomputed after each sweep; returns (updates/s, description)."""
     import oracle
@@ -188,13 +197,14 @@ def oracle_sample_rate(budget_s: float, L: int, betas, n_lattices: int):
     while True:
         b = betas[j % len(betas)]
         oracle.run(2, L, b, BASE_SEED + (j % len(betas)), 1, measure_every=1,
-                   start=oracle.COLD_UP)
+                   start=oracle.COLD_UP, heatbath=heatbath)
         done += L * L
         j += 1
         if time.perf_counter() - t0 >= budget_s or j >= n_lattices:
             break
     dt = time.perf_counter() - t0
-    return done / dt, f"{j} single sweeps (cold start, E/M after each) of 2D L={L} lattices"
+    return done / dt, (f"{j} single sweeps (cold start, E/M after each) of 2D L={L} lattices"
+                       + (", heat-bath rule" if heatbath else ""))
 
 
 def run_reference(args, world, rank):
@@ -209,13 +219,15 @@ def run_reference(args, world, rank):
         L //= 2
     import oracle
     oracle.build()
+    hb = args.rule == "heatbath"
     for w in range(args.warmup):
         oracle.run(2, L, betas[w % N_BETA], BASE_SEED + w, 1, measure_every=1,
-                   start=oracle.COLD_UP)
+                   start=oracle.COLD_UP, heatbath=hb)
     t0 = time.perf_counter()
     for k in range(args.steps):
         j = k % N_BETA
-        oracle.run(2, L, betas[j], BASE_SEED + j, 1, measure_every=1, start=oracle.COLD_UP)
+        oracle.run(2, L, betas[j], BASE_SEED + j, 1, measure_every=1, start=oracle.COLD_UP,
+                   heatbath=hb)
     dt = time.perf_counter() - t0
     value = args.steps * L * L / dt
     sample = (f"each step: one sweep (cold start, E/M recomputed) of one 2D L={L} lattice "
@@ -226,7 +238,7 @@ def run_reference(args, world, rank):
         "unit": "site updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-        "config": workload_config(args.L, args.steps, args.lattices),
+        "config": workload_config(args.L, args.steps, args.lattices, args.rule),
         "cpu_baseline": {"value": value, "unit": "site updates/s", "cores": 1,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "site updates/s", "h2d_bytes_per_step": 0,
@@ -268,8 +280,10 @@ def run_gpu(args, world, rank, local):
         layouts = [x for x in layouts if x[0] == args.layout]
     stream = torch.cuda.current_stream()
     int8_kernel = {"strip": engine.KERNEL_STRIP, "tma": engine.KERNEL_TMA}[args.int8_kernel]
+    rule = {"metropolis": engine.RULE_METROPOLIS, "heatbath": engine.RULE_HEATBATH}[args.rule]
     sets = {name: [engine.Lattice(2, L, b, BASE_SEED + 16 * rank + j, layout=lay,
-                                  start=engine.COLD_UP, stream=stream, kernel=int8_kernel)
+                                  start=engine.COLD_UP, stream=stream, kernel=int8_kernel,
+                                  rule=rule)
                    for j, b in enumerate(betas)] for name, lay in layouts}
 
     def barrier():
@@ -341,21 +355,24 @@ def run_gpu(args, world, rank, local):
         if name == "int8":
             bytes_per_pass = BYTES_PER_UPDATE_INT8 * updates_per_pass
             achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
-            kname = "pass_int8_tma<2,measure>" if args.int8_kernel == "tma" else \
-                "pass_int8_strip<2,measure>"
+            rtag = "" if args.rule == "metropolis" else ",heatbath"
+            kname = (f"pass_int8_tma<2,measure{rtag}>" if args.int8_kernel == "tma" else
+                     f"pass_int8_strip<2,measure{rtag}>")
             rooflines[name] = {"kernel": kname, "bound": "hbm",
                                "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                                "frac": achieved / peak_hbm,
-                               "traffic": measured_traffic("int8", updates_per_pass),
+                               "traffic": measured_traffic("int8", updates_per_pass, args.rule),
                                "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
                                "peak_source": f"{peak_kind} hbm_gbs (copy)"}
         else:
             peak = philox_alu_peak_sites_per_s(sm_count, sm_mhz)
             achieved = updates_per_pass / (pass_ms / 1e3)
-            rooflines[name] = {"kernel": "pass_packed<2,measure>", "bound": "alu",
+            rtag = "" if args.rule == "metropolis" else ",heatbath"
+            rooflines[name] = {"kernel": f"pass_packed<2,measure{rtag}>", "bound": "alu",
                                "achieved": achieved, "peak": peak, "unit": "site updates/s",
                                "frac": achieved / peak,
-                               "traffic": measured_traffic("bitpack", updates_per_pass),
+                               "traffic": measured_traffic("bitpack", updates_per_pass,
+                                                           args.rule),
                                "launch_ms": pass_ms,
                                "peak_source": "derived: SMs x 32 wide multiplies/clk / 18 per "
                                               "Philox call x 4 sites x median SM clock"}
@@ -401,7 +418,8 @@ def run_gpu(args, world, rank, local):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, sample = oracle_sample_rate(args.cpu_seconds, L_SCAN, betas, 64)
+        rate, sample = oracle_sample_rate(args.cpu_seconds, L_SCAN, betas, 64,
+                                          heatbath=args.rule == "heatbath")
         cpu = {"value": rate, "unit": "site updates/s", "cores": 1, "kind": "oracle",
                "sample": sample}
 
@@ -410,7 +428,7 @@ def run_gpu(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
         "data": "synthetic",
-        "config": workload_config(L, args.steps, len(betas)),
+        "config": workload_config(L, args.steps, len(betas), args.rule),
         "layouts": layout_stats,
         "roofline": rooflines.get("int8") or rooflines.get("bitpack"),
         "roofline_bitpack": rooflines.get("bitpack"),
@@ -604,6 +622,8 @@ def main():
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--L", type=int, default=L_SCAN)
     ap.add_argument("--layout", choices=["both", "int8", "bitpack"], default="both")
+    ap.add_argument("--rule", choices=["metropolis", "heatbath"], default="metropolis",
+                    help="local update rule of the scan workload")
     ap.add_argument("--int8-kernel", choices=["strip", "tma"], default="tma",
                     help="int8 pass: register-window strips or shared-memory tiles staged by "
                          "bulk (TMA) copies")

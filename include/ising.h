@@ -53,6 +53,23 @@ enum {
     ISING_KERNEL_TMA = 2    /* tiles staged in shared memory by bulk (TMA) copies */
 };
 
+/*
+ * Local update rules of a colour pass (see ising_set_rule).  Both visit the
+ * same sites with the same draw u per site and keep the Boltzmann
+ * distribution P(S) of Sec. 2.2 stationary.  With d the number of the site's
+ * 2*dims neighbours that disagree with it (dE = 4 (dims - d)):
+ *   METROPOLIS (Sec. 2.2, steps 1-4): d >= dims flips without a draw; otherwise
+ *       flip iff u < floor(exp(-beta dE) 2^32).
+ *   HEATBATH: the site takes its conditional Boltzmann distribution given its
+ *       neighbours, P(S') / (P(S) + P(S')) = 1 / (1 + exp(beta dE)) for the
+ *       flipped state: every site draws and flips iff
+ *       u < floor(2^32 / (1 + exp(4 beta (dims - d)))).
+ */
+enum {
+    ISING_RULE_METROPOLIS = 0,
+    ISING_RULE_HEATBATH = 1
+};
+
 /* Initial states (Sec. 2.2: spins up with probability p). */
 enum {
     ISING_HOT = 0,       /* p = 1/2: s_i = +1 iff Philox(seed; i>>2, 0, 0, 1)[i&3] < 2^31 */
@@ -75,7 +92,7 @@ typedef struct ising_info_t {
     int dims;              /* 2 or 3 */
     int L;                 /* linear size */
     int layout;            /* ISING_INT8 or ISING_BITPACK (never AUTO) */
-    int reserved;
+    int rule;              /* ISING_RULE_METROPOLIS or ISING_RULE_HEATBATH */
     double beta;           /* inverse temperature J/kT */
     uint64_t seed;         /* Philox key */
     uint64_t sweeps_done;  /* global sweep counter t (next sweep's index) */
@@ -91,9 +108,9 @@ typedef struct ising_info_t {
  *   L      even, >= 2 (odd L has no valid checkerboard on a torus: the wrap
  *          bond would join two sites of one colour); L^dims <= 2^32.
  *   beta   > 0 (may be +inf for a zero-temperature quench).  The thresholds
- *          floor(exp(-2 beta k) 2^32), k = 2..2*dims, are built on the host;
- *          a beta whose exact value lies within 2^-24 of an integer boundary
- *          at long-double precision is rejected with ISING_EINVAL.
+ *          of both rules (ISING_RULE_*) are built on the host; a beta for
+ *          which one of them lies too close to an integer boundary to decide
+ *          its floor at long-double precision is rejected with ISING_EINVAL.
  *   seed   64-bit Philox key (low word, high word).
  *   layout ISING_INT8, ISING_BITPACK or ISING_AUTO.
  * Allocates device memory; issues the init kernel on the default stream.
@@ -169,6 +186,18 @@ int ising_thresholds(const ising_lattice *lat, uint32_t out[3]);
  * beta whose floor cannot be decided as described at ising_create). */
 int ising_compute_thresholds(int dims, double beta, uint32_t out[3]);
 
+/* Select the local update rule (ISING_RULE_*) for the lattice's later
+ * sweeps; the default is ISING_RULE_METROPOLIS.  Both thresholds tables are
+ * built at ising_create, so this never fails for a valid handle and rule
+ * (ISING_EINVAL otherwise).  The sweep counter and records are unchanged. */
+int ising_set_rule(ising_lattice *lat, int rule);
+
+/* The heat-bath thresholds for (dims, beta) without a handle or a GPU:
+ * out[d] = floor(2^32 / (1 + exp(4 beta (dims - d)))) for d = 0..2*dims
+ * (out[dims] = 2^31), 0 beyond; out has 7 entries.  Errors as at
+ * ising_compute_thresholds. */
+int ising_compute_thresholds_heatbath(int dims, double beta, uint32_t out[7]);
+
 /* Describe the handle. */
 int ising_get_info(const ising_lattice *lat, ising_info_t *out);
 
@@ -211,7 +240,10 @@ typedef struct ising_batch_opts {
  * give a value >= 1 per lattice; opts may be NULL.  All lattices are moved to
  * `stream` (as by ising_set_stream).  The batch borrows the handles: between
  * ising_batch_launch and ising_batch_sync they must not be used directly, and
- * they must outlive the batch.  Device memory: a job table (64 B per lattice).
+ * they must outlive the batch.  Device memory: a job table (96 B per lattice).
+ * Lattices of each update rule (ISING_RULE_*) form their own queues, run by
+ * one persistent launch per rule present; a lattice's rule must not change
+ * while the batch exists (ising_batch_launch then returns ISING_EINVAL).
  */
 int ising_batch_create(ising_batch **out, ising_lattice *const *lats, int n,
                        const int64_t *sweeps, const int *measure_every,
@@ -242,7 +274,7 @@ void ising_batch_destroy(ising_batch *b);
  * allocates nothing: its work queue (job table, queue order, counters) lives
  * in one file-scope device array of fixed size, at most 2048 lattices per
  * call (more gives ISING_ERANGE before any work is issued); every GPU that
- * loads the library holds that array, about 168 KiB, until the process exits.
+ * loads the library holds that array, about 200 KiB, until the process exits.
  *
  *   lats, n        n distinct lattices of the current device (1 <= n <= 2048).
  *   sweeps         n sweep counts (>= 0).

@@ -42,12 +42,33 @@ struct BatchJob {
     void* col0;
     void* col1;
     unsigned long long* obs;  // (E, M) slots of this launch's records; zeroed
-    uint32_t thr0, thr1, thr2, key0, key1;
+    uint32_t thr[7];          // thresholds of the job's rule (PassArgs::thr)
+    uint32_t key0, key1;
     uint32_t t0;              // index of the job's next sweep
     int32_t dims, layout, L, W;
     uint32_t rows, half;
     int32_t nsweeps, measure_every;
 };
+
+// Everything but the record slots and the sweep count, from the lattice.
+static void fill_job(BatchJob& j, const ising_lattice* h, int64_t nsweeps, int every,
+                     unsigned long long* obs) {
+    j.col0 = h->col[0];
+    j.col1 = h->col[1];
+    j.obs = obs;
+    rule_thresholds(h, j.thr);
+    j.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
+    j.key1 = (uint32_t)(h->seed >> 32);
+    j.t0 = (uint32_t)h->t;
+    j.dims = h->dims;
+    j.layout = h->layout;
+    j.L = h->L;
+    j.W = h->W;
+    j.rows = (uint32_t)h->rows;
+    j.half = (uint32_t)h->half_sites;
+    j.nsweeps = (int32_t)nsweeps;
+    j.measure_every = every;
+}
 
 namespace {
 
@@ -61,7 +82,7 @@ __device__ __forceinline__ void group_sync() {
         __syncthreads();
 }
 
-template <int DIMS, int LAYOUT, bool MEASURE, int NC>
+template <int DIMS, int LAYOUT, bool MEASURE, int NC, int RULE>
 __device__ __forceinline__ void job_pass(const BatchJob& j, int c, uint32_t t, uint32_t rank,
                                          uint32_t nthr, int& e_acc, int& m_acc) {
     PassArgs a;
@@ -71,9 +92,8 @@ __device__ __forceinline__ void job_pass(const BatchJob& j, int c, uint32_t t, u
     a.rows = j.rows;
     a.L = j.L;
     a.W = j.W;
-    a.thr0 = j.thr0;
-    a.thr1 = j.thr1;
-    a.thr2 = j.thr2;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) a.thr[i] = j.thr[i];
     a.key0 = j.key0;
     a.key1 = j.key1;
     a.t = t;
@@ -88,21 +108,21 @@ __device__ __forceinline__ void job_pass(const BatchJob& j, int c, uint32_t t, u
         int m_neg = 0, n_sites = 0;
         if (j.W >= 64 && vecs >= nthr) {
             for (uint32_t v = rank; v < vecs; v += nthr)
-                int8_vec<DIMS, MEASURE, NC>(a, g, v, e_acc, m_neg, n_sites);
+                int8_vec<DIMS, MEASURE, NC, RULE>(a, g, v, e_acc, m_neg, n_sites);
         } else {  // short rows or few vectors: four sites per item spread further
             const uint32_t words = (j.half + 3u) >> 2;
             for (uint32_t w = rank; w < words; w += nthr)
-                int8_word<DIMS, MEASURE, NC>(a, g, w, e_acc, m_neg, n_sites);
+                int8_word<DIMS, MEASURE, NC, RULE>(a, g, w, e_acc, m_neg, n_sites);
         }
         if (MEASURE) m_acc += n_sites - 2 * m_neg;
     } else {
         const uint32_t items = j.rows * (((uint32_t)j.W + 31u) >> 5);
         for (uint32_t it = rank; it < items; it += nthr)
-            packed_word<DIMS, MEASURE, NC>(a, it, e_acc, m_acc);
+            packed_word<DIMS, MEASURE, NC, RULE>(a, it, e_acc, m_acc);
     }
 }
 
-template <int DIMS, int LAYOUT, int MODE>
+template <int DIMS, int LAYOUT, int MODE, int RULE>
 __device__ void run_job(BatchJob* jp, uint32_t rank, uint32_t nthr, bool leader) {
     constexpr int NC = MODE == kModeCluster ? 2 : 0;
     const BatchJob j = *jp;
@@ -113,9 +133,9 @@ __device__ void run_job(BatchJob* jp, uint32_t rank, uint32_t nthr, bool leader)
         int e = 0, m = 0;
         for (int c = 0; c < 2; ++c) {
             if (measure)
-                job_pass<DIMS, LAYOUT, true, NC>(j, c, t, rank, nthr, e, m);
+                job_pass<DIMS, LAYOUT, true, NC, RULE>(j, c, t, rank, nthr, e, m);
             else
-                job_pass<DIMS, LAYOUT, false, NC>(j, c, t, rank, nthr, e, m);
+                job_pass<DIMS, LAYOUT, false, NC, RULE>(j, c, t, rank, nthr, e, m);
             group_sync<MODE>();  // this pass's writes before the next pass reads them
         }
         if (measure) {
@@ -130,26 +150,31 @@ __device__ void run_job(BatchJob* jp, uint32_t rank, uint32_t nthr, bool leader)
     }
 }
 
-template <int MODE>
+template <int MODE, int RULE>
 __device__ void dispatch_job(BatchJob* jp, uint32_t rank, uint32_t nthr, bool leader) {
     const int dims = jp->dims, layout = jp->layout;
     if (dims == 2) {
         if (layout == ISING_BITPACK)
-            run_job<2, ISING_BITPACK, MODE>(jp, rank, nthr, leader);
+            run_job<2, ISING_BITPACK, MODE, RULE>(jp, rank, nthr, leader);
         else
-            run_job<2, ISING_INT8, MODE>(jp, rank, nthr, leader);
+            run_job<2, ISING_INT8, MODE, RULE>(jp, rank, nthr, leader);
     } else {
         if (layout == ISING_BITPACK)
-            run_job<3, ISING_BITPACK, MODE>(jp, rank, nthr, leader);
+            run_job<3, ISING_BITPACK, MODE, RULE>(jp, rank, nthr, leader);
         else
-            run_job<3, ISING_INT8, MODE>(jp, rank, nthr, leader);
+            run_job<3, ISING_INT8, MODE, RULE>(jp, rank, nthr, leader);
     }
 }
 
-// counters[0] / counters[1]: next index into the large / small queue.
+// counters[0] / counters[1]: next index into the large / small queue.  Every
+// job of the queues uses the update rule RULE: a batch with both rules runs
+// one launch per rule, so that each instance keeps its own register budget.
 // 256 threads and at most 80 registers (three CTAs per SM) measured 5 % faster
-// on the 2048-lattice workload than 126 registers at two per SM.
-__global__ void __launch_bounds__(256, 3) batch_kernel(BatchJob* jobs, const int* order_big,
+// on the 2048-lattice workload than 126 registers at two per SM.  The
+// heat-bath instance (every site draws, seven thresholds live) would spill at
+// 80 registers, so it keeps two CTAs per SM.
+template <int RULE>
+__global__ void __launch_bounds__(256, RULE == kRuleHeatBath ? 2 : 3) batch_kernel(BatchJob* jobs, const int* order_big,
                                                     int n_big, const int* order_small,
                                                     int n_small, int* counters) {
     __shared__ int s_job;
@@ -163,7 +188,7 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(BatchJob* jobs, const int
         const int j = *cl.map_shared_rank(&s_job, 0);
         cl.sync();
         if (j >= n_big) break;
-        dispatch_job<kModeCluster>(&jobs[order_big[j]], crank, cthreads, crank == 0);
+        dispatch_job<kModeCluster, RULE>(&jobs[order_big[j]], crank, cthreads, crank == 0);
     }
     // phase 2: small jobs, one CTA per job
     while (true) {
@@ -172,8 +197,52 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(BatchJob* jobs, const int
         __syncthreads();
         const int j = s_job;
         if (j >= n_small) break;
-        dispatch_job<kModeCta>(&jobs[order_small[j]], threadIdx.x, blockDim.x, threadIdx.x == 0);
+        dispatch_job<kModeCta, RULE>(&jobs[order_small[j]], threadIdx.x, blockDim.x,
+                                     threadIdx.x == 0);
     }
+}
+
+using BatchKernel = void (*)(BatchJob*, const int*, int, const int*, int, int*);
+
+BatchKernel batch_kernel_for(int rule) {
+    return rule == kRuleHeatBath ? batch_kernel<kRuleHeatBath> : batch_kernel<kRuleMetropolis>;
+}
+
+// Resident clusters of the persistent kernel of `rule` for a launch shape.
+cudaError_t resident_clusters(int rule, int threads, int cluster, int* out) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.gridDim = dim3((unsigned)(cluster * 1024));
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(out, batch_kernel_for(rule), &cfg);
+    if (e == cudaSuccess && *out < 1) return cudaErrorInvalidConfiguration;
+    return e;
+}
+
+// One persistent launch over the queues of one rule.
+cudaError_t launch_rule(int rule, int grid, int threads, int cluster, BatchJob* jobs,
+                        const int* order, int n_big, int n_small, int* counters,
+                        cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_kernel_for(rule), jobs, order, n_big, order + n_big,
+                              n_small, counters);
 }
 
 }  // namespace
@@ -181,6 +250,13 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(BatchJob* jobs, const int
 }  // namespace ising
 
 using namespace ising;
+
+// The queues of one update rule: order[offset, offset + n_big) are the
+// cluster jobs, the next n_small the per-CTA jobs.
+struct RuleQueues {
+    int offset = 0, n_big = 0, n_small = 0;
+    int grid = 0;  // resident CTAs of that rule's kernel
+};
 
 struct ising_batch {
     std::vector<ising_lattice*> lats;
@@ -192,10 +268,10 @@ struct ising_batch {
     cudaStream_t stream = nullptr;
     BatchJob* d_jobs = nullptr;
     BatchJob* h_jobs = nullptr;  // pinned mirror
-    int* d_order = nullptr;      // [big..., small...]
-    int* d_counters = nullptr;
-    int n_big = 0, n_small = 0;
-    int grid = 0;
+    int* d_order = nullptr;      // per rule: [big..., small...]
+    int* d_counters = nullptr;   // two per rule
+    RuleQueues q[2];             // [ISING_RULE_METROPOLIS], [ISING_RULE_HEATBATH]
+    std::vector<int> rule;       // each lattice's rule when the batch was made
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t uploaded = nullptr;
     bool table_valid = false;  // device table equals the host mirror's continuation
@@ -209,22 +285,18 @@ int records_in(uint64_t t, int64_t n, int every) {
 }
 
 cudaError_t launch_batch_kernel(ising_batch* b, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)b->grid);
-    cfg.blockDim = dim3((unsigned)b->opts.block_threads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)b->opts.cluster_size;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batch_kernel, b->d_jobs, (const int*)b->d_order, b->n_big,
-                              (const int*)(b->d_order + b->n_big), b->n_small, b->d_counters);
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(int), st);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+        const RuleQueues& q = b->q[r];
+        if (q.n_big + q.n_small == 0) continue;
+        e = launch_rule(r, q.grid, b->opts.block_threads, b->opts.cluster_size, b->d_jobs,
+                        b->d_order + q.offset, q.n_big, q.n_small, b->d_counters + 2 * r, st);
+    }
+    return e;
+}
+
+int queued_jobs(const ising_batch* b) {
+    return b->q[0].n_big + b->q[0].n_small + b->q[1].n_big + b->q[1].n_small;
 }
 
 void free_batch(ising_batch* b) {
@@ -282,56 +354,49 @@ int ising_batch_create(ising_batch** out, ising_lattice* const* lats, int n,
         return rc;
     }
 
-    // queues: largest work first, split at the size thresholds
-    std::vector<int> big, small;
+    // queues per rule: largest work first, split at the size thresholds
+    std::vector<int> big[2], small[2];
     b->in_table.assign(n, 1);
+    b->rule.resize(n);
     for (int i = 0; i < n; ++i) {
+        const int r = b->lats[i]->rule == ISING_RULE_HEATBATH ? 1 : 0;
+        b->rule[i] = b->lats[i]->rule;
         if (o.huge_sites > 0 && b->lats[i]->sites >= o.huge_sites) {
             b->huge.push_back(i);
             b->in_table[i] = 0;
         } else {
-            (b->lats[i]->sites >= o.big_sites ? big : small).push_back(i);
+            (o.cluster_size > 1 && b->lats[i]->sites >= o.big_sites ? big[r] : small[r])
+                .push_back(i);
         }
     }
     auto by_work = [&](int x, int y) {
         return b->lats[x]->sites * b->sweeps[x] > b->lats[y]->sites * b->sweeps[y];
     };
-    std::stable_sort(big.begin(), big.end(), by_work);
-    std::stable_sort(small.begin(), small.end(), by_work);
-    if (o.cluster_size == 1) {  // no cooperative phase: everything per CTA
-        small.insert(small.begin(), big.begin(), big.end());
-        std::stable_sort(small.begin(), small.end(), by_work);
-        big.clear();
+    std::vector<int> order;
+    for (int r = 0; r < 2; ++r) {
+        std::stable_sort(big[r].begin(), big[r].end(), by_work);
+        std::stable_sort(small[r].begin(), small[r].end(), by_work);
+        b->q[r].offset = (int)order.size();
+        b->q[r].n_big = (int)big[r].size();
+        b->q[r].n_small = (int)small[r].size();
+        order.insert(order.end(), big[r].begin(), big[r].end());
+        order.insert(order.end(), small[r].begin(), small[r].end());
     }
-    b->n_big = (int)big.size();
-    b->n_small = (int)small.size();
-    std::vector<int> order(big);
-    order.insert(order.end(), small.begin(), small.end());
 
     cudaError_t e = cudaMalloc(&b->d_jobs, sizeof(BatchJob) * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_jobs, sizeof(BatchJob) * (size_t)n);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
     if (e == cudaSuccess && !order.empty())  // empty when every lattice is huge
         e = cudaMemcpy(b->d_order, order.data(), sizeof(int) * order.size(),
                        cudaMemcpyHostToDevice);
-    // persistent grid: as many clusters as can be resident
-    if (e == cudaSuccess) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.blockDim = dim3((unsigned)o.block_threads);
-        cfg.gridDim = dim3((unsigned)(o.cluster_size * 1024));
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)o.cluster_size;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+    // persistent grids: as many clusters as can be resident
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+        if (b->q[r].n_big + b->q[r].n_small == 0) continue;
         int clusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&clusters, batch_kernel, &cfg);
-        if (e == cudaSuccess && clusters < 1) e = cudaErrorInvalidConfiguration;
-        b->grid = clusters * o.cluster_size;
+        e = resident_clusters(r, o.block_threads, o.cluster_size, &clusters);
+        b->q[r].grid = clusters * o.cluster_size;
     }
     if (e != cudaSuccess) {
         free_batch(b);
@@ -349,6 +414,7 @@ int ising_batch_launch(ising_batch* b) {
     for (int i = 0; i < n; ++i) {
         ising_lattice* h = b->lats[i];
         if (b->sweeps[i] > 0 && h->t + (uint64_t)b->sweeps[i] - 1 > kMaxSweep) return ISING_ERANGE;
+        if (h->rule != b->rule[i]) return ISING_EINVAL;  // queues are per rule, fixed at create
     }
     // the largest lattices first, each pass over the whole GPU
     for (int i : b->huge) {
@@ -365,24 +431,7 @@ int ising_batch_launch(ising_batch* b) {
         int rc = ensure_records(h, h->n_rec + 8 * (int64_t)(r > 0 ? r : 0));
         if (rc != ISING_OK) return rc;
         if (h->obs != before) moved = true;
-        BatchJob& j = b->h_jobs[i];
-        j.col0 = h->col[0];
-        j.col1 = h->col[1];
-        j.obs = h->obs + 2 * h->n_rec;
-        j.thr0 = h->thr[0];
-        j.thr1 = h->thr[1];
-        j.thr2 = h->thr[2];
-        j.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
-        j.key1 = (uint32_t)(h->seed >> 32);
-        j.t0 = (uint32_t)h->t;
-        j.dims = h->dims;
-        j.layout = h->layout;
-        j.L = h->L;
-        j.W = h->W;
-        j.rows = (uint32_t)h->rows;
-        j.half = (uint32_t)h->half_sites;
-        j.nsweeps = (int32_t)b->sweeps[i];
-        j.measure_every = b->every[i];
+        fill_job(b->h_jobs[i], h, b->sweeps[i], b->every[i], h->obs + 2 * h->n_rec);
     }
     // records reserved for later launches must stay inside the capacity: if the
     // last reserve is about to run out, the table is rebuilt (moved == true)
@@ -392,7 +441,7 @@ int ising_batch_launch(ising_batch* b) {
         ISING_BCHECK(cudaEventRecord(b->uploaded, b->stream));
         b->table_valid = true;
     }
-    if (b->opts.use_graph >= 0 && !b->exec && b->n_big + b->n_small > 0) {
+    if (b->opts.use_graph >= 0 && !b->exec && queued_jobs(b) > 0) {
         // capture [reset queue counters, persistent kernel] once; replay it
         cudaStream_t cap = nullptr;
         ISING_BCHECK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -408,7 +457,7 @@ int ising_batch_launch(ising_batch* b) {
         cudaStreamDestroy(cap);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    if (b->n_big + b->n_small > 0) {
+    if (queued_jobs(b) > 0) {
         if (b->exec)
             ISING_BCHECK(cudaGraphLaunch(b->exec, b->stream));
         else
@@ -441,9 +490,9 @@ void ising_batch_destroy(ising_batch* b) {
 
 int ising_batch_info(const ising_batch* b, int* grid, int* n_big, int* n_small, int* n_huge) {
     if (!b) return ISING_EINVAL;
-    if (grid) *grid = b->grid;
-    if (n_big) *n_big = b->n_big;
-    if (n_small) *n_small = b->n_small;
+    if (grid) *grid = b->q[0].grid > b->q[1].grid ? b->q[0].grid : b->q[1].grid;
+    if (n_big) *n_big = b->q[0].n_big + b->q[1].n_big;
+    if (n_small) *n_small = b->q[0].n_small + b->q[1].n_small;
     if (n_huge) *n_huge = (int)b->huge.size();
     return ISING_OK;
 }
@@ -464,16 +513,17 @@ namespace {
 constexpr int kStaticMaxJobs = 2048;
 constexpr size_t kStaticTableBytes = sizeof(BatchJob) * kStaticMaxJobs;
 constexpr size_t kStaticOrderBytes = sizeof(int) * kStaticMaxJobs;
+static_assert(sizeof(BatchJob) == 96, "the scratch size quoted in ising.h assumes 96-byte jobs");
 
 // job table | order | queue counters; every GPU that loads the library holds
-// it (about 168 KiB) until the process exits
+// it (about 200 KiB) until the process exits
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticTableBytes +
                                                                   kStaticOrderBytes + 256];
 
 struct StaticSetup {
     bool ready = false;
     unsigned char* scratch = nullptr;  // device address of g_static_scratch
-    int clusters[3][9] = {};           // resident clusters per [block size][cluster size]
+    int clusters[2][2][9] = {};        // resident clusters per [rule][block size][cluster size]
 };
 std::mutex g_static_mu;
 StaticSetup g_static[64];
@@ -482,8 +532,8 @@ int block_index(int threads) { return threads == 128 ? 0 : 1; }
 
 // Once per device, with that device current: the device address of the
 // scratch array (its host-side name is only a stand-in for it) and, once per
-// launch shape, the resident grid size.  Neither call allocates.
-int static_setup(int threads, int cluster, unsigned char** scratch, int* grid) {
+// rule and launch shape, the resident grid size.  Neither call allocates.
+int static_setup(int threads, int cluster, unsigned char** scratch, int grid[2]) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -497,26 +547,17 @@ int static_setup(int threads, int cluster, unsigned char** scratch, int* grid) {
         st.scratch = static_cast<unsigned char*>(ptr);
         st.ready = true;
     }
-    int& c = st.clusters[block_index(threads)][cluster];
-    if (c < 1) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.blockDim = dim3((unsigned)threads);
-        cfg.gridDim = dim3((unsigned)(cluster * 1024));
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)cluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nc = 0;
-        e = cudaOccupancyMaxActiveClusters(&nc, batch_kernel, &cfg);
-        if (e != cudaSuccess) return cuda_fail(e);
-        if (nc < 1) return ISING_ECUDA;
-        c = nc;
+    for (int r = 0; r < 2; ++r) {
+        int& c = st.clusters[r][block_index(threads)][cluster];
+        if (c < 1) {
+            int nc = 0;
+            e = resident_clusters(r, threads, cluster, &nc);
+            if (e != cudaSuccess) return cuda_fail(e);
+            c = nc;
+        }
+        grid[r] = c * cluster;
     }
     *scratch = st.scratch;
-    *grid = c * cluster;
     return ISING_OK;
 }
 
@@ -550,25 +591,35 @@ int ising_batch_run_static(ising_lattice* const* lats, int n, const int64_t* swe
     }
     if (total_rec > 0 && (!records || records_cap < total_rec)) return ISING_ERANGE;
     unsigned char* scratch = nullptr;
-    int grid = 0;
-    int rc = static_setup(o.block_threads, o.cluster_size, &scratch, &grid);
+    int grid[2] = {0, 0};
+    int rc = static_setup(o.block_threads, o.cluster_size, &scratch, grid);
     if (rc != ISING_OK) return rc;
     cudaStream_t sm = static_cast<cudaStream_t>(stream);
     BatchJob* d_jobs = reinterpret_cast<BatchJob*>(scratch);
     int* d_order = reinterpret_cast<int*>(scratch + kStaticTableBytes);
     int* d_counters = reinterpret_cast<int*>(scratch + kStaticTableBytes + kStaticOrderBytes);
 
-    // queues, largest work first: cluster-cooperative jobs, then per-CTA jobs
+    // queues per rule, largest work first: cluster-cooperative jobs, then
+    // per-CTA jobs (the same order as ising_batch_create)
     int order[kStaticMaxJobs];
-    int n_big = 0;
-    for (int i = 0; i < n; ++i)
-        if (o.cluster_size > 1 && lats[i]->sites >= o.big_sites) order[n_big++] = i;
-    int n_all = n_big;
-    for (int i = 0; i < n; ++i)
-        if (!(o.cluster_size > 1 && lats[i]->sites >= o.big_sites)) order[n_all++] = i;
+    int off[3] = {0, 0, 0}, n_big[2] = {0, 0};
     auto work = [&](int i) { return lats[i]->sites * sweeps[i]; };
-    std::stable_sort(order, order + n_big, [&](int x, int y) { return work(x) > work(y); });
-    std::stable_sort(order + n_big, order + n, [&](int x, int y) { return work(x) > work(y); });
+    auto by_work = [&](int x, int y) { return work(x) > work(y); };
+    int n_all = 0;
+    for (int r = 0; r < 2; ++r) {
+        off[r] = n_all;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int begin = n_all;
+            for (int i = 0; i < n; ++i) {
+                const bool big = o.cluster_size > 1 && lats[i]->sites >= o.big_sites;
+                if ((lats[i]->rule == ISING_RULE_HEATBATH ? 1 : 0) == r && big == (pass == 0))
+                    order[n_all++] = i;
+            }
+            std::stable_sort(order + begin, order + n_all, by_work);
+            if (pass == 0) n_big[r] = n_all - begin;
+        }
+    }
+    off[2] = n_all;
 
     cudaError_t e = cudaSuccess;
     if (total_rec > 0)  // the fused reductions add into zeroed record slots
@@ -584,24 +635,8 @@ int ising_batch_run_static(ising_lattice* const* lats, int n, const int64_t* swe
             const int i = base + q;
             const ising_lattice* h = lats[i];
             const int every = measure_every ? measure_every[i] : 1;
-            BatchJob& j = chunk[q];
-            j.col0 = h->col[0];
-            j.col1 = h->col[1];
-            j.obs = reinterpret_cast<unsigned long long*>(records) + 2 * rec_off;
-            j.thr0 = h->thr[0];
-            j.thr1 = h->thr[1];
-            j.thr2 = h->thr[2];
-            j.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
-            j.key1 = (uint32_t)(h->seed >> 32);
-            j.t0 = (uint32_t)h->t;
-            j.dims = h->dims;
-            j.layout = h->layout;
-            j.L = h->L;
-            j.W = h->W;
-            j.rows = (uint32_t)h->rows;
-            j.half = (uint32_t)h->half_sites;
-            j.nsweeps = (int32_t)sweeps[i];
-            j.measure_every = every;
+            fill_job(chunk[q], h, sweeps[i], every,
+                     reinterpret_cast<unsigned long long*>(records) + 2 * rec_off);
             rec_off += records_in(h->t, sweeps[i], every);
         }
         e = cudaMemcpyAsync(d_jobs + base, chunk, sizeof(BatchJob) * (size_t)m,
@@ -609,21 +644,12 @@ int ising_batch_run_static(ising_lattice* const* lats, int n, const int64_t* swe
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_order, order, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, sm);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), sm);
-    if (e == cudaSuccess) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)grid);
-        cfg.blockDim = dim3((unsigned)o.block_threads);
-        cfg.stream = sm;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)o.cluster_size;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, batch_kernel, d_jobs, (const int*)d_order, n_big,
-                               (const int*)(d_order + n_big), n - n_big, d_counters);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, 4 * sizeof(int), sm);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+        const int jobs = off[r + 1] - off[r];
+        if (jobs == 0) continue;
+        e = launch_rule(r, grid[r], o.block_threads, o.cluster_size, d_jobs, d_order + off[r],
+                        n_big[r], jobs - n_big[r], d_counters + 2 * r, sm);
     }
     if (e != cudaSuccess) return cuda_fail(e);
     for (int i = 0; i < n; ++i) lats[i]->t += (uint64_t)sweeps[i];
@@ -642,35 +668,23 @@ namespace ising {
 
 namespace {
 
+template <int RULE>
 __global__ void __launch_bounds__(256, 1) small_job_kernel(BatchJob job) {
     __shared__ BatchJob sj;
     if (threadIdx.x == 0) sj = job;
     __syncthreads();
-    dispatch_job<kModeCta>(&sj, threadIdx.x, blockDim.x, threadIdx.x == 0);
+    dispatch_job<kModeCta, RULE>(&sj, threadIdx.x, blockDim.x, threadIdx.x == 0);
 }
 
 }  // namespace
 
 int small_sweep(ising_lattice* h, int64_t n, int every, unsigned long long* slots) {
     BatchJob j;
-    j.col0 = h->col[0];
-    j.col1 = h->col[1];
-    j.obs = slots;
-    j.thr0 = h->thr[0];
-    j.thr1 = h->thr[1];
-    j.thr2 = h->thr[2];
-    j.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
-    j.key1 = (uint32_t)(h->seed >> 32);
-    j.t0 = (uint32_t)h->t;
-    j.dims = h->dims;
-    j.layout = h->layout;
-    j.L = h->L;
-    j.W = h->W;
-    j.rows = (uint32_t)h->rows;
-    j.half = (uint32_t)h->half_sites;
-    j.nsweeps = (int32_t)n;
-    j.measure_every = every;
-    small_job_kernel<<<1, 256, 0, h->stream>>>(j);
+    fill_job(j, h, n, every, slots);
+    if (h->rule == ISING_RULE_HEATBATH)
+        small_job_kernel<kRuleHeatBath><<<1, 256, 0, h->stream>>>(j);
+    else
+        small_job_kernel<kRuleMetropolis><<<1, 256, 0, h->stream>>>(j);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : cuda_fail(e);
 }

@@ -17,6 +17,9 @@
 using ising::DeviceProps;
 using ising::PassArgs;
 
+static_assert(ising::kRuleMetropolis == ISING_RULE_METROPOLIS, "rule values");
+static_assert(ising::kRuleHeatBath == ISING_RULE_HEATBATH, "rule values");
+
 namespace {
 
 constexpr uint64_t kMaxSites = 1ull << 32;  // 32-bit half indices in the kernels
@@ -99,6 +102,59 @@ int build_thresholds(int dims, double beta, uint32_t thr[3]) {
     return ISING_OK;
 }
 
+// floor(2^32 / (1 + e^x)) for the heat-bath flip probability, x = 4 beta m,
+// m = dims - d.  s = 2^32 / (1 + e^|x|) is the less likely outcome's share; the
+// threshold is floor(s) for m > 0 and floor(2^32 - s) = 2^32 - 1 - floor(s) for
+// m < 0 (s is never an integer there: the bracket test below excludes it).  s is
+// decided with the same relative brackets as floor_exp_scaled; near x = 0 the
+// answer is fixed by 0 < 2^31 - s = 2^31 tanh(|x| / 2) < 2^31 |x| / 2 < 1.
+int floor_logistic_scaled(double beta, int m, uint32_t* out) {
+    if (m == 0) {
+        *out = 0x80000000u;
+        return ISING_OK;
+    }
+    const int am = m < 0 ? -m : m;
+    const double x = 4.0 * beta * (double)am;
+    uint32_t fs;
+    if (std::isinf(x) || x > 64.0) {
+        fs = 0u;  // 0 < s < 2^32 e^-64 < 1
+    } else if (x < 0x1p-32) {
+        fs = 0x7FFFFFFFu;
+    } else {
+        const double v = std::ldexp(1.0 / (1.0 + std::exp(x)), 32);
+        const double lo = v * (1.0 - 0x1p-40), hi = v * (1.0 + 0x1p-40);
+        if (std::floor(lo) == std::floor(hi)) {
+            fs = (uint32_t)std::floor(v);
+        } else {
+            const long double xl = 4.0L * (long double)beta * (long double)am;
+            const long double vl = std::ldexp(1.0L / (1.0L + std::exp(xl)), 32);
+            const long double lol = vl * (1.0L - 0x1p-56L), hil = vl * (1.0L + 0x1p-56L);
+            if (std::floor(lol) != std::floor(hil)) return ISING_EINVAL;
+            fs = (uint32_t)std::floor(vl);
+        }
+    }
+    *out = m > 0 ? fs : 0xFFFFFFFFu - fs;
+    return ISING_OK;
+}
+
+int build_thresholds_heatbath(int dims, double beta, uint32_t thb[7]) {
+    if (!(beta > 0.0)) return ISING_EINVAL;
+    for (int d = 0; d < 7; ++d) thb[d] = 0u;
+    for (int d = 0; d <= 2 * dims; ++d) {
+        const int rc = floor_logistic_scaled(beta, dims - d, &thb[d]);
+        if (rc != ISING_OK) return rc;
+    }
+    return ISING_OK;
+}
+
+void rule_thresholds(const ising_lattice* h, uint32_t out[7]) {
+    for (int i = 0; i < 7; ++i) out[i] = 0u;
+    if (h->rule == ISING_RULE_HEATBATH)
+        std::memcpy(out, h->thb, sizeof(h->thb));
+    else
+        std::memcpy(out, h->thr, sizeof(h->thr));
+}
+
 void free_device(ising_lattice* h) {
     for (void*& p : h->col) {
         if (p) cudaFree(p);
@@ -156,26 +212,25 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     a.rows = h->rows;
     a.L = h->L;
     a.W = h->W;
-    a.thr0 = h->thr[0];
-    a.thr1 = h->thr[1];
-    a.thr2 = h->thr[2];
+    rule_thresholds(h, a.thr);
     a.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
     a.key1 = (uint32_t)(h->seed >> 32);
     a.t = t;
     a.c = c;
     if (h->layout == ISING_BITPACK)
-        ISING_CHECK(ising::packed_pass(a, h->dims, slot != nullptr, *h->dp, h->stream));
+        ISING_CHECK(ising::packed_pass(a, h->dims, slot != nullptr, h->rule, *h->dp, h->stream));
     else if (ising::int8_tma_ok(h->dims, h->L) &&
              (h->kernel == ISING_KERNEL_TMA ||
               // AUTO: the staged kernel where it measured faster (2D, long rows);
               // with short rows (3D, small 2D) its tiles hold about one vector
               // per thread and barriers dominate, so the strip kernel runs
               (h->kernel == ISING_KERNEL_AUTO && h->dims == 2 && h->L >= 4096)))
-        ISING_CHECK(ising::int8_pass_tma(a, h->dims, slot != nullptr, *h->dp, h->dp->d_err,
-                                         g_inject_timeout.load() ? 16u : 0u, h->stream));
+        ISING_CHECK(ising::int8_pass_tma(a, h->dims, slot != nullptr, h->rule, *h->dp,
+                                         h->dp->d_err, g_inject_timeout.load() ? 16u : 0u,
+                                         h->stream));
     else
-        ISING_CHECK(ising::int8_pass(a, h->dims, h->half_sites, slot != nullptr, *h->dp,
-                                     h->stream));
+        ISING_CHECK(ising::int8_pass(a, h->dims, h->half_sites, slot != nullptr, h->rule,
+                                     *h->dp, h->stream));
     return ISING_OK;
 }
 
@@ -212,8 +267,9 @@ int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t see
     // ISING_AUTO: the bit-packed layout, the faster of the two on this GPU
     // (results are identical in both layouts)
     const int use_layout = layout == ISING_AUTO ? ISING_BITPACK : layout;
-    uint32_t thr[3];
+    uint32_t thr[3], thb[7];
     int rc = build_thresholds(dims, beta, thr);
+    if (rc == ISING_OK) rc = build_thresholds_heatbath(dims, beta, thb);
     if (rc != ISING_OK) return rc;
     const DeviceProps* dp = nullptr;
     rc = device_props(&dp);
@@ -227,6 +283,7 @@ int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t see
     h->beta = beta;
     h->seed = seed;
     std::memcpy(h->thr, thr, sizeof(thr));
+    std::memcpy(h->thb, thb, sizeof(thb));
     h->sites = (int64_t)sites;
     h->half_sites = (int64_t)(sites / 2);
     h->W = L / 2;
@@ -400,12 +457,25 @@ int ising_compute_thresholds(int dims, double beta, uint32_t out[3]) {
     return build_thresholds(dims, beta, out);
 }
 
+int ising_compute_thresholds_heatbath(int dims, double beta, uint32_t out[7]) {
+    if (!out || (dims != 2 && dims != 3)) return ISING_EINVAL;
+    return build_thresholds_heatbath(dims, beta, out);
+}
+
+int ising_set_rule(ising_lattice* h, int rule) {
+    if (!h) return ISING_EINVAL;
+    if (rule != ISING_RULE_METROPOLIS && rule != ISING_RULE_HEATBATH) return ISING_EINVAL;
+    h->rule = rule;
+    return ISING_OK;
+}
+
 int ising_get_info(const ising_lattice* h, ising_info_t* out) {
     if (!h || !out) return ISING_EINVAL;
     std::memset(out, 0, sizeof(*out));
     out->dims = h->dims;
     out->L = h->L;
     out->layout = h->layout;
+    out->rule = h->rule;
     out->beta = h->beta;
     out->seed = h->seed;
     out->sweeps_done = h->t;

@@ -20,7 +20,9 @@ struct ising_lattice {
     int dims = 0, L = 0, layout = ISING_INT8;
     double beta = 0.0;
     uint64_t seed = 0;
-    uint32_t thr[3] = {0, 0, 0};
+    uint32_t thr[3] = {0, 0, 0};        // Metropolis: floor(exp(-2 beta k) 2^32), k = 2, 4, 6
+    uint32_t thb[7] = {0, 0, 0, 0, 0, 0, 0}; // heat bath: floor(2^32 / (1 + exp(4 beta (dims - d))))
+    int rule = ISING_RULE_METROPOLIS;
     int64_t sites = 0, half_sites = 0, rows = 0;
     int W = 0;
     void* col[2] = {nullptr, nullptr};  // colour 0 (black) and colour 1 (white) arrays
@@ -38,13 +40,17 @@ namespace ising {
 struct DeviceProps {
     int device = -1;
     int sm_count = 0;
-    int blocks_per_sm_vec[2][2] = {{1, 1}, {1, 1}};    // int8 vector pass [dims-2][measure]
-    int blocks_per_sm_packed[2][2] = {{1, 1}, {1, 1}}; // bit-packed pass [dims-2][measure]
+    // resident CTAs per SM of the int8 strip pass and the bit-packed pass,
+    // indexed [rule][dims - 2][measure]
+    int blocks_per_sm_vec[2][2][2] = {{{1, 1}, {1, 1}}, {{1, 1}, {1, 1}}};
+    int blocks_per_sm_packed[2][2][2] = {{{1, 1}, {1, 1}}, {{1, 1}, {1, 1}}};
     int* d_err = nullptr;  // raised by a kernel whose bounded wait ran out
 };
 
 // engine.cu helpers shared with batch.cu
 int cuda_fail(cudaError_t e);
+// the threshold table of the lattice's rule, as the kernels take it (PassArgs::thr)
+void rule_thresholds(const ising_lattice* h, uint32_t out[7]);
 int device_props(const DeviceProps** out);
 int ensure_records(ising_lattice* h, int64_t need);
 // n sweeps of a small lattice in one persistent single-CTA launch (batch.cu)
@@ -57,7 +63,7 @@ cudaError_t int8_query_occupancy(DeviceProps& dp);
 bool int8_vec_ok(int L);
 cudaError_t philox_fill(uint32_t* out, uint32_t n, uint32_t c1, uint32_t c2, uint32_t c3,
                         uint32_t key0, uint32_t key1, const DeviceProps& dp, cudaStream_t st);
-cudaError_t int8_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure,
+cudaError_t int8_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure, int rule,
                       const DeviceProps& dp, cudaStream_t st);
 cudaError_t int8_init(int8_t* col0, int8_t* col1, int L, int dims, int64_t sites, int start,
                       uint32_t key0, uint32_t key1, const DeviceProps& dp, cudaStream_t st);
@@ -68,13 +74,13 @@ cudaError_t int8_import(int8_t* col0, int8_t* col1, const int8_t* in, int L, int
 
 // int8 layout, inputs staged by bulk copies (sweep_int8_tma.cu)
 bool int8_tma_ok(int dims, int L);
-cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
-                          int* err, uint32_t extra_tx, cudaStream_t st);
+cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, int rule,
+                          const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st);
 
 // bit-packed layout (sweep_bitpack.cu)
 cudaError_t packed_query_occupancy(DeviceProps& dp);
-cudaError_t packed_pass(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
-                        cudaStream_t st);
+cudaError_t packed_pass(const PassArgs& a, int dims, bool measure, int rule,
+                        const DeviceProps& dp, cudaStream_t st);
 cudaError_t packed_init(uint32_t* col0, uint32_t* col1, int L, int dims, int64_t rows, int start,
                         uint32_t key0, uint32_t key1, const DeviceProps& dp, cudaStream_t st);
 cudaError_t packed_export(const uint32_t* col0, const uint32_t* col1, int8_t* out, int L,

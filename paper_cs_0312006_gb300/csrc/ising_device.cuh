@@ -23,6 +23,10 @@ constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u;
 constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
 
+// Local update rules (the values of ISING_RULE_* in ising.h).
+constexpr int kRuleMetropolis = 0;
+constexpr int kRuleHeatBath = 1;
+
 // Counter word 3 ("tag") separates the uses of the stream.
 constexpr uint32_t kTagSweep = 0u;
 constexpr uint32_t kTagInit = 1u;
@@ -58,7 +62,11 @@ struct PassArgs {
     int64_t rows;           // half rows per colour: L^(dims-1)
     int L;                  // linear size
     int W;                  // sites of one colour per row: L / 2
-    uint32_t thr0, thr1, thr2; // floor(exp(-2 beta k) 2^32), k = 2, 4, 6
+    // acceptance thresholds of the pass's rule:
+    //   kRuleMetropolis: thr[j] = floor(exp(-2 beta k) 2^32), k = 2j + 2 (j < dims)
+    //   kRuleHeatBath:   thr[d] = floor(2^32 / (1 + exp(4 beta (dims - d)))),
+    //                    d = 0..2*dims disagreeing neighbours
+    uint32_t thr[7];
     uint32_t key0, key1;    // seed (low, high)
     uint32_t t;             // sweep index
     int c;                  // colour of this pass: 0 black, 1 white

@@ -55,9 +55,9 @@ __device__ __forceinline__ uint32_t uphill_accept(uint32_t D, uint32_t u, int j,
     const uint32_t dj = D & (0x0Eu << (8 * j));  // 2*d_j in place
     uint32_t t;
     if (DIMS == 2) {
-        t = dj == 0u ? a.thr1 : a.thr0;
+        t = dj == 0u ? a.thr[1] : a.thr[0];
     } else {
-        t = dj == 0u ? a.thr2 : (dj == (0x02u << (8 * j)) ? a.thr1 : a.thr0);
+        t = dj == 0u ? a.thr[2] : (dj == (0x02u << (8 * j)) ? a.thr[1] : a.thr[0]);
     }
     return u < t ? (0xFEu << (8 * j)) : 0u;
 }
@@ -69,16 +69,46 @@ template <int DIMS>
 __device__ __forceinline__ uint32_t uphill_count(uint32_t D, const Philox4& u, const PassArgs& a) {
     constexpr uint32_t bias = (0x80u - 2u * DIMS) * kByteOnes;
     uint32_t acc = D + bias;
-    acc += (u.w0 < a.thr0 ? 0x00000002u : 0u) + (u.w0 < a.thr1 ? 0x00000002u : 0u);
-    acc += (u.w1 < a.thr0 ? 0x00000200u : 0u) + (u.w1 < a.thr1 ? 0x00000200u : 0u);
-    acc += (u.w2 < a.thr0 ? 0x00020000u : 0u) + (u.w2 < a.thr1 ? 0x00020000u : 0u);
-    acc += (u.w3 < a.thr0 ? 0x02000000u : 0u) + (u.w3 < a.thr1 ? 0x02000000u : 0u);
+    acc += (u.w0 < a.thr[0] ? 0x00000002u : 0u) + (u.w0 < a.thr[1] ? 0x00000002u : 0u);
+    acc += (u.w1 < a.thr[0] ? 0x00000200u : 0u) + (u.w1 < a.thr[1] ? 0x00000200u : 0u);
+    acc += (u.w2 < a.thr[0] ? 0x00020000u : 0u) + (u.w2 < a.thr[1] ? 0x00020000u : 0u);
+    acc += (u.w3 < a.thr[0] ? 0x02000000u : 0u) + (u.w3 < a.thr[1] ? 0x02000000u : 0u);
     if (DIMS == 3) {
-        acc += (u.w0 < a.thr2 ? 0x00000002u : 0u) + (u.w1 < a.thr2 ? 0x00000200u : 0u);
-        acc += (u.w2 < a.thr2 ? 0x00020000u : 0u) + (u.w3 < a.thr2 ? 0x02000000u : 0u);
+        acc += (u.w0 < a.thr[2] ? 0x00000002u : 0u) + (u.w1 < a.thr[2] ? 0x00000200u : 0u);
+        acc += (u.w2 < a.thr[2] ? 0x00020000u : 0u) + (u.w3 < a.thr[2] ? 0x02000000u : 0u);
     }
     const uint32_t F = acc & kByteBit7;
     return F | (F - (F >> 6));
+}
+
+// Heat-bath rule (every site draws; it flips iff u < thr[d], the thresholds
+// rising with d): with cnt = #{m = 0..2 dims : u < thr[m]}, u < thr[d] iff
+// cnt + d >= 2 dims + 1.  Byte j of D is 2 d_j, so byte j of D + bias + 2 cnt_j
+// reaches bit 7 exactly then (at most 4*(2 dims) + 2 + bias < 256: no carry).
+template <int DIMS>
+__device__ __forceinline__ uint32_t heatbath_count(uint32_t D, const Philox4& u,
+                                                   const PassArgs& a) {
+    constexpr uint32_t bias = (0x80u - 2u * (2u * DIMS + 1u)) * kByteOnes;
+    const uint32_t w[4] = {u.w0, u.w1, u.w2, u.w3};
+    uint32_t acc = D + bias;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t cnt = 0u;
+#pragma unroll
+        for (int m = 0; m <= 2 * DIMS; ++m) cnt += w[j] < a.thr[m] ? 2u : 0u;
+        acc += cnt << (8 * j);
+    }
+    const uint32_t F = acc & kByteBit7;
+    return F | (F - (F >> 6));
+}
+
+// thr[d] by selects (d = 0..2*dims), for code that holds PassArgs in registers.
+template <int DIMS>
+__device__ __forceinline__ uint32_t heatbath_threshold(int d, const PassArgs& a) {
+    uint32_t t = a.thr[0];
+#pragma unroll
+    for (int m = 1; m <= 2 * DIMS; ++m) t = d == m ? a.thr[m] : t;
+    return t;
 }
 
 template <int DIMS>
@@ -111,7 +141,7 @@ struct WordGeom {
 // Update word w of the int8 colour array `own` (colour a.c).  Accumulates the
 // number of -1 spins written (m_neg), the number of sites written (n_sites)
 // and, in the white pass, sum (2 d_new - 2 dims) over them (e_acc).
-template <int DIMS, bool MEASURE, int NC>
+template <int DIMS, bool MEASURE, int NC, int RULE = kRuleMetropolis>
 __device__ __forceinline__ void int8_word(const PassArgs& a, const WordGeom& g, uint32_t w,
                                           int& e_acc, int& m_neg, int& n_sites) {
     uint32_t* own = static_cast<uint32_t*>(a.own);
@@ -141,11 +171,17 @@ __device__ __forceinline__ void int8_word(const PassArgs& a, const WordGeom& g, 
             nzp = window4<NC>(other, h0 + g.L * g.W);
         }
         const uint32_t D = disagreements<DIMS>(s, nx, nxs, nym, nyp, nzm, nzp);
-        uint32_t X = downhill_mask<DIMS>(D);
-        if (X != 0xFEFEFEFEu) {
+        uint32_t X;
+        if (RULE == kRuleHeatBath) {
             const Philox4 u = philox4x32_10(w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
-            X |= uphill_accept<DIMS>(D, u.w0, 0, a) | uphill_accept<DIMS>(D, u.w1, 1, a) |
-                 uphill_accept<DIMS>(D, u.w2, 2, a) | uphill_accept<DIMS>(D, u.w3, 3, a);
+            X = heatbath_count<DIMS>(D, u, a);
+        } else {
+            X = downhill_mask<DIMS>(D);
+            if (X != 0xFEFEFEFEu) {
+                const Philox4 u = philox4x32_10(w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
+                X |= uphill_accept<DIMS>(D, u.w0, 0, a) | uphill_accept<DIMS>(D, u.w1, 1, a) |
+                     uphill_accept<DIMS>(D, u.w2, 2, a) | uphill_accept<DIMS>(D, u.w3, 3, a);
+            }
         }
         const uint32_t snew = s ^ X;
         own[w] = snew;
@@ -197,7 +233,7 @@ __device__ __forceinline__ void int8_word(const PassArgs& a, const WordGeom& g, 
         }
         s_val[j] = s;
         d_val[j] = (2 * DIMS - s * hsum) >> 1;  // k = s*h = 2*(dims - d)
-        if (d_val[j] < DIMS) need = true;
+        if (d_val[j] < DIMS || RULE == kRuleHeatBath) need = true;
     }
     uint32_t u[4] = {0u, 0u, 0u, 0u};
     if (need) {
@@ -210,11 +246,16 @@ __device__ __forceinline__ void int8_word(const PassArgs& a, const WordGeom& g, 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (!valid[j]) continue;
-        bool flip = d_val[j] >= DIMS;
-        if (!flip) {
-            const uint32_t t = DIMS == 2 ? (d_val[j] == 0 ? a.thr1 : a.thr0)
-                                         : (d_val[j] == 0 ? a.thr2 : (d_val[j] == 1 ? a.thr1 : a.thr0));
-            flip = u[j] < t;
+        bool flip;
+        if (RULE == kRuleHeatBath) {
+            flip = u[j] < heatbath_threshold<DIMS>(d_val[j], a);
+        } else {
+            flip = d_val[j] >= DIMS;
+            if (!flip) {
+                const uint32_t t = DIMS == 2 ? (d_val[j] == 0 ? a.thr[1] : a.thr[0])
+                                             : (d_val[j] == 0 ? a.thr[2] : (d_val[j] == 1 ? a.thr[1] : a.thr[0]));
+                flip = u[j] < t;
+            }
         }
         const int sn = flip ? -s_val[j] : s_val[j];
         if (flip) own_b[h0 + j] = (int8_t)sn;
@@ -231,9 +272,9 @@ __device__ __forceinline__ void int8_word(const PassArgs& a, const WordGeom& g, 
 
 // Update the 16 sites of one 16-byte vector (four Philox groups g0..g0+3).
 // The four Philox calls are independent and computed together when any of
-// the 16 sites needs its draw.  Accumulates the number of -1 spins (m_neg)
+// the 16 sites needs its draw (always, under the heat-bath rule).  Accumulates the number of -1 spins (m_neg)
 // and, in the white pass, sum_j 2*d_new_j (e_acc).
-template <int DIMS, bool MEASURE>
+template <int DIMS, bool MEASURE, int RULE = kRuleMetropolis>
 __device__ __forceinline__ uint4 update_vec(const uint4& s, const uint4& x, const uint4& xs,
                                             const uint4& ym, const uint4& yp, const uint4& zm,
                                             const uint4& zp, uint32_t g0, const PassArgs& a,
@@ -244,22 +285,32 @@ __device__ __forceinline__ uint4 update_vec(const uint4& s, const uint4& x, cons
     D[1] = disagreements<DIMS>(s.y, x.y, xs.y, ym.y, yp.y, zm.y, zp.y);
     D[2] = disagreements<DIMS>(s.z, x.z, xs.z, ym.z, yp.z, zm.z, zp.z);
     D[3] = disagreements<DIMS>(s.w, x.w, xs.w, ym.w, yp.w, zm.w, zp.w);
-    bool need = false;
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        X[w] = downhill_mask<DIMS>(D[w]);
-        need |= X[w] != 0xFEFEFEFEu;
-    }
-    if (need) {
+    if (RULE == kRuleHeatBath) {  // every site draws
         Philox4 u[4];
 #pragma unroll
         for (int w = 0; w < 4; ++w)
             u[w] = philox4x32_10(g0 + (uint32_t)w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
-        // counting thresholds below each draw measured a little faster here
-        // than selecting one threshold per site (uphill_accept): it spreads the
-        // work over the integer ALU and the multiply-add pipe
 #pragma unroll
-        for (int w = 0; w < 4; ++w) X[w] |= uphill_count<DIMS>(D[w], u[w], a);
+        for (int w = 0; w < 4; ++w) X[w] = heatbath_count<DIMS>(D[w], u[w], a);
+    } else {
+        bool need = false;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            X[w] = downhill_mask<DIMS>(D[w]);
+            need |= X[w] != 0xFEFEFEFEu;
+        }
+        if (need) {
+            Philox4 u[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                u[w] = philox4x32_10(g0 + (uint32_t)w, a.t, (uint32_t)a.c, kTagSweep, a.key0,
+                                     a.key1);
+            // counting thresholds below each draw measured a little faster here
+            // than selecting one threshold per site (uphill_accept): it spreads
+            // the work over the integer ALU and the multiply-add pipe
+#pragma unroll
+            for (int w = 0; w < 4; ++w) X[w] |= uphill_count<DIMS>(D[w], u[w], a);
+        }
     }
     uint32_t out[4];
 #pragma unroll
@@ -306,7 +357,7 @@ __device__ __forceinline__ uint4 window16(const uint4* other16, uint32_t o) {
 // the x-wrap and the first/last row and plane, is updated as a whole from
 // 16-byte neighbour windows; any other vector word by word (int8_word).
 // Accumulates m_neg, n_sites and, in the white pass, e_acc as int8_word does.
-template <int DIMS, bool MEASURE, int NC>
+template <int DIMS, bool MEASURE, int NC, int RULE = kRuleMetropolis>
 __device__ __forceinline__ void int8_vec(const PassArgs& a, const WordGeom& g, uint32_t v,
                                          int& e_acc, int& m_neg, int& n_sites) {
     const uint32_t h0 = 16u * v;
@@ -324,7 +375,7 @@ __device__ __forceinline__ void int8_vec(const PassArgs& a, const WordGeom& g, u
     if (!fast) {
 #pragma unroll 1
         for (uint32_t w = 4u * v; w < 4u * v + 4u; ++w)
-            if (4u * w < g.half) int8_word<DIMS, MEASURE, NC>(a, g, w, e_acc, m_neg, n_sites);
+            if (4u * w < g.half) int8_word<DIMS, MEASURE, NC, RULE>(a, g, w, e_acc, m_neg, n_sites);
         return;
     }
     const uint4* other16 = static_cast<const uint4*>(a.other);
@@ -349,7 +400,8 @@ __device__ __forceinline__ void int8_vec(const PassArgs& a, const WordGeom& g, u
         nzp = window16<NC>(other16, h0 + g.L * g.W);
     }
     int e_vec = 0;
-    own16[v] = update_vec<DIMS, MEASURE>(s, nx, nxs, nym, nyp, nzm, nzp, 4u * v, a, e_vec, m_neg);
+    own16[v] = update_vec<DIMS, MEASURE, RULE>(s, nx, nxs, nym, nyp, nzm, nzp, 4u * v, a, e_vec,
+                                               m_neg);
     if (MEASURE) {
         n_sites += 16;
         if (a.c == 1) e_acc += e_vec - 16 * 2 * DIMS;
@@ -383,34 +435,66 @@ __device__ __forceinline__ Counts count3(uint32_t a, uint32_t b, uint32_t c, uin
     return Counts{always, low & ~bit0, low & bit0, bit1 & ~bit0 & ~bit2};
 }
 
+// Bit-sliced number of disagreeing neighbours d = d0 + 2 d1 + 4 d2 of each
+// of the 32 sites (the heat-bath rule needs every value of d).
+struct Digits {
+    uint32_t d0, d1, d2;
+};
+
+__device__ __forceinline__ Digits digits2(uint32_t a, uint32_t b, uint32_t c, uint32_t e) {
+    const uint32_t s1 = a ^ b, c1 = a & b;
+    const uint32_t s2 = c ^ e, c2 = c & e;
+    const uint32_t c3 = s1 & s2;  // d = (s1 ^ s2) + 2 (c1 + c2 + c3)
+    return Digits{s1 ^ s2, c1 ^ c2 ^ c3, (c1 & c2) | (c3 & (c1 ^ c2))};
+}
+
+__device__ __forceinline__ Digits digits3(uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                          uint32_t e, uint32_t f) {
+    const uint32_t s1 = a ^ b ^ c, k1 = (a & b) | (c & (a ^ b));
+    const uint32_t s2 = d ^ e ^ f, k2 = (d & e) | (f & (d ^ e));
+    const uint32_t k0 = s1 & s2;  // d = (s1 ^ s2) + 2 (k1 + k2 + k0)
+    return Digits{s1 ^ s2, k1 ^ k2 ^ k0, (k1 & k2) | (k0 & (k1 ^ k2))};
+}
+
+// Threshold of bit b: Metropolis, for a site with dE > 0 (d < dims) ...
 template <int DIMS>
-__device__ __forceinline__ uint32_t group_accept(const Counts& k, const Philox4& u, int i,
+__device__ __forceinline__ uint32_t site_threshold(const Counts& k, int b, const PassArgs& a) {
+    if (DIMS == 2) return (k.eq0 >> b) & 1u ? a.thr[1] : a.thr[0];
+    return (k.eq0 >> b) & 1u ? a.thr[2] : ((k.eq1 >> b) & 1u ? a.thr[1] : a.thr[0]);
+}
+
+// ... and heat bath, thr[d] for any d.
+template <int DIMS>
+__device__ __forceinline__ uint32_t site_threshold(const Digits& k, int b, const PassArgs& a) {
+    const bool d0 = (k.d0 >> b) & 1u, d1 = (k.d1 >> b) & 1u, d2 = (k.d2 >> b) & 1u;
+    const uint32_t lo = d1 ? (d0 ? a.thr[3] : a.thr[2]) : (d0 ? a.thr[1] : a.thr[0]);
+    const uint32_t hi = DIMS == 2 ? a.thr[4] : (d1 ? a.thr[6] : (d0 ? a.thr[5] : a.thr[4]));
+    return d2 ? hi : lo;
+}
+
+template <int DIMS, typename K>
+__device__ __forceinline__ uint32_t group_accept(const K& k, const Philox4& u, int i,
                                                  const PassArgs& a) {
     const uint32_t w[4] = {u.w0, u.w1, u.w2, u.w3};
     uint32_t acc = 0u;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int b = 4 * i + j;
-        uint32_t t;
-        if (DIMS == 2) {
-            t = (k.eq0 >> b) & 1u ? a.thr1 : a.thr0;
-        } else {
-            t = (k.eq0 >> b) & 1u ? a.thr2 : ((k.eq1 >> b) & 1u ? a.thr1 : a.thr0);
-        }
-        acc |= (w[j] < t ? 1u : 0u) << b;
+        acc |= (w[j] < site_threshold<DIMS>(k, b, a) ? 1u : 0u) << b;
     }
     return acc;
 }
 
-// Accept mask of the sites with dE > 0 among the `need` bits of a packed word
-// whose 32 bits are the half indices hb = hbase + b (b = 0..31).  Bit b's draw
+// Accept mask of the `need` bits of a packed word (Metropolis: the sites with
+// dE > 0; heat bath: every valid site) whose 32 bits are the half indices
+// hb = hbase + b (b = 0..31).  Bit b's draw
 // is word (hb & 3) of Philox group hb >> 2.  When hbase is a multiple of 4 the
 // eight groups are the word's nibbles and are computed four at a time; when a
 // row starts inside a group (W not a multiple of 4) the word spans nine
 // groups, taken one at a time (measured faster here than interleaving them,
 // which raises register pressure in the batched kernel).
-template <int DIMS>
-__device__ __forceinline__ uint32_t packed_accept(const Counts& k, uint32_t need, uint32_t hbase,
+template <int DIMS, typename K>
+__device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uint32_t hbase,
                                                   const PassArgs& a) {
     uint32_t acc = 0u;
     const uint32_t m = hbase & 3u, g0 = hbase >> 2;
@@ -444,13 +528,7 @@ __device__ __forceinline__ uint32_t packed_accept(const Counts& k, uint32_t need
         for (int j = 0; j < 4; ++j) {
             const int b = lo + j;
             if (b < 0 || b > 31) continue;
-            uint32_t t;
-            if (DIMS == 2) {
-                t = (k.eq0 >> b) & 1u ? a.thr1 : a.thr0;
-            } else {
-                t = (k.eq0 >> b) & 1u ? a.thr2 : ((k.eq1 >> b) & 1u ? a.thr1 : a.thr0);
-            }
-            acc |= (w[j] < t ? 1u : 0u) << b;
+            acc |= (w[j] < site_threshold<DIMS>(k, b, a) ? 1u : 0u) << b;
         }
     }
     return acc;
@@ -461,7 +539,7 @@ __device__ __forceinline__ uint32_t packed_accept(const Counts& k, uint32_t need
 // when xh < W; the other bits of a row's last word stay 0 and never flip).
 // The x-neighbour wrap at the row ends comes from the row's last valid bit
 // (p = 0, first word) or first bit (p = 1, last word).
-template <int DIMS, bool MEASURE, int NC>
+template <int DIMS, bool MEASURE, int NC, int RULE = kRuleMetropolis>
 __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, int& e_acc,
                                             int& m_acc) {
     const uint32_t W = (uint32_t)a.W;
@@ -508,15 +586,22 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
             sh = __funnelshift_r(o, load_other<NC>(other + row + q + 1u), 1);
         }
     }
-    Counts k;
-    if (DIMS == 2) {
-        k = count2(s ^ o, s ^ sh, s ^ oym, s ^ oyp);
+    uint32_t flip;
+    if constexpr (RULE == kRuleHeatBath) {  // every valid site draws
+        const Digits k = DIMS == 2 ? digits2(s ^ o, s ^ sh, s ^ oym, s ^ oyp)
+                                   : digits3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
+        flip = packed_accept<DIMS>(k, valid, r * W + 32u * q, a);
     } else {
-        k = count3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
+        Counts k;
+        if (DIMS == 2) {
+            k = count2(s ^ o, s ^ sh, s ^ oym, s ^ oyp);
+        } else {
+            k = count3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
+        }
+        flip = k.always;
+        const uint32_t need = ~k.always & valid;
+        if (need) flip |= packed_accept<DIMS>(k, need, r * W + 32u * q, a);
     }
-    uint32_t flip = k.always;
-    const uint32_t need = ~k.always & valid;
-    if (need) flip |= packed_accept<DIMS>(k, need, r * W + 32u * q, a);
     const uint32_t snew = s ^ (flip & valid);
     own[row + q] = snew;
     if (MEASURE) {

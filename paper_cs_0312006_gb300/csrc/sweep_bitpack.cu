@@ -28,13 +28,13 @@ namespace ising {
 namespace {
 
 // One item = one 32-site word of the colour array (see packed_word()).
-template <int DIMS, bool MEASURE>
+template <int DIMS, bool MEASURE, int RULE>
 __global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a) {
     const uint32_t items = (uint32_t)a.rows * (((uint32_t)a.W + 31u) >> 5);
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_acc = 0;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride)
-        packed_word<DIMS, MEASURE, 1>(a, g, e_acc, m_acc);
+        packed_word<DIMS, MEASURE, 1, RULE>(a, g, e_acc, m_acc);
     if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
 }
 
@@ -112,14 +112,14 @@ unsigned grid_for(int64_t n, const DeviceProps& dp) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
-template <int DIMS, bool MEASURE>
+template <int DIMS, bool MEASURE, int RULE>
 cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream_t st) {
     const int64_t items = a.rows * ((a.W + 31) >> 5);
     int64_t blocks = (items + 255) / 256;
-    const int64_t cap = (int64_t)dp.sm_count * dp.blocks_per_sm_packed[DIMS - 2][MEASURE];
+    const int64_t cap = (int64_t)dp.sm_count * dp.blocks_per_sm_packed[RULE][DIMS - 2][MEASURE];
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    pass_packed<DIMS, MEASURE><<<(unsigned)blocks, 256, 0, st>>>(a);
+    pass_packed<DIMS, MEASURE, RULE><<<(unsigned)blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -127,23 +127,36 @@ cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream
 
 cudaError_t packed_query_occupancy(DeviceProps& dp) {
     cudaError_t e;
-#define ISING_OCC(D, M)                                                                       \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_packed[D - 2][M],      \
-                                                      pass_packed<D, M>, 256, 0);              \
+#define ISING_OCC(R, D, M)                                                                    \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_packed[R][D - 2][M],   \
+                                                      pass_packed<D, M, R>, 256, 0);           \
     if (e != cudaSuccess) return e;
-    ISING_OCC(2, false)
-    ISING_OCC(2, true)
-    ISING_OCC(3, false)
-    ISING_OCC(3, true)
+    ISING_OCC(kRuleMetropolis, 2, false)
+    ISING_OCC(kRuleMetropolis, 2, true)
+    ISING_OCC(kRuleMetropolis, 3, false)
+    ISING_OCC(kRuleMetropolis, 3, true)
+    ISING_OCC(kRuleHeatBath, 2, false)
+    ISING_OCC(kRuleHeatBath, 2, true)
+    ISING_OCC(kRuleHeatBath, 3, false)
+    ISING_OCC(kRuleHeatBath, 3, true)
 #undef ISING_OCC
     return cudaSuccess;
 }
 
-cudaError_t packed_pass(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
-                        cudaStream_t st) {
+template <int RULE>
+static cudaError_t packed_pass_rule(const PassArgs& a, int dims, bool measure,
+                                    const DeviceProps& dp, cudaStream_t st) {
     if (dims == 2)
-        return measure ? launch_packed_t<2, true>(a, dp, st) : launch_packed_t<2, false>(a, dp, st);
-    return measure ? launch_packed_t<3, true>(a, dp, st) : launch_packed_t<3, false>(a, dp, st);
+        return measure ? launch_packed_t<2, true, RULE>(a, dp, st)
+                       : launch_packed_t<2, false, RULE>(a, dp, st);
+    return measure ? launch_packed_t<3, true, RULE>(a, dp, st)
+                   : launch_packed_t<3, false, RULE>(a, dp, st);
+}
+
+cudaError_t packed_pass(const PassArgs& a, int dims, bool measure, int rule,
+                        const DeviceProps& dp, cudaStream_t st) {
+    return rule == kRuleHeatBath ? packed_pass_rule<kRuleHeatBath>(a, dims, measure, dp, st)
+                                 : packed_pass_rule<kRuleMetropolis>(a, dims, measure, dp, st);
 }
 
 cudaError_t packed_init(uint32_t* col0, uint32_t* col1, int L, int dims, int64_t rows, int start,

@@ -42,7 +42,7 @@ __device__ __forceinline__ int wrap_next(int v, int n) { return v == n - 1 ? 0 :
 // x-shift comes from the neighbouring lane.  Strips are as balanced as the
 // row count allows; a strip that reaches the end of a plane reloads its
 // window for the next plane.
-template <int DIMS, bool MEASURE>
+template <int DIMS, bool MEASURE, int RULE>
 __global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 2) pass_int8_strip(PassArgs a) {
     const int nv = a.nv, S = a.strips, L = a.L;
     const int rows = (int)a.rows;
@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 2) pass_int8_strip(PassAr
                 sh.w = __funnelshift_r(oc.w, next_x, 8);
             }
             const uint32_t g0 = ((uint32_t)r * nv + (uint32_t)v) * 4u;  // Philox group of word 0
-            const uint4 s = update_vec<DIMS, MEASURE>(sc, oc, sh, om, op, zm, zp, g0, a, e_acc,
-                                                      m_neg);
+            const uint4 s = update_vec<DIMS, MEASURE, RULE>(sc, oc, sh, om, op, zm, zp, g0, a,
+                                                            e_acc, m_neg);
             Sv[(uint32_t)r * nv] = s;
             ++n_rows;
         }
@@ -150,13 +150,13 @@ __global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 2) pass_int8_strip(PassAr
 
 // General kernel: any even L.  One item = one 16-byte vector of the colour
 // array (16 consecutive half indices, four Philox groups); see int8_vec().
-template <int DIMS, bool MEASURE>
+template <int DIMS, bool MEASURE, int RULE>
 __global__ void __launch_bounds__(256) pass_int8_vecs(PassArgs a, WordGeom g) {
     const uint32_t vecs = (g.half + 15u) >> 4;
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_neg = 0, n_sites = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < vecs; v += stride)
-        int8_vec<DIMS, MEASURE, 1>(a, g, v, e_acc, m_neg, n_sites);
+        int8_vec<DIMS, MEASURE, 1, RULE>(a, g, v, e_acc, m_neg, n_sites);
     if (MEASURE) block_reduce_add(e_acc, n_sites - 2 * m_neg, a.obs, a.c == 1);
 }
 
@@ -201,7 +201,7 @@ __global__ void import_int8(int8_t* col0, int8_t* col1, const int8_t* in, int L,
     }
 }
 
-template <int DIMS, bool MEASURE>
+template <int DIMS, bool MEASURE, int RULE>
 cudaError_t launch_pass_t(const PassArgs& a0, int64_t half_sites, bool vec, const DeviceProps& dp,
                           cudaStream_t st) {
     const int threads = 256;
@@ -209,14 +209,14 @@ cudaError_t launch_pass_t(const PassArgs& a0, int64_t half_sites, bool vec, cons
         PassArgs a = a0;
         a.nv = a.W >> 4;
         // one wave of resident threads, each walking a strip of rows of one column
-        const int64_t resident = (int64_t)dp.sm_count * dp.blocks_per_sm_vec[DIMS - 2][MEASURE] *
-                                 threads;
+        const int64_t resident =
+            (int64_t)dp.sm_count * dp.blocks_per_sm_vec[RULE][DIMS - 2][MEASURE] * threads;
         int64_t strips = resident / a.nv;
         if (strips > a.rows) strips = a.rows;
         if (strips < 1) strips = 1;
         a.strips = (int)strips;
         const int64_t blocks = (strips * a.nv + threads - 1) / threads;
-        pass_int8_strip<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a);
+        pass_int8_strip<DIMS, MEASURE, RULE><<<(unsigned)blocks, threads, 0, st>>>(a);
     } else {
         const int64_t vecs = (half_sites + 15) >> 4;
         int64_t blocks = (vecs + threads - 1) / threads;
@@ -228,7 +228,7 @@ cudaError_t launch_pass_t(const PassArgs& a0, int64_t half_sites, bool vec, cons
         g.L = (uint32_t)a0.L;
         g.rows = (uint32_t)a0.rows;
         g.half = (uint32_t)half_sites;
-        pass_int8_vecs<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a0, g);
+        pass_int8_vecs<DIMS, MEASURE, RULE><<<(unsigned)blocks, threads, 0, st>>>(a0, g);
     }
     return cudaGetLastError();
 }
@@ -249,14 +249,18 @@ __global__ void philox_fill_kernel(uint4* out, uint32_t n, uint32_t c1, uint32_t
 
 cudaError_t int8_query_occupancy(DeviceProps& dp) {
     cudaError_t e;
-#define ISING_OCC(D, M)                                                                      \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_vec[D - 2][M],        \
-                                                      pass_int8_strip<D, M>, 256, 0);           \
+#define ISING_OCC(R, D, M)                                                                   \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_vec[R][D - 2][M],     \
+                                                      pass_int8_strip<D, M, R>, 256, 0);        \
     if (e != cudaSuccess) return e;
-    ISING_OCC(2, false)
-    ISING_OCC(2, true)
-    ISING_OCC(3, false)
-    ISING_OCC(3, true)
+    ISING_OCC(kRuleMetropolis, 2, false)
+    ISING_OCC(kRuleMetropolis, 2, true)
+    ISING_OCC(kRuleMetropolis, 3, false)
+    ISING_OCC(kRuleMetropolis, 3, true)
+    ISING_OCC(kRuleHeatBath, 2, false)
+    ISING_OCC(kRuleHeatBath, 2, true)
+    ISING_OCC(kRuleHeatBath, 3, false)
+    ISING_OCC(kRuleHeatBath, 3, true)
 #undef ISING_OCC
     return cudaSuccess;
 }
@@ -274,14 +278,22 @@ cudaError_t philox_fill(uint32_t* out, uint32_t n, uint32_t c1, uint32_t c2, uin
     return cudaGetLastError();
 }
 
-cudaError_t int8_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure,
-                      const DeviceProps& dp, cudaStream_t st) {
+template <int RULE>
+cudaError_t int8_pass_rule(const PassArgs& a, int dims, int64_t half_sites, bool measure,
+                           const DeviceProps& dp, cudaStream_t st) {
     const bool vec = (a.W % 16) == 0;
     if (dims == 2)
-        return measure ? launch_pass_t<2, true>(a, half_sites, vec, dp, st)
-                       : launch_pass_t<2, false>(a, half_sites, vec, dp, st);
-    return measure ? launch_pass_t<3, true>(a, half_sites, vec, dp, st)
-                   : launch_pass_t<3, false>(a, half_sites, vec, dp, st);
+        return measure ? launch_pass_t<2, true, RULE>(a, half_sites, vec, dp, st)
+                       : launch_pass_t<2, false, RULE>(a, half_sites, vec, dp, st);
+    return measure ? launch_pass_t<3, true, RULE>(a, half_sites, vec, dp, st)
+                   : launch_pass_t<3, false, RULE>(a, half_sites, vec, dp, st);
+}
+
+cudaError_t int8_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure, int rule,
+                      const DeviceProps& dp, cudaStream_t st) {
+    return rule == kRuleHeatBath
+               ? int8_pass_rule<kRuleHeatBath>(a, dims, half_sites, measure, dp, st)
+               : int8_pass_rule<kRuleMetropolis>(a, dims, half_sites, measure, dp, st);
 }
 
 static unsigned grid_for(int64_t n, const DeviceProps& dp) {

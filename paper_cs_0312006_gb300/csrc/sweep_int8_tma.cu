@@ -137,7 +137,7 @@ __device__ __forceinline__ void issue_tile(const PassArgs& a, const TmaGeom& tg,
     }
 }
 
-template <int DIMS, bool MEASURE>
+template <int DIMS, bool MEASURE, int RULE>
 __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kStages];
@@ -207,8 +207,8 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
                 }
                 const uint32_t row = (z * (uint32_t)a.L + y) * nv + v;  // global vector index
                 int e_vec = 0;
-                own_g[row] = update_vec<DIMS, MEASURE>(own_s[i * nv + v], oc, sh, om, op, zm, zp,
-                                                       row * 4u, a, e_vec, m_neg);
+                own_g[row] = update_vec<DIMS, MEASURE, RULE>(own_s[i * nv + v], oc, sh, om, op,
+                                                             zm, zp, row * 4u, a, e_vec, m_neg);
                 e_acc += e_vec;
                 ++n_vec;
             }
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
     }
 }
 
-template <int DIMS, bool MEASURE>
+template <int DIMS, bool MEASURE, int RULE>
 cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uint32_t extra_tx,
                          cudaStream_t st) {
     TmaGeom tg;
@@ -246,19 +246,19 @@ cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uin
     static int attr_set = 0;  // largest dynamic shared memory opted into so far
     cudaError_t e = cudaSuccess;
     if ((int)smem > attr_set) {
-        e = cudaFuncSetAttribute(pass_int8_tma<DIMS, MEASURE>,
+        e = cudaFuncSetAttribute(pass_int8_tma<DIMS, MEASURE, RULE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = 200 * 1024;
     }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_int8_tma<DIMS, MEASURE>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_int8_tma<DIMS, MEASURE, RULE>,
                                                       threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int grid = dp.sm_count * per_sm;
     if (grid > tg.tiles) grid = tg.tiles;
-    pass_int8_tma<DIMS, MEASURE><<<grid, threads, smem, st>>>(a, tg, err);
+    pass_int8_tma<DIMS, MEASURE, RULE><<<grid, threads, smem, st>>>(a, tg, err);
     return cudaGetLastError();
 }
 
@@ -274,13 +274,22 @@ bool int8_tma_ok(int dims, int L) {
     return (size_t)kStages * stage <= 200 * 1024;
 }
 
-cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
-                          int* err, uint32_t extra_tx, cudaStream_t st) {
+template <int RULE>
+static cudaError_t int8_pass_tma_rule(const PassArgs& a, int dims, bool measure,
+                                      const DeviceProps& dp, int* err, uint32_t extra_tx,
+                                      cudaStream_t st) {
     if (dims == 2)
-        return measure ? launch_tma_t<2, true>(a, dp, err, extra_tx, st)
-                       : launch_tma_t<2, false>(a, dp, err, extra_tx, st);
-    return measure ? launch_tma_t<3, true>(a, dp, err, extra_tx, st)
-                   : launch_tma_t<3, false>(a, dp, err, extra_tx, st);
+        return measure ? launch_tma_t<2, true, RULE>(a, dp, err, extra_tx, st)
+                       : launch_tma_t<2, false, RULE>(a, dp, err, extra_tx, st);
+    return measure ? launch_tma_t<3, true, RULE>(a, dp, err, extra_tx, st)
+                   : launch_tma_t<3, false, RULE>(a, dp, err, extra_tx, st);
+}
+
+cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, int rule,
+                          const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st) {
+    return rule == kRuleHeatBath
+               ? int8_pass_tma_rule<kRuleHeatBath>(a, dims, measure, dp, err, extra_tx, st)
+               : int8_pass_tma_rule<kRuleMetropolis>(a, dims, measure, dp, err, extra_tx, st);
 }
 
 }  // namespace ising

@@ -20,6 +20,7 @@ from . import _build
 INT8, BITPACK, AUTO = 0, 1, 2
 HOT, COLD_UP, COLD_DOWN = 0, 1, 2
 KERNEL_AUTO, KERNEL_STRIP, KERNEL_TMA = 0, 1, 2
+RULE_METROPOLIS, RULE_HEATBATH = 0, 1
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, ERANGE = 0, -1, -2, -3, -4, -5, -6
 
@@ -42,7 +43,7 @@ class BatchOpts(ctypes.Structure):
 
 class IsingInfo(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int), ("L", ctypes.c_int), ("layout", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("beta", ctypes.c_double),
+                ("rule", ctypes.c_int), ("beta", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("sweeps_done", ctypes.c_uint64),
                 ("sites", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("pending_records", ctypes.c_int64)]
@@ -79,6 +80,9 @@ def load_library():
             "ising_set_stream": ([P, P], ctypes.c_int),
             "ising_thresholds": ([P, u32p], ctypes.c_int),
             "ising_compute_thresholds": ([ctypes.c_int, ctypes.c_double, u32p], ctypes.c_int),
+            "ising_compute_thresholds_heatbath": ([ctypes.c_int, ctypes.c_double, u32p],
+                                                  ctypes.c_int),
+            "ising_set_rule": ([P, ctypes.c_int], ctypes.c_int),
             "ising_get_info": ([P, ctypes.POINTER(IsingInfo)], ctypes.c_int),
             "ising_synchronize": ([P], ctypes.c_int),
             "ising_set_kernel": ([P, ctypes.c_int], ctypes.c_int),
@@ -137,11 +141,21 @@ def compute_thresholds(dims: int, beta: float) -> np.ndarray:
     return out
 
 
+def compute_thresholds_heatbath(dims: int, beta: float) -> np.ndarray:
+    """``ising_compute_thresholds_heatbath``: the engine's heat-bath table (7 entries)."""
+    out = np.zeros(7, dtype=np.uint32)
+    _check(load_library().ising_compute_thresholds_heatbath(
+        dims, float(beta), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))),
+        f"ising_compute_thresholds_heatbath(dims={dims}, beta={beta})")
+    return out
+
+
 class Lattice:
     """One lattice on the current CUDA device (``ising_create``)."""
 
     def __init__(self, dims: int, L: int, beta: float, seed: int, layout: int = INT8,
-                 start: int = HOT, stream=None, kernel: int = KERNEL_AUTO):
+                 start: int = HOT, stream=None, kernel: int = KERNEL_AUTO,
+                 rule: int = RULE_METROPOLIS):
         lib = load_library()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -152,6 +166,8 @@ class Lattice:
             self.set_stream(stream)
         if kernel != KERNEL_AUTO:
             self.set_kernel(kernel)
+        if rule != RULE_METROPOLIS:
+            self.set_rule(rule)
         if start != HOT:
             self.init(start)
 
@@ -236,6 +252,10 @@ class Lattice:
     def set_kernel(self, kernel: int) -> None:
         """int8 pass kernel: KERNEL_AUTO, KERNEL_STRIP or KERNEL_TMA."""
         _check(self._lib.ising_set_kernel(self._h, int(kernel)), "ising_set_kernel")
+
+    def set_rule(self, rule: int) -> None:
+        """Local update rule of later sweeps: RULE_METROPOLIS or RULE_HEATBATH."""
+        _check(self._lib.ising_set_rule(self._h, int(rule)), "ising_set_rule")
 
     @property
     def handle(self) -> int:

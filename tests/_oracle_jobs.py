@@ -4,10 +4,10 @@ is a plain call into ``oracle``; nothing here touches the GPU."""
 import numpy as np
 
 
-def run(dims, L, beta, seed, start, nsweeps, every, s=None, t0=0):
+def run(dims, L, beta, seed, start, nsweeps, every, s=None, t0=0, heatbath=False):
     import oracle
     s_out, E, M = oracle.run(dims, L, beta, seed, nsweeps, measure_every=every, start=start,
-                             s=s, t0=t0)
+                             s=s, t0=t0, heatbath=heatbath)
     return s_out, E, M
 
 

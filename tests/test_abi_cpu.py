@@ -79,3 +79,25 @@ def test_engine_thresholds_match_oracle_and_mpmath(lib, orc):
     for bad in (0.0, -1.0, float("nan")):
         with pytest.raises(Exception):
             compute_thresholds(2, bad)
+
+
+def test_engine_heatbath_thresholds_match_oracle_and_mpmath(lib, orc):
+    from oracle import exact
+    from paper_cs_0312006_gb300.engine import compute_thresholds_heatbath
+    rng = np.random.default_rng(4)
+    betas = [0.4406868, 0.2216544, 1e-30, 1e-12, 1e-9, 3.0, 50.0, math.inf] + \
+        list(rng.uniform(0.01, 2.0, size=300))
+    for beta in betas:
+        for dims in (2, 3):
+            eng = compute_thresholds_heatbath(dims, beta)
+            assert eng.tolist() == orc.thresholds_heatbath(dims, beta).tolist(), (dims, beta)
+            if math.isfinite(beta) and beta < 10:
+                assert eng.tolist() == exact.exact_thresholds_heatbath(dims, beta)
+    for bad in (0.0, -1.0, float("nan")):
+        with pytest.raises(Exception):
+            compute_thresholds_heatbath(3, bad)
+
+
+def test_set_rule_rejects_null_and_unknown(lib):
+    assert lib.ising_set_rule(None, 0) == -1
+    assert lib.ising_compute_thresholds_heatbath(4, ctypes.c_double(0.3), None) == -1
