@@ -53,16 +53,25 @@ BASE_SEED = 20031109
 BYTES_PER_UPDATE_INT8 = 3  # per colour pass: read own N/2, read other N/2, write own N/2
 
 
-# DRAM bytes per site update of the two pass kernels on this workload, from one
+# DRAM bytes per site update of the pass kernels, from one
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` capture of the
-# bench's own run (profiles/dram_traffic_bench_scan_L8192.md).  They describe
-# the kernel sources whose hash is recorded; any change to those sources makes
-# the bench report "traffic": null until the capture is redone.
+# bench's own run per workload (profiles/dram_traffic_bench_scan_L8192.md,
+# profiles/dram_traffic_bench_big_L65536.md).  They describe the kernel sources
+# whose hash is recorded; any change to those sources makes the bench report
+# "traffic": null until the capture is redone.
 TRAFFIC = {
-    "int8": {"bytes_per_update": 1.9656, "sha1": "593903d67fa083d7bf84ff7ab3b969c5774fbb62",
-             "sources": ["sweep_int8_tma.cu", "pass_bodies.cuh", "ising_device.cuh"]},
-    "bitpack": {"bytes_per_update": 0.2230, "sha1": "7eaa6f9995ad8b6cc3269ccc2ec50aaa3a3cf8b8",
-                "sources": ["sweep_bitpack.cu", "pass_bodies.cuh", "ising_device.cuh"]},
+    ("scan", "int8"): {"bytes_per_update": 1.9656,
+                       "sha1": "593903d67fa083d7bf84ff7ab3b969c5774fbb62",
+                       "sources": ["sweep_int8_tma.cu", "pass_bodies.cuh", "ising_device.cuh"]},
+    ("scan", "bitpack"): {"bytes_per_update": 0.2230,
+                          "sha1": "7eaa6f9995ad8b6cc3269ccc2ec50aaa3a3cf8b8",
+                          "sources": ["sweep_bitpack.cu", "pass_bodies.cuh", "ising_device.cuh"]},
+    ("big", "int8"): {"bytes_per_update": 3.0038,
+                      "sha1": "3510fb0f7769ee1940b19835f50c6f7aa35e3752",
+                      "sources": ["sweep_int8.cu", "pass_bodies.cuh", "ising_device.cuh"]},
+    ("big", "bitpack"): {"bytes_per_update": 0.3828,
+                         "sha1": "2cea39923be5e5d0369d4c02c5b9068936caf58a",
+                         "sources": ["sweep_bitpack.cu", "pass_bodies.cuh", "ising_device.cuh"]},
 }
 
 
@@ -75,8 +84,11 @@ def kernel_sources_sha1(names) -> str:
     return h.hexdigest()
 
 
-def measured_traffic(layout: str, updates_per_launch: int, rule: str = "metropolis"):
-    t = TRAFFIC[layout]
+def measured_traffic(workload: str, layout: str, updates_per_launch: int,
+                     rule: str = "metropolis"):
+    t = TRAFFIC.get((workload, layout))
+    if t is None:
+        return None
     if rule != "metropolis":  # the capture covers the Metropolis instances only
         return None
     if t["bytes_per_update"] is None or kernel_sources_sha1(t["sources"]) != t["sha1"]:
@@ -100,11 +112,17 @@ def scan_betas():
 
 
 def workload_config(L: int, steps: int, lattices: int = N_BETA,
-                    rule: str = "metropolis") -> dict:
+                    rule: str = "metropolis", big: bool = False) -> dict:
     name = "checkerboard Metropolis" if rule == "metropolis" else "checkerboard heat-bath"
-    return {"workload": f"2D Ising beta scan ({name}): L={L} square lattice, 16 betas evenly "
-                        f"spaced in [0.30,0.60], cold start, {steps} sweeps, E/M every sweep, "
-                        f"int8 and bit-packed layouts",
+    if big:
+        text = (f"2D Ising single lattice ({name}): L={L} square lattice ({L * L} sites, "
+                f"{L * L // 2 // 2 ** 20} MiB per colour in int8), beta=0.30, cold start, "
+                f"{steps} sweeps, E/M every sweep, int8 and bit-packed layouts")
+    else:
+        text = (f"2D Ising beta scan ({name}): L={L} square lattice, 16 betas evenly spaced in "
+                f"[0.30,0.60], cold start, {steps} sweeps, E/M every sweep, int8 and bit-packed "
+                f"layouts")
+    return {"workload": text,
             "rule": rule,
             "lattices_per_gpu": lattices,
             "l2": f"inputs larger than L2: a step touches {lattices} x L^2 bytes of int8 spins",
@@ -279,12 +297,15 @@ def run_gpu(args, world, rank, local):
     if args.layout != "both":
         layouts = [x for x in layouts if x[0] == args.layout]
     stream = torch.cuda.current_stream()
-    int8_kernel = {"strip": engine.KERNEL_STRIP, "tma": engine.KERNEL_TMA}[args.int8_kernel]
+    int8_kernel = {"auto": engine.KERNEL_AUTO, "strip": engine.KERNEL_STRIP,
+                   "tma": engine.KERNEL_TMA}[args.int8_kernel]
     rule = {"metropolis": engine.RULE_METROPOLIS, "heatbath": engine.RULE_HEATBATH}[args.rule]
     sets = {name: [engine.Lattice(2, L, b, BASE_SEED + 16 * rank + j, layout=lay,
                                   start=engine.COLD_UP, stream=stream, kernel=int8_kernel,
                                   rule=rule)
                    for j, b in enumerate(betas)] for name, lay in layouts}
+
+    int8_ran = sets["int8"][0].kernel() if "int8" in sets else -1
 
     def barrier():
         if world > 1:
@@ -356,12 +377,13 @@ def run_gpu(args, world, rank, local):
             bytes_per_pass = BYTES_PER_UPDATE_INT8 * updates_per_pass
             achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
             rtag = "" if args.rule == "metropolis" else ",heatbath"
-            kname = (f"pass_int8_tma<2,measure{rtag}>" if args.int8_kernel == "tma" else
+            kname = (f"pass_int8_tma<2,measure{rtag}>" if int8_ran == engine.KERNEL_TMA else
                      f"pass_int8_strip<2,measure{rtag}>")
             rooflines[name] = {"kernel": kname, "bound": "hbm",
                                "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                                "frac": achieved / peak_hbm,
-                               "traffic": measured_traffic("int8", updates_per_pass, args.rule),
+                               "traffic": measured_traffic(args.workload, "int8",
+                                                           updates_per_pass, args.rule),
                                "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
                                "peak_source": f"{peak_kind} hbm_gbs (copy)"}
         else:
@@ -371,8 +393,8 @@ def run_gpu(args, world, rank, local):
             rooflines[name] = {"kernel": f"pass_packed<2,measure{rtag}>", "bound": "alu",
                                "achieved": achieved, "peak": peak, "unit": "site updates/s",
                                "frac": achieved / peak,
-                               "traffic": measured_traffic("bitpack", updates_per_pass,
-                                                           args.rule),
+                               "traffic": measured_traffic(args.workload, "bitpack",
+                                                           updates_per_pass, args.rule),
                                "launch_ms": pass_ms,
                                "peak_source": "derived: SMs x 32 wide multiplies/clk / 18 per "
                                               "Philox call x 4 sites x median SM clock"}
@@ -428,7 +450,8 @@ def run_gpu(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
         "data": "synthetic",
-        "config": workload_config(L, args.steps, len(betas), args.rule),
+        "config": workload_config(L, args.steps, len(betas), args.rule,
+                                  big=args.workload == "big"),
         "layouts": layout_stats,
         "roofline": rooflines.get("int8") or rooflines.get("bitpack"),
         "roofline_bitpack": rooflines.get("bitpack"),
@@ -624,11 +647,11 @@ def main():
     ap.add_argument("--layout", choices=["both", "int8", "bitpack"], default="both")
     ap.add_argument("--rule", choices=["metropolis", "heatbath"], default="metropolis",
                     help="local update rule of the scan workload")
-    ap.add_argument("--int8-kernel", choices=["strip", "tma"], default="tma",
+    ap.add_argument("--int8-kernel", choices=["auto", "strip", "tma"], default="auto",
                     help="int8 pass: register-window strips or shared-memory tiles staged by "
                          "bulk (TMA) copies")
     ap.add_argument("--workload", choices=["scan", "batched", "serving", "philox", "small",
-                                           "cubic"],
+                                           "cubic", "big"],
                     default="scan",
                     help="scan: the 2D L=8192 beta scan (default line); batched: 2048 "
                          "lattices in one launch vs one launch per lattice; serving: Poisson "
@@ -637,6 +660,8 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=500)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batched: fixed launch shape")
+    ap.add_argument("--big-L", type=int, default=65536,
+                    help="big: linear size of the single 2D lattice")
     ap.add_argument("--cubic-L", type=int, default=256)
     ap.add_argument("--cubic-sweeps", type=int, default=1000)
     ap.add_argument("--serve-jobs", type=int, default=2000)
@@ -666,6 +691,11 @@ def main():
         return run_small_workload(args)
     if args.workload == "cubic" and args.impl != "reference":
         return run_cubic_workload(args)
+    if args.workload == "big":  # one lattice far larger than L2
+        args.L = args.big_L
+        args.lattices = 1
+        if args.impl == "engine":
+            args.no_e2e = True  # the scan's e2e leg sizes host buffers per lattice set
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_gpu(args, world, rank, local)

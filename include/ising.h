@@ -48,7 +48,7 @@ enum {
 
 /* Kernels for the int8 colour pass (same results; see ising_set_kernel). */
 enum {
-    ISING_KERNEL_AUTO = 0,  /* staged for 2D with L >= 4096, strip otherwise (measured) */
+    ISING_KERNEL_AUTO = 0,  /* staged for 2D with 4096 <= L <= 16384, strip otherwise (measured) */
     ISING_KERNEL_STRIP = 1, /* per-thread row strips, neighbour rows in registers */
     ISING_KERNEL_TMA = 2    /* tiles staged in shared memory by bulk (TMA) copies */
 };
@@ -157,6 +157,12 @@ int ising_export_device(ising_lattice *lat, int8_t *dev_out);
  * for the bit-packed layout, the choice is recorded but the general kernels
  * run.  Results never depend on it. */
 int ising_set_kernel(ising_lattice *lat, int kernel);
+
+/* The int8 pass kernel the lattice's sweeps run, with ISING_KERNEL_AUTO and the
+ * size limits resolved: ISING_KERNEL_TMA or ISING_KERNEL_STRIP (which also
+ * stands for the general kernel used when L/2 is not a multiple of 16).  For
+ * the bit-packed layout *kernel is set to -1. */
+int ising_get_kernel(const ising_lattice *lat, int *kernel);
 
 /* The engine's counter-based generator on the device: for c0 = 0..n-1,
  * dev_out[4*c0 + j] = word j of Philox4x32-10(key = seed; counter =

@@ -75,6 +75,9 @@ def _load():
         lib.orc_half_sweep_rule.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64,
                                             u32p, ctypes.c_uint32, ctypes.c_int, ctypes.c_int]
         lib.orc_half_sweep_rule.restype = ctypes.c_int
+        lib.orc_site_update.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64, u32p,
+                                        ctypes.c_uint32, ctypes.c_int64, ctypes.c_int]
+        lib.orc_site_update.restype = ctypes.c_int
         lib.orc_thresholds_heatbath.argtypes = [ctypes.c_int, ctypes.c_double, u32p]
         lib.orc_thresholds_heatbath.restype = ctypes.c_int
         lib.orc_sweep.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64,
@@ -161,6 +164,22 @@ def half_sweep(dims: int, L: int, s: np.ndarray, seed: int, thr: np.ndarray,
                                      _ptr(tab, ctypes.c_uint32), t, c, rule)
     if rc != 0:
         raise ValueError(f"orc_half_sweep -> {rc}")
+
+
+def site_update(dims: int, L: int, s: np.ndarray, seed: int, thr: np.ndarray, t: int,
+                sites, rule: int = METROPOLIS_RULE) -> np.ndarray:
+    """The spins that the canonical sites ``sites`` hold after their colour's
+    pass of sweep t, each decided from the state ``s`` that pass starts from
+    (the colour pass's own decision, one site at a time)."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    src = np.asarray(thr, dtype=np.uint32).ravel()
+    tab = np.zeros(7, dtype=np.uint32)
+    tab[:min(7, src.size)] = src[:7]
+    lib = _load()
+    sp = _ptr(s, ctypes.c_int8)
+    tp = _ptr(tab, ctypes.c_uint32)
+    return np.array([lib.orc_site_update(dims, L, sp, seed, tp, t, int(i), rule)
+                     for i in np.asarray(sites).ravel()], dtype=np.int8)
 
 
 def sweep(dims: int, L: int, s: np.ndarray, seed: int, thr: np.ndarray,

@@ -297,6 +297,23 @@ static int heatbath_flip(int dims, int k, const uint32_t thb[7], uint64_t seed,
 /* Draw for site i in sweep t: Philox(seed; hh>>2, t, c, TAG_SWEEP)[hh & 3] */
 /* with hh = i >> 1 (the site's index within its colour).  Requires L even. */
 /* ------------------------------------------------------------------------ */
+/* The decision for one site i = (x, y, z) of colour c in sweep t, reading */
+/* its own spin and its neighbours from s: returns 1 iff the spin flips.    */
+static int site_flips(int dims, int L, const int8_t *s, uint64_t seed,
+                      const uint32_t *thr, uint32_t t, int c, int rule,
+                      int x, int y, int z)
+{
+    int64_t i = (int64_t)z * L * L + (int64_t)y * L + x;
+    int h = neighbour_sum(dims, L, s, x, y, z);
+    int k = s[i] * h;
+    int64_t hh = i >> 1;
+    return rule == 0
+        ? accept_flip(k, thr, seed, (uint32_t)(hh >> 2), t, (uint32_t)c,
+                      TAG_SWEEP, (unsigned)(hh & 3))
+        : heatbath_flip(dims, k, thr, seed, (uint32_t)(hh >> 2), t,
+                        (uint32_t)c, TAG_SWEEP, (unsigned)(hh & 3));
+}
+
 int orc_half_sweep_rule(int dims, int L, int8_t *s, uint64_t seed,
                         const uint32_t *thr, uint32_t t, int c, int rule)
 {
@@ -310,17 +327,27 @@ int orc_half_sweep_rule(int dims, int L, int8_t *s, uint64_t seed,
             for (int x = 0; x < L; ++x) {
                 if (((x + y + z) & 1) != c) continue;
                 int64_t i = (int64_t)z * LL + (int64_t)y * L + x;
-                int h = neighbour_sum(dims, L, s, x, y, z);
-                int k = s[i] * h;
-                int64_t hh = i >> 1;
-                int flip = rule == 0
-                    ? accept_flip(k, thr, seed, (uint32_t)(hh >> 2), t, (uint32_t)c,
-                                  TAG_SWEEP, (unsigned)(hh & 3))
-                    : heatbath_flip(dims, k, thr, seed, (uint32_t)(hh >> 2), t,
-                                    (uint32_t)c, TAG_SWEEP, (unsigned)(hh & 3));
-                if (flip) s[i] = (int8_t)-s[i];
+                if (site_flips(dims, L, s, seed, thr, t, c, rule, x, y, z))
+                    s[i] = (int8_t)-s[i];
             }
     return 0;
+}
+
+/* The spin that site i (canonical index) holds after its colour's pass of  */
+/* sweep t, given the state s that pass starts from (for a white site: the  */
+/* black sites already updated).  The same decision as the colour pass, for */
+/* checking a large lattice one sampled site at a time.                     */
+int orc_site_update(int dims, int L, const int8_t *s, uint64_t seed,
+                    const uint32_t *thr, uint32_t t, int64_t i, int rule)
+{
+    if (dims != 2 && dims != 3) return 0;
+    if (L < 2 || (L & 1)) return 0;
+    int64_t n = dims == 3 ? (int64_t)L * L * L : (int64_t)L * L;
+    if (i < 0 || i >= n) return 0;
+    int x = (int)(i % L), y = (int)((i / L) % L), z = dims == 3 ? (int)(i / ((int64_t)L * L)) : 0;
+    int c = (x + y + z) & 1;
+    int f = site_flips(dims, L, s, seed, thr, t, c, rule, x, y, z);
+    return f ? -s[i] : s[i];
 }
 
 /* Metropolis colour pass (rule 0). */

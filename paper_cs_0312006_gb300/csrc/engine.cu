@@ -204,6 +204,12 @@ int check_timeout(ising_lattice* h) {
     return ISING_ETIMEOUT;
 }
 
+bool uses_tma(const ising_lattice* h) {
+    return h->layout != ISING_BITPACK && ising::int8_tma_ok(h->dims, h->L) &&
+           (h->kernel == ISING_KERNEL_TMA ||
+            (h->kernel == ISING_KERNEL_AUTO && ising::int8_tma_preferred(h->dims, h->L)));
+}
+
 int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     PassArgs a;
     a.own = h->col[c];
@@ -219,12 +225,7 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     a.c = c;
     if (h->layout == ISING_BITPACK)
         ISING_CHECK(ising::packed_pass(a, h->dims, slot != nullptr, h->rule, *h->dp, h->stream));
-    else if (ising::int8_tma_ok(h->dims, h->L) &&
-             (h->kernel == ISING_KERNEL_TMA ||
-              // AUTO: the staged kernel where it measured faster (2D, long rows);
-              // with short rows (3D, small 2D) its tiles hold about one vector
-              // per thread and barriers dominate, so the strip kernel runs
-              (h->kernel == ISING_KERNEL_AUTO && h->dims == 2 && h->L >= 4096)))
+    else if (uses_tma(h))
         ISING_CHECK(ising::int8_pass_tma(a, h->dims, slot != nullptr, h->rule, *h->dp,
                                          h->dp->d_err, g_inject_timeout.load() ? 16u : 0u,
                                          h->stream));
@@ -496,6 +497,13 @@ int ising_set_kernel(ising_lattice* h, int kernel) {
     if (kernel != ISING_KERNEL_AUTO && kernel != ISING_KERNEL_STRIP && kernel != ISING_KERNEL_TMA)
         return ISING_EINVAL;
     h->kernel = kernel;
+    return ISING_OK;
+}
+
+int ising_get_kernel(const ising_lattice* h, int* kernel) {
+    if (!h || !kernel) return ISING_EINVAL;
+    *kernel = h->layout == ISING_BITPACK ? -1
+                                         : (uses_tma(h) ? ISING_KERNEL_TMA : ISING_KERNEL_STRIP);
     return ISING_OK;
 }
 

@@ -74,6 +74,8 @@ cudaError_t int8_import(int8_t* col0, int8_t* col1, const int8_t* in, int L, int
 
 // int8 layout, inputs staged by bulk copies (sweep_int8_tma.cu)
 bool int8_tma_ok(int dims, int L);
+// ISING_KERNEL_AUTO's choice of the staged kernel (measured; see the definition)
+bool int8_tma_preferred(int dims, int L);
 cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, int rule,
                           const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st);
 

@@ -285,6 +285,18 @@ static cudaError_t int8_pass_tma_rule(const PassArgs& a, int dims, bool measure,
                    : launch_tma_t<3, false, RULE>(a, dp, err, extra_tx, st);
 }
 
+// Where the staged kernel measured faster than the strip kernel on GB300: 2D
+// with long rows (L >= 4096) while two CTAs' stages fit in one SM's shared
+// memory (L <= 16384: 8.38e11 against 7.76e11 site updates/s per pass at
+// L = 16384; at L = 32768 one CTA per SM gives 7.24e11 against the strip
+// kernel's 8.02e11).  With short rows (3D, small 2D) a tile holds about one
+// vector per thread and its barriers dominate.
+bool int8_tma_preferred(int dims, int L) {
+    if (dims != 2 || L < 4096 || !int8_tma_ok(dims, L)) return false;
+    const int W = L / 2, R = tile_rows(L);
+    return 2 * (size_t)kStages * (size_t)(2 * R + 2) * W <= 200 * 1024;
+}
+
 cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, int rule,
                           const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st) {
     return rule == kRuleHeatBath

@@ -86,6 +86,7 @@ def load_library():
             "ising_get_info": ([P, ctypes.POINTER(IsingInfo)], ctypes.c_int),
             "ising_synchronize": ([P], ctypes.c_int),
             "ising_set_kernel": ([P, ctypes.c_int], ctypes.c_int),
+            "ising_get_kernel": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "ising_test_inject_timeout": ([ctypes.c_int], ctypes.c_int),
             "ising_philox_fill": ([P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint32, ctypes.c_uint64, P], ctypes.c_int),
@@ -252,6 +253,12 @@ class Lattice:
     def set_kernel(self, kernel: int) -> None:
         """int8 pass kernel: KERNEL_AUTO, KERNEL_STRIP or KERNEL_TMA."""
         _check(self._lib.ising_set_kernel(self._h, int(kernel)), "ising_set_kernel")
+
+    def kernel(self) -> int:
+        """The int8 pass kernel the sweeps run (KERNEL_STRIP / KERNEL_TMA; -1 if packed)."""
+        k = ctypes.c_int(0)
+        _check(self._lib.ising_get_kernel(self._h, ctypes.byref(k)), "ising_get_kernel")
+        return k.value
 
     def set_rule(self, rule: int) -> None:
         """Local update rule of later sweeps: RULE_METROPOLIS or RULE_HEATBATH."""

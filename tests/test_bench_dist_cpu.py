@@ -44,5 +44,17 @@ def test_two_gloo_ranks_agree_on_the_slowest_time():
 def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.25, 1) == 3.25
-    assert bench.measured_traffic("int8", 10) in (None, pytest.approx(
-        bench.TRAFFIC["int8"]["bytes_per_update"] * 10 if bench.TRAFFIC["int8"]["bytes_per_update"] else 0))
+
+
+
+def test_measured_traffic_follows_the_kernel_sources():
+    """A traffic figure is reported only for the sources it was captured on."""
+    import bench
+    for (workload, layout), t in bench.TRAFFIC.items():
+        got = bench.measured_traffic(workload, layout, 10)
+        if bench.kernel_sources_sha1(t["sources"]) == t["sha1"]:
+            assert got == pytest.approx(10 * t["bytes_per_update"])
+        else:
+            assert got is None
+        assert bench.measured_traffic(workload, layout, 10, rule="heatbath") is None
+    assert bench.measured_traffic("cubic", "int8", 10) is None

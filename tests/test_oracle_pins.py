@@ -316,3 +316,21 @@ def test_run_records_and_resume(orc):
     assert np.array_equal(E_a, np.concatenate([E_b1, E_b2]))
     assert np.array_equal(M_a, np.concatenate([M_b1, M_b2]))
     assert E_a[-1] == orc.energy(2, 16, s_a) and M_a[-1] == orc.magnetization(2, 16, s_a)
+
+
+@pytest.mark.parametrize("dims,L,rule", [(2, 10, 0), (2, 12, 1), (3, 6, 0), (3, 4, 1)])
+def test_site_update_is_the_pass_decision(orc, dims, L, rule):
+    """site_update (used to check huge lattices one sampled site at a time)
+    gives, site by site, the spins the colour pass writes."""
+    seed, beta, t = 13, 0.37, 4
+    thr = orc.thresholds_heatbath(dims, beta) if rule else orc.thresholds(dims, beta)
+    s = orc.init(dims, L, seed, oracle.HOT)
+    n = L ** dims
+    idx = np.arange(n)
+    x, y, z = idx % L, (idx // L) % L, idx // (L * L)
+    colour = (x + y + (z if dims == 3 else 0)) % 2
+    for c in (0, 1):
+        sites = np.nonzero(colour == c)[0]
+        got = orc.site_update(dims, L, s, seed, thr, t, sites, rule=rule)
+        orc.half_sweep(dims, L, s, seed, thr, t, c, rule=rule)
+        assert np.array_equal(got, s[sites])
