@@ -30,7 +30,9 @@ offset by 16 * rank), no collective on the data path; scaling "weak".
 
 --rule heatbath runs the same workload with the heat-bath update rule (every
 site draws; flip iff u < floor(2^32 / (1 + exp(beta dE)))) instead of the
-Metropolis rule, in the engine and in the oracle arms alike.
+Metropolis rule, in the engine and in the oracle arms alike.  --rule demon
+runs Creutz's deterministic demon dynamics (int8 layout only): cold spins and
+demons (qmax 3) drawn at each lattice's beta; no draws, 5 bytes per update.
 """
 from __future__ import annotations
 
@@ -43,6 +45,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -51,6 +55,8 @@ L_SCAN = 8192
 N_BETA = 16
 BASE_SEED = 20031109
 BYTES_PER_UPDATE_INT8 = 3  # per colour pass: read own N/2, read other N/2, write own N/2
+BYTES_PER_UPDATE_DEMON = 5  # and read + write the own colour's demons (1 byte per site)
+DEMON_QMAX = 3
 
 
 # DRAM bytes per site update of the pass kernels, from one
@@ -113,7 +119,8 @@ def scan_betas():
 
 def workload_config(L: int, steps: int, lattices: int = N_BETA,
                     rule: str = "metropolis", big: bool = False) -> dict:
-    name = "checkerboard Metropolis" if rule == "metropolis" else "checkerboard heat-bath"
+    name = {"metropolis": "checkerboard Metropolis", "heatbath": "checkerboard heat-bath",
+            "demon": f"deterministic demon dynamics, qmax={DEMON_QMAX}"}[rule]
     if big:
         text = (f"2D Ising single lattice ({name}): L={L} square lattice ({L * L} sites, "
                 f"{L * L // 2 // 2 ** 20} MiB per colour in int8), beta=0.30, cold start, "
@@ -204,6 +211,26 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
+def oracle_demon_rate(budget_s: float, L: int, betas, n_lattices: int):
+    """The oracle's demon dynamics on cold lattices with demons at each beta."""
+    import oracle
+    from paper_cs_0312006_gb300 import workloads
+    oracle.build()
+    done, j, spent = 0, 0, 0.0
+    while True:
+        b = betas[j % len(betas)]
+        q = workloads.demon_field(L * L, DEMON_QMAX, b, BASE_SEED + (j % len(betas)))
+        s = np.ones(L * L, dtype=np.int8)
+        t0 = time.perf_counter()
+        oracle.run_demon(2, L, s, q, DEMON_QMAX, 1, measure_every=1)
+        spent += time.perf_counter() - t0
+        done += L * L
+        j += 1
+        if spent >= budget_s or j >= n_lattices:
+            break
+    return done / spent, f"{j} single demon sweeps (E/M after each) of 2D L={L} lattices"
+
+
 def oracle_sample_rate(budget_s: float, L: int, betas, n_lattices: int, heatbath: bool = False):
     """Time the oracle (as it stands) sweeping cold-started lattices of size L
     with E/M recomputed after each sweep; returns (updates/s, description)."""
@@ -238,6 +265,23 @@ def run_reference(args, world, rank):
     import oracle
     oracle.build()
     hb = args.rule == "heatbath"
+    if args.rule == "demon":
+        from paper_cs_0312006_gb300 import workloads
+        # every lattice's demons are drawn before the clock starts
+        fields = [workloads.demon_field(L * L, DEMON_QMAX, b, BASE_SEED + j)
+                  for j, b in enumerate(betas)]
+        cold = np.ones(L * L, dtype=np.int8)
+
+        def step(j):
+            oracle.run_demon(2, L, cold, fields[j], DEMON_QMAX, 1)
+
+        for w in range(args.warmup):
+            step(w % N_BETA)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step(k % N_BETA)
+        dt = time.perf_counter() - t0
+        return _reference_line(args, world, L, dt, "demon sweep")
     for w in range(args.warmup):
         oracle.run(2, L, betas[w % N_BETA], BASE_SEED + w, 1, measure_every=1,
                    start=oracle.COLD_UP, heatbath=hb)
@@ -247,8 +291,13 @@ def run_reference(args, world, rank):
         oracle.run(2, L, betas[j], BASE_SEED + j, 1, measure_every=1, start=oracle.COLD_UP,
                    heatbath=hb)
     dt = time.perf_counter() - t0
+    return _reference_line(args, world, L, dt, "sweep")
+
+
+def _reference_line(args, world, L, dt, what):
+    total_steps = args.steps + args.warmup
     value = args.steps * L * L / dt
-    sample = (f"each step: one sweep (cold start, E/M recomputed) of one 2D L={L} lattice "
+    sample = (f"each step: one {what} (cold start, E/M recomputed) of one 2D L={L} lattice "
               f"of the 16-beta scan (beta cycling), single-threaded C oracle; the workload's "
               f"L={args.L} is sampled at L={L} so that {total_steps} steps end in minutes")
     line = {
@@ -296,15 +345,24 @@ def run_gpu(args, world, rank, local):
     layouts = [("int8", engine.INT8), ("bitpack", engine.BITPACK)]
     if args.layout != "both":
         layouts = [x for x in layouts if x[0] == args.layout]
+    if args.rule == "demon":  # the demon dynamics runs on the int8 layout
+        layouts = [("int8", engine.INT8)]
     stream = torch.cuda.current_stream()
     int8_kernel = {"auto": engine.KERNEL_AUTO, "strip": engine.KERNEL_STRIP,
                    "tma": engine.KERNEL_TMA}[args.int8_kernel]
-    rule = {"metropolis": engine.RULE_METROPOLIS, "heatbath": engine.RULE_HEATBATH}[args.rule]
+    rule = {"metropolis": engine.RULE_METROPOLIS, "heatbath": engine.RULE_HEATBATH,
+            "demon": engine.RULE_METROPOLIS}[args.rule]
     sets = {name: [engine.Lattice(2, L, b, BASE_SEED + 16 * rank + j, layout=lay,
                                   start=engine.COLD_UP, stream=stream, kernel=int8_kernel,
                                   rule=rule)
                    for j, b in enumerate(betas)] for name, lay in layouts}
 
+    if args.rule == "demon":
+        from paper_cs_0312006_gb300 import workloads
+        for j, lat in enumerate(sets["int8"]):
+            lat.set_demons(workloads.demon_field(n_sites, DEMON_QMAX, betas[j],
+                                                 BASE_SEED + 16 * rank + j), qmax=DEMON_QMAX)
+            lat.set_rule(engine.RULE_DEMON)
     int8_ran = sets["int8"][0].kernel() if "int8" in sets else -1
 
     def barrier():
@@ -373,7 +431,17 @@ def run_gpu(args, world, rank, local):
         layout_stats[name] = {"value": world * len(betas) * n_sites * args.steps / (part_ms / 1e3),
                               "ms": part_ms, "pass_ms": pass_ms,
                               "pass_updates_per_s": updates_per_pass / (pass_ms / 1e3)}
-        if name == "int8":
+        if name == "int8" and args.rule == "demon":
+            bytes_per_pass = BYTES_PER_UPDATE_DEMON * updates_per_pass
+            achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
+            rooflines[name] = {"kernel": "pass_demon_strip<2,measure>", "bound": "hbm",
+                               "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                               "frac": achieved / peak_hbm,
+                               "traffic": measured_traffic(args.workload, "demon",
+                                                           updates_per_pass),
+                               "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
+                               "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+        elif name == "int8":
             bytes_per_pass = BYTES_PER_UPDATE_INT8 * updates_per_pass
             achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
             rtag = "" if args.rule == "metropolis" else ",heatbath"
@@ -439,7 +507,11 @@ def run_gpu(args, world, rank, local):
         return 0
 
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.rule == "demon":
+        rate, sample = oracle_demon_rate(args.cpu_seconds, L_SCAN, betas, 64)
+        cpu = {"value": rate, "unit": "site updates/s", "cores": 1, "kind": "oracle",
+               "sample": sample}
+    elif world == 1 and not args.no_cpu_baseline:
         rate, sample = oracle_sample_rate(args.cpu_seconds, L_SCAN, betas, 64,
                                           heatbath=args.rule == "heatbath")
         cpu = {"value": rate, "unit": "site updates/s", "cores": 1, "kind": "oracle",
@@ -645,7 +717,7 @@ def main():
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--L", type=int, default=L_SCAN)
     ap.add_argument("--layout", choices=["both", "int8", "bitpack"], default="both")
-    ap.add_argument("--rule", choices=["metropolis", "heatbath"], default="metropolis",
+    ap.add_argument("--rule", choices=["metropolis", "heatbath", "demon"], default="metropolis",
                     help="local update rule of the scan workload")
     ap.add_argument("--int8-kernel", choices=["auto", "strip", "tma"], default="auto",
                     help="int8 pass: register-window strips or shared-memory tiles staged by "

@@ -64,10 +64,19 @@ enum {
  *       neighbours, P(S') / (P(S) + P(S')) = 1 / (1 + exp(beta dE)) for the
  *       flipped state: every site draws and flips iff
  *       u < floor(2^32 / (1 + exp(4 beta (dims - d)))).
+ *   DEMON: Creutz's deterministic dynamics, which Sec. 2.2 cites (checkerboard
+ *       sweeps, no random numbers).  Every site carries a demon of energy 4q,
+ *       q = 0..qmax; a site flips iff 0 <= q - (dims - d) <= qmax, and its
+ *       demon keeps q - (dims - d), so E + 4 sum q is conserved (the
+ *       microcanonical ensemble; beta and the draws are not used).  After each
+ *       sweep every demon moves on by one half row within its colour: from the
+ *       colour-c site in half row r = y + L z, half column x >> 1, to the
+ *       colour-c site in half row r + 1 (mod L^(dims-1)), same half column.
  */
 enum {
     ISING_RULE_METROPOLIS = 0,
-    ISING_RULE_HEATBATH = 1
+    ISING_RULE_HEATBATH = 1,
+    ISING_RULE_DEMON = 2  /* deterministic demon dynamics, int8 layout (ising_set_demons) */
 };
 
 /* Initial states (Sec. 2.2: spins up with probability p). */
@@ -194,9 +203,21 @@ int ising_compute_thresholds(int dims, double beta, uint32_t out[3]);
 
 /* Select the local update rule (ISING_RULE_*) for the lattice's later
  * sweeps; the default is ISING_RULE_METROPOLIS.  Both thresholds tables are
- * built at ising_create, so this never fails for a valid handle and rule
- * (ISING_EINVAL otherwise).  The sweep counter and records are unchanged. */
+ * built at ising_create; ISING_RULE_DEMON needs demons (ising_set_demons)
+ * first.  ISING_EINVAL for an invalid handle or rule.  The sweep counter and
+ * records are unchanged. */
 int ising_set_rule(ising_lattice *lat, int rule);
+
+/* Load the demons of ISING_RULE_DEMON (int8 layout only; ISING_EINVAL for the
+ * bit-packed layout).  host_q: L^dims bytes in canonical order, each <= qmax;
+ * or NULL, every demon = fill (0 <= fill <= qmax).  1 <= qmax <= 63.  The
+ * first call allocates two device arrays the size of the spin arrays.  Syncs.
+ * The spins, the sweep counter and the rule are unchanged. */
+int ising_set_demons(ising_lattice *lat, const uint8_t *host_q, int fill, int qmax);
+
+/* The demons in canonical order (L^dims bytes of host memory), as the next
+ * sweep will see them; ISING_EINVAL if none were loaded.  Syncs. */
+int ising_get_demons(ising_lattice *lat, uint8_t *host_out);
 
 /* The heat-bath thresholds for (dims, beta) without a handle or a GPU:
  * out[d] = floor(2^32 / (1 + exp(4 beta (dims - d)))) for d = 0..2*dims
@@ -248,8 +269,10 @@ typedef struct ising_batch_opts {
  * ising_batch_launch and ising_batch_sync they must not be used directly, and
  * they must outlive the batch.  Device memory: a job table (96 B per lattice).
  * Lattices of each update rule (ISING_RULE_*) form their own queues, run by
- * one persistent launch per rule present; a lattice's rule must not change
- * while the batch exists (ising_batch_launch then returns ISING_EINVAL).
+ * one persistent launch per rule present; demon-dynamics lattices are
+ * advanced by the per-lattice kernels like the huge ones.  A lattice's rule
+ * must not change while the batch exists (ising_batch_launch then returns
+ * ISING_EINVAL).
  */
 int ising_batch_create(ising_batch **out, ising_lattice *const *lats, int n,
                        const int64_t *sweeps, const int *measure_every,
@@ -294,7 +317,8 @@ void ising_batch_destroy(ising_batch *b);
  *                  The handles' own record buffers are not touched.
  *   opts           block_threads, cluster_size and big_sites as for
  *                  ising_batch_create (NULL: defaults); every lattice runs in
- *                  the persistent kernel (huge_sites and use_graph are ignored).
+ *                  the persistent kernel (huge_sites and use_graph are ignored),
+ *                  so ISING_RULE_DEMON lattices are refused (ISING_EINVAL).
  * The spins and sweep counters of the handles advance as with ising_sweep.
  * The first call on a device looks up the array's device address and the
  * resident grid size; make that first call before any stream capture.

@@ -90,6 +90,18 @@ def _load():
                                 ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                 i64p, i64p, ctypes.c_int64]
         lib.orc_run.restype = ctypes.c_int64
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        lib.orc_demon_half_sweep.argtypes = [ctypes.c_int, ctypes.c_int, i8p, u8p, ctypes.c_int,
+                                             ctypes.c_int]
+        lib.orc_demon_half_sweep.restype = ctypes.c_int
+        lib.orc_demon_shift.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int]
+        lib.orc_demon_shift.restype = ctypes.c_int
+        lib.orc_demon_sweep.argtypes = [ctypes.c_int, ctypes.c_int, i8p, u8p, ctypes.c_int]
+        lib.orc_demon_sweep.restype = ctypes.c_int
+        lib.orc_demon_run.argtypes = [ctypes.c_int, ctypes.c_int, i8p, u8p, ctypes.c_int,
+                                      ctypes.c_uint32, ctypes.c_int64, ctypes.c_int, i64p, i64p,
+                                      ctypes.c_int64]
+        lib.orc_demon_run.restype = ctypes.c_int64
         lib.orc_enumerate.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
         lib.orc_enumerate.restype = ctypes.c_int
         _lib = lib
@@ -217,6 +229,52 @@ def run(dims: int, L: int, beta: float, seed: int, nsweeps: int,
     if n < 0:
         raise ValueError(f"orc_run -> {n}")
     return s, E[:n].copy(), M[:n].copy()
+
+
+def _demon_args(s, q):
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    assert q.dtype == np.uint8 and q.flags.c_contiguous and q.size == s.size
+    return _ptr(s, ctypes.c_int8), _ptr(q, ctypes.c_uint8)
+
+
+def demon_half_sweep(dims: int, L: int, s: np.ndarray, q: np.ndarray, qmax: int, c: int) -> None:
+    """One colour pass of Creutz's demon dynamics, in place on spins s and demons q."""
+    sp, qp = _demon_args(s, q)
+    rc = _load().orc_demon_half_sweep(dims, L, sp, qp, qmax, c)
+    if rc != 0:
+        raise ValueError(f"orc_demon_half_sweep -> {rc}")
+
+
+def demon_shift(dims: int, L: int, q: np.ndarray, step: int = 1) -> None:
+    """Move every demon one half row on (step=1) or back (step=-1), in place."""
+    assert q.dtype == np.uint8 and q.flags.c_contiguous
+    rc = _load().orc_demon_shift(dims, L, _ptr(q, ctypes.c_uint8), step)
+    if rc != 0:
+        raise ValueError(f"orc_demon_shift -> {rc}")
+
+
+def demon_sweep(dims: int, L: int, s: np.ndarray, q: np.ndarray, qmax: int) -> None:
+    sp, qp = _demon_args(s, q)
+    rc = _load().orc_demon_sweep(dims, L, sp, qp, qmax)
+    if rc != 0:
+        raise ValueError(f"orc_demon_sweep -> {rc}")
+
+
+def run_demon(dims: int, L: int, s: np.ndarray, q: np.ndarray, qmax: int, nsweeps: int,
+              measure_every: int = 1, t0: int = 0):
+    """Demon sweeps numbered t0, t0+1, ... from (s, q) (copied).  Returns
+    (s, q, E, M) with E, M recorded after sweep t iff (t+1) % measure_every == 0."""
+    s = np.ascontiguousarray(s, dtype=np.int8).copy()
+    q = np.ascontiguousarray(q, dtype=np.uint8).copy()
+    cap = nsweeps // measure_every + 2
+    E = np.zeros(cap, dtype=np.int64)
+    M = np.zeros(cap, dtype=np.int64)
+    sp, qp = _demon_args(s, q)
+    n = _load().orc_demon_run(dims, L, sp, qp, qmax, t0, nsweeps, measure_every,
+                              _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64), cap)
+    if n < 0:
+        raise ValueError(f"orc_demon_run -> {n}")
+    return s, q, E[:n].copy(), M[:n].copy()
 
 
 def enumerate_states(dims: int, L: int) -> np.ndarray:

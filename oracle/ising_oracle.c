@@ -434,6 +434,99 @@ int64_t orc_run(int dims, int L, double beta, uint64_t seed, int8_t *s,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Creutz's deterministic demon dynamics (Sec. 2.2 cites it: checkerboard   */
+/* sweeps with a fully deterministic flip rule and no random numbers).      */
+/* Readings (the paper gives no details):                                    */
+/*   - every site carries a demon holding energy 4q, q = 0..qmax (the flip  */
+/*     costs dE = 2k = 4 (dims - d) are multiples of 4);                     */
+/*   - a site of the pass's colour flips iff its demon can pay or absorb    */
+/*     the cost within its range, 0 <= q - (dims - d) <= qmax, and then     */
+/*     q <- q - (dims - d); so E(S) + 4 sum q never changes;                */
+/*   - after each sweep (black pass, white pass) every demon moves on by     */
+/*     one half row within its colour: from the colour-c site in half row r */
+/*     (r = y + L z) and half column xh = x >> 1 to the colour-c site in    */
+/*     half row r + 1 (mod the number of half rows) and the same xh.        */
+/* ------------------------------------------------------------------------ */
+int orc_demon_half_sweep(int dims, int L, int8_t *s, uint8_t *q, int qmax, int c)
+{
+    if (dims != 2 && dims != 3) return -1;
+    if (L < 2 || (L & 1) || (c != 0 && c != 1)) return -1;
+    if (qmax < 1 || qmax > 63) return -1;
+    int zdim = dims == 3 ? L : 1;
+    int64_t LL = (int64_t)L * L;
+    for (int z = 0; z < zdim; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                if (((x + y + z) & 1) != c) continue;
+                int64_t i = (int64_t)z * LL + (int64_t)y * L + x;
+                int k = s[i] * neighbour_sum(dims, L, s, x, y, z); /* 2 (dims - d) */
+                int qn = (int)q[i] - k / 2;
+                if (qn >= 0 && qn <= qmax) {
+                    s[i] = (int8_t)-s[i];
+                    q[i] = (uint8_t)qn;
+                }
+            }
+    return 0;
+}
+
+/* Move every demon one half row on (step = +1) or back (step = -1). */
+int orc_demon_shift(int dims, int L, uint8_t *q, int step)
+{
+    if (dims != 2 && dims != 3) return -1;
+    if (L < 2 || (L & 1) || (step != 1 && step != -1)) return -1;
+    int64_t n = n_sites(dims, L), LL = (int64_t)L * L;
+    int64_t rows = dims == 3 ? LL : L;
+    uint8_t *out = (uint8_t *)malloc((size_t)n);
+    if (!out) return -2;
+    int zdim = dims == 3 ? L : 1;
+    for (int z = 0; z < zdim; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                int c = (x + y + z) & 1;
+                int64_t r = (int64_t)y + (int64_t)L * z;
+                int64_t r2 = (r + step + rows) % rows;
+                int y2 = (int)(r2 % L), z2 = dims == 3 ? (int)(r2 / L) : 0;
+                int x2 = 2 * (x >> 1) + ((c + y2 + z2) & 1);
+                out[(int64_t)z2 * LL + (int64_t)y2 * L + x2] =
+                    q[(int64_t)z * LL + (int64_t)y * L + x];
+            }
+    memcpy(q, out, (size_t)n);
+    free(out);
+    return 0;
+}
+
+/* One demon sweep: black pass, white pass, demons move one half row on. */
+int orc_demon_sweep(int dims, int L, int8_t *s, uint8_t *q, int qmax)
+{
+    int rc = orc_demon_half_sweep(dims, L, s, q, qmax, 0);
+    if (rc == 0) rc = orc_demon_half_sweep(dims, L, s, q, qmax, 1);
+    if (rc == 0) rc = orc_demon_shift(dims, L, q, 1);
+    return rc;
+}
+
+/* nsweeps demon sweeps numbered t0, t0+1, ...; E and M recorded after sweep */
+/* t iff (t + 1) % measure_every == 0.  Returns the number of records.      */
+int64_t orc_demon_run(int dims, int L, int8_t *s, uint8_t *q, int qmax, uint32_t t0,
+                      int64_t nsweeps, int measure_every, int64_t *E, int64_t *M,
+                      int64_t cap)
+{
+    if (measure_every < 1 || nsweeps < 0) return -1;
+    int64_t n = 0;
+    for (int64_t k = 0; k < nsweeps; ++k) {
+        int rc = orc_demon_sweep(dims, L, s, q, qmax);
+        if (rc) return rc;
+        uint64_t t = (uint64_t)t0 + (uint64_t)k;
+        if ((t + 1) % (uint64_t)measure_every == 0) {
+            if (n >= cap) return -3;
+            E[n] = orc_energy(dims, L, s);
+            M[n] = orc_magnetization(dims, L, s);
+            ++n;
+        }
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exact enumeration for Eq. 1: the number of states g(E, M) of a tiny      */
 /* lattice, visiting all 2^N states in Gray-code order (one spin changes    */
 /* per step, so E and M are updated by the local rule and re-checked from   */

@@ -19,6 +19,7 @@ using ising::PassArgs;
 
 static_assert(ising::kRuleMetropolis == ISING_RULE_METROPOLIS, "rule values");
 static_assert(ising::kRuleHeatBath == ISING_RULE_HEATBATH, "rule values");
+static_assert(ising::kRuleDemon == ISING_RULE_DEMON, "rule values");
 
 namespace {
 
@@ -51,6 +52,7 @@ int device_props(const DeviceProps** out) {
         ISING_CHECK(cudaDeviceGetAttribute(&q.sm_count, cudaDevAttrMultiProcessorCount, dev));
         ISING_CHECK(ising::int8_query_occupancy(q));
         ISING_CHECK(ising::packed_query_occupancy(q));
+        ISING_CHECK(ising::demon_query_occupancy(q));
         ISING_CHECK(cudaMalloc(reinterpret_cast<void**>(&q.d_err), sizeof(int)));
         ISING_CHECK(cudaMemset(q.d_err, 0, sizeof(int)));
         p = q;
@@ -160,6 +162,10 @@ void free_device(ising_lattice* h) {
         if (p) cudaFree(p);
         p = nullptr;
     }
+    for (void*& p : h->dem) {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
     if (h->obs) cudaFree(h->obs);
     h->obs = nullptr;
     h->obs_cap = 0;
@@ -223,6 +229,18 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     a.key1 = (uint32_t)(h->seed >> 32);
     a.t = t;
     a.c = c;
+    a.dem = nullptr;
+    a.qmax = 0;
+    a.rot = 0;
+    if (h->rule == ISING_RULE_DEMON) {
+        a.dem = h->dem[c];
+        a.qmax = h->qmax;
+        a.rot = (uint32_t)h->dem_rot;
+        ISING_CHECK(ising::demon_pass(a, h->dims, h->half_sites, slot != nullptr, *h->dp,
+                                      h->stream));
+        if (c == 1) h->dem_rot = h->dem_rot + 1 == h->rows ? 0 : h->dem_rot + 1;
+        return ISING_OK;
+    }
     if (h->layout == ISING_BITPACK)
         ISING_CHECK(ising::packed_pass(a, h->dims, slot != nullptr, h->rule, *h->dp, h->stream));
     else if (uses_tma(h))
@@ -341,7 +359,7 @@ int ising_sweep(ising_lattice* h, int64_t n, int measure_every) {
         if (rc != ISING_OK) return rc;
     }
     int64_t rec = h->n_rec;
-    if (h->sites <= kSmallSites && n >= 2 && n <= 0x7FFFFFFF) {
+    if (h->sites <= kSmallSites && n >= 2 && n <= 0x7FFFFFFF && h->rule != ISING_RULE_DEMON) {
         const int rc = small_sweep(h, n, measure_every, h->obs ? h->obs + 2 * rec : nullptr);
         if (rc != ISING_OK) return rc;
         h->t += (uint64_t)n;
@@ -465,8 +483,61 @@ int ising_compute_thresholds_heatbath(int dims, double beta, uint32_t out[7]) {
 
 int ising_set_rule(ising_lattice* h, int rule) {
     if (!h) return ISING_EINVAL;
-    if (rule != ISING_RULE_METROPOLIS && rule != ISING_RULE_HEATBATH) return ISING_EINVAL;
+    if (rule != ISING_RULE_METROPOLIS && rule != ISING_RULE_HEATBATH && rule != ISING_RULE_DEMON)
+        return ISING_EINVAL;
+    if (rule == ISING_RULE_DEMON && !h->dem[0]) return ISING_EINVAL;  // ising_set_demons first
     h->rule = rule;
+    return ISING_OK;
+}
+
+int ising_set_demons(ising_lattice* h, const uint8_t* host_q, int fill, int qmax) {
+    if (!h || h->layout != ISING_INT8) return ISING_EINVAL;
+    if (qmax < 1 || qmax > 63) return ISING_EINVAL;
+    if (host_q) {
+        for (int64_t i = 0; i < h->sites; ++i)
+            if (host_q[i] > qmax) return ISING_EINVAL;
+    } else if (fill < 0 || fill > qmax) {
+        return ISING_EINVAL;
+    }
+    for (int c = 0; c < 2; ++c) {
+        if (h->dem[c]) continue;
+        ISING_CHECK(cudaMalloc(&h->dem[c], h->col_bytes));
+        ISING_CHECK(cudaMemsetAsync(h->dem[c], 0, h->col_bytes, h->stream));
+    }
+    if (host_q) {
+        uint8_t* tmp = nullptr;
+        ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+        cudaError_t e = cudaMemcpyAsync(tmp, host_q, (size_t)h->sites, cudaMemcpyHostToDevice,
+                                        h->stream);
+        if (e == cudaSuccess)
+            e = ising::demon_import(static_cast<uint8_t*>(h->dem[0]),
+                                    static_cast<uint8_t*>(h->dem[1]), tmp, h->L, h->dims,
+                                    h->sites, *h->dp, h->stream);
+        cudaFreeAsync(tmp, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    } else {
+        for (int c = 0; c < 2; ++c)
+            ISING_CHECK(cudaMemsetAsync(h->dem[c], fill, (size_t)h->half_sites, h->stream));
+    }
+    h->qmax = qmax;
+    h->dem_rot = 0;
+    ISING_CHECK(cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
+int ising_get_demons(ising_lattice* h, uint8_t* host_out) {
+    if (!h || !host_out || !h->dem[0]) return ISING_EINVAL;
+    uint8_t* tmp = nullptr;
+    ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+    cudaError_t e = ising::demon_export(static_cast<const uint8_t*>(h->dem[0]),
+                                        static_cast<const uint8_t*>(h->dem[1]), tmp, h->L,
+                                        h->dims, h->sites, h->rows, h->dem_rot, *h->dp,
+                                        h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, tmp, (size_t)h->sites, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(tmp, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ISING_CHECK(cudaStreamSynchronize(h->stream));
     return ISING_OK;
 }
 
@@ -481,7 +552,7 @@ int ising_get_info(const ising_lattice* h, ising_info_t* out) {
     out->seed = h->seed;
     out->sweeps_done = h->t;
     out->sites = (uint64_t)h->sites;
-    out->device_bytes = (uint64_t)(2 * h->col_bytes);
+    out->device_bytes = (uint64_t)((h->dem[0] ? 4 : 2) * h->col_bytes);
     out->pending_records = h->n_rec;
     return ISING_OK;
 }

@@ -33,6 +33,9 @@ struct ising_lattice {
     int64_t obs_cap = 0, n_rec = 0;
     const ising::DeviceProps* dp = nullptr;
     int kernel = ISING_KERNEL_AUTO;     // int8 pass kernel choice
+    void* dem[2] = {nullptr, nullptr};  // demons per colour (int8 layout), or null
+    int qmax = 0;                       // demon capacity: q = 0..qmax
+    int64_t dem_rot = 0;                // half rows the demons have moved on, mod rows
 };
 
 namespace ising {
@@ -44,6 +47,7 @@ struct DeviceProps {
     // indexed [rule][dims - 2][measure]
     int blocks_per_sm_vec[2][2][2] = {{{1, 1}, {1, 1}}, {{1, 1}, {1, 1}}};
     int blocks_per_sm_packed[2][2][2] = {{{1, 1}, {1, 1}}, {{1, 1}, {1, 1}}};
+    int blocks_per_sm_demon[2][2] = {{1, 1}, {1, 1}};  // demon strip pass [dims-2][measure]
     int* d_err = nullptr;  // raised by a kernel whose bounded wait ran out
 };
 
@@ -78,6 +82,16 @@ bool int8_tma_ok(int dims, int L);
 bool int8_tma_preferred(int dims, int L);
 cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, int rule,
                           const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st);
+
+// demon dynamics, int8 layout (sweep_demon.cu)
+cudaError_t demon_query_occupancy(DeviceProps& dp);
+cudaError_t demon_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure,
+                       const DeviceProps& dp, cudaStream_t st);
+cudaError_t demon_export(const uint8_t* d0, const uint8_t* d1, uint8_t* out, int L, int dims,
+                         int64_t sites, int64_t rows, int64_t rot, const DeviceProps& dp,
+                         cudaStream_t st);
+cudaError_t demon_import(uint8_t* d0, uint8_t* d1, const uint8_t* in, int L, int dims,
+                         int64_t sites, const DeviceProps& dp, cudaStream_t st);
 
 // bit-packed layout (sweep_bitpack.cu)
 cudaError_t packed_query_occupancy(DeviceProps& dp);

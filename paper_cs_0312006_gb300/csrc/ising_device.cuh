@@ -26,6 +26,7 @@ constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
 // Local update rules (the values of ISING_RULE_* in ising.h).
 constexpr int kRuleMetropolis = 0;
 constexpr int kRuleHeatBath = 1;
+constexpr int kRuleDemon = 2;
 
 // Counter word 3 ("tag") separates the uses of the stream.
 constexpr uint32_t kTagSweep = 0u;
@@ -72,6 +73,11 @@ struct PassArgs {
     int c;                  // colour of this pass: 0 black, 1 white
     int nv;                 // 16-byte vectors per half row (W / 16), vector kernels only
     int strips;             // row strips per column, vector kernels only
+    // demon dynamics only: the own colour's demons (one byte per site, half
+    // rows; half row r's demons in storage row (r - rot) mod rows) and their cap
+    void* dem;
+    int qmax;
+    uint32_t rot;
 };
 
 // Block-wide sum of two ints followed by one 64-bit atomic each into the

@@ -1,0 +1,339 @@
+// sweep_demon.cu -- colour pass of Creutz's deterministic demon dynamics on
+// the int8 layout, with the E and M reductions fused in.
+//
+// Sec. 2.2 cites Creutz's checkerboard simulation with a fully deterministic
+// flip rule that needs no random numbers.  Here every site carries a demon
+// holding energy 4q, q = 0..qmax, stored as one byte per site in two arrays
+// laid out like the spins (one per colour, half rows of W = L/2 bytes).  A
+// site with d disagreeing neighbours (flip cost dE = 4 (dims - d)) flips iff
+// 0 <= q - (dims - d) <= qmax, and its demon then keeps q - (dims - d), so
+// E + 4 sum q is conserved.  After each sweep every demon moves one half row
+// on within its colour (half row r, half column xh -> half row r + 1, same
+// xh).  Nothing is moved in memory: the demon of half row r sits in storage
+// row (r - rot) mod rows, and rot grows by one per sweep.
+//
+// With no draw the pass is a pure stream: it reads the own spins, the own
+// demons and the other colour and writes the own spins and demons, 5 bytes
+// per site update.
+//
+// Byte-sliced arithmetic (four sites per 32-bit word, no carries between
+// bytes): D = 2d per byte as in the Metropolis pass; v = q + d per byte; the
+// flip condition dims <= v <= dims + qmax is bit 7 of v + (0x80 - dims) and
+// not bit 7 of v + (0x80 - dims - qmax - 1); the new demon is v - dims.
+#include <cstdint>
+
+#include "engine_internal.h"
+#include "ising_device.cuh"
+#include "pass_bodies.cuh"
+
+namespace ising {
+
+namespace {
+
+__device__ __forceinline__ int wrap_prev(int v, int n) { return v == 0 ? n - 1 : v - 1; }
+__device__ __forceinline__ int wrap_next(int v, int n) { return v == n - 1 ? 0 : v + 1; }
+
+// Update four sites (one word): spins s, demons q, byte-sliced D = 2d.
+// Returns the flip mask (0xFE per flipped byte) and updates q in place.
+template <int DIMS>
+__device__ __forceinline__ uint32_t demon_word(uint32_t D, uint32_t& q, uint32_t lo_bias,
+                                               uint32_t hi_bias) {
+    const uint32_t v = q + (D >> 1);  // q + d per byte (D's bytes are even)
+    const uint32_t F = (v + lo_bias) & ~(v + hi_bias) & kByteBit7;
+    const uint32_t keep = F | (F - (F >> 7));  // 0xFF per flipped byte
+    // v - dims per byte, without borrows between bytes (every byte of v is < 0x80)
+    const uint32_t vn = ((v | kByteBit7) - (uint32_t)DIMS * kByteOnes) & 0x7F7F7F7Fu;
+    q = (q & ~keep) | (vn & keep);
+    return F | (F - (F >> 6));  // 0xFE per flipped byte
+}
+
+// The 16 sites of one vector; accumulates -1 spins written (m_neg) and, in the
+// white pass, sum 2 d_new (e_acc).
+template <int DIMS, bool MEASURE>
+__device__ __forceinline__ uint4 demon_vec(const uint4& s, uint4& qv, const uint4& x,
+                                           const uint4& xs, const uint4& ym, const uint4& yp,
+                                           const uint4& zm, const uint4& zp, uint32_t lo_bias,
+                                           uint32_t hi_bias, int c, int& e_acc, int& m_neg) {
+    const uint32_t sv[4] = {s.x, s.y, s.z, s.w};
+    uint32_t D[4], X[4], q[4] = {qv.x, qv.y, qv.z, qv.w};
+    D[0] = disagreements<DIMS>(s.x, x.x, xs.x, ym.x, yp.x, zm.x, zp.x);
+    D[1] = disagreements<DIMS>(s.y, x.y, xs.y, ym.y, yp.y, zm.y, zp.y);
+    D[2] = disagreements<DIMS>(s.z, x.z, xs.z, ym.z, yp.z, zm.z, zp.z);
+    D[3] = disagreements<DIMS>(s.w, x.w, xs.w, ym.w, yp.w, zm.w, zp.w);
+    uint32_t out[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        X[w] = demon_word<DIMS>(D[w], q[w], lo_bias, hi_bias);
+        out[w] = sv[w] ^ X[w];
+        if (MEASURE) {
+            m_neg += __popc(out[w] & kByteBit7);
+            if (c == 1) {
+                constexpr uint32_t q2 = 4u * DIMS * kByteOnes;
+                const uint32_t Dn = (D[w] & ~X[w]) | ((q2 - D[w]) & X[w]);
+                e_acc = __dp4a((int)Dn, (int)kByteOnes, e_acc);
+            }
+        }
+    }
+    qv = make_uint4(q[0], q[1], q[2], q[3]);
+    return make_uint4(out[0], out[1], out[2], out[3]);
+}
+
+// W % 16 == 0: the register-window strip walk of the Metropolis strip kernel,
+// with the own demons streamed beside the own spins.
+template <int DIMS, bool MEASURE>
+__global__ void __launch_bounds__(256) pass_demon_strip(PassArgs a) {
+    const int nv = a.nv, S = a.strips, L = a.L;
+    const int rows = (int)a.rows;
+    const int lane = threadIdx.x & 31;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = tid < S * nv;
+    const int sidx = active ? tid / nv : 0;
+    const int v = active ? tid - sidx * nv : 0;
+    const int r_begin = (int)(((int64_t)sidx * rows) / S);
+    const int len = active ? (int)(((int64_t)(sidx + 1) * rows) / S) - r_begin : 0;
+    const int max_len = (rows + S - 1) / S;
+    const uint4* __restrict__ O = reinterpret_cast<const uint4*>(a.other) + v;
+    uint4* __restrict__ Sv = reinterpret_cast<uint4*>(a.own) + v;
+    uint4* __restrict__ Q = reinterpret_cast<uint4*>(a.dem) + v;
+    const uint32_t* __restrict__ Ow = reinterpret_cast<const uint32_t*>(a.other);
+    const uint32_t vm_word = 4u * (uint32_t)wrap_prev(v, nv) + 3u;
+    const uint32_t vp_word = 4u * (uint32_t)wrap_next(v, nv);
+    const uint32_t lo_bias = (0x80u - (uint32_t)DIMS) * kByteOnes;
+    const uint32_t hi_bias = (0x80u - (uint32_t)DIMS - (uint32_t)a.qmax - 1u) * kByteOnes;
+
+    int z = DIMS == 3 ? r_begin / L : 0;
+    int y = r_begin - z * L;
+    int plane = z * L, plane_m = 0, plane_p = 0;
+    if (DIMS == 3) {
+        plane_m = wrap_prev(z, L) * L;
+        plane_p = wrap_next(z, L) * L;
+    }
+    // storage row of half row r's demons
+    int rd = r_begin - (int)a.rot;
+    if (rd < 0) rd += rows;
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    uint4 om = zero, oc = zero, op = zero, sc = zero, qc = zero, zm = zero, zp = zero;
+    bool reload = true;
+    int e_acc = 0, m_neg = 0, n_rows = 0;
+
+    for (int i = 0; i < max_len; ++i) {
+        const bool valid = i < len;
+        const int r = r_begin + i;
+        const int rd_next = rd + 1 == rows ? 0 : rd + 1;
+        if (valid && reload) {
+            om = __ldg(O + (uint32_t)(plane + wrap_prev(y, L)) * nv);
+            oc = __ldg(O + (uint32_t)r * nv);
+            op = __ldg(O + (uint32_t)(plane + wrap_next(y, L)) * nv);
+            sc = Sv[(uint32_t)r * nv];
+            qc = Q[(uint32_t)rd * nv];
+            if (DIMS == 3) {
+                zm = __ldg(O + (uint32_t)(plane_m + y) * nv);
+                zp = __ldg(O + (uint32_t)(plane_p + y) * nv);
+            }
+        }
+        // prefetch row r + 1 while it stays in this plane
+        const bool pf = (i + 1 < len) && (y + 1 < L);
+        uint4 op_n = zero, sc_n = zero, qc_n = zero, zm_n = zero, zp_n = zero;
+        if (pf) {
+            op_n = __ldg(O + (uint32_t)(plane + (y + 2 < L ? y + 2 : y + 2 - L)) * nv);
+            sc_n = Sv[(uint32_t)(r + 1) * nv];
+            qc_n = Q[(uint32_t)rd_next * nv];
+            if (DIMS == 3) {
+                zm_n = __ldg(O + (uint32_t)(plane_m + y + 1) * nv);
+                zp_n = __ldg(O + (uint32_t)(plane_p + y + 1) * nv);
+            }
+        }
+        uint32_t prev_w = __shfl_up_sync(0xffffffffu, oc.w, 1);
+        uint32_t next_x = __shfl_down_sync(0xffffffffu, oc.x, 1);
+        if (valid) {
+            const int p = (a.c + y + z) & 1;
+            uint4 sh;
+            if (p == 0) {
+                if (lane == 0 || v == 0) prev_w = __ldg(Ow + (uint32_t)r * nv * 4u + vm_word);
+                sh.x = __funnelshift_l(prev_w, oc.x, 8);
+                sh.y = __funnelshift_l(oc.x, oc.y, 8);
+                sh.z = __funnelshift_l(oc.y, oc.z, 8);
+                sh.w = __funnelshift_l(oc.z, oc.w, 8);
+            } else {
+                if (lane == 31 || v == nv - 1) next_x = __ldg(Ow + (uint32_t)r * nv * 4u + vp_word);
+                sh.x = __funnelshift_r(oc.x, oc.y, 8);
+                sh.y = __funnelshift_r(oc.y, oc.z, 8);
+                sh.z = __funnelshift_r(oc.z, oc.w, 8);
+                sh.w = __funnelshift_r(oc.w, next_x, 8);
+            }
+            const uint4 s = demon_vec<DIMS, MEASURE>(sc, qc, oc, sh, om, op, zm, zp, lo_bias,
+                                                     hi_bias, a.c, e_acc, m_neg);
+            Sv[(uint32_t)r * nv] = s;
+            Q[(uint32_t)rd * nv] = qc;
+            ++n_rows;
+        }
+        if (pf) {
+            om = oc;
+            oc = op;
+            op = op_n;
+            sc = sc_n;
+            qc = qc_n;
+            zm = zm_n;
+            zp = zp_n;
+        }
+        reload = !pf;
+        rd = rd_next;
+        if (++y == L) {
+            y = 0;
+            ++z;
+            plane += L;
+            if (DIMS == 3) {
+                plane_m = wrap_prev(z, L) * L;
+                plane_p = wrap_next(z, L) * L;
+            }
+        }
+    }
+    if (MEASURE) {
+        e_acc -= n_rows * 16 * 2 * DIMS;
+        const int m_acc = n_rows * 16 - 2 * m_neg;
+        block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
+    }
+}
+
+// Any even L: one site per item, neighbours found from the coordinates.
+template <int DIMS, bool MEASURE>
+__global__ void __launch_bounds__(256) pass_demon_sites(PassArgs a, uint32_t half) {
+    const int8_t* other = static_cast<const int8_t*>(a.other);
+    int8_t* own = static_cast<int8_t*>(a.own);
+    uint8_t* dem = static_cast<uint8_t*>(a.dem);
+    const uint32_t W = (uint32_t)a.W, L = (uint32_t)a.L, rows = (uint32_t)a.rows;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    int e_acc = 0, m_acc = 0;
+    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < half; h += stride) {
+        const uint32_t r = h / W, xh = h - r * W;
+        uint32_t y = r, z = 0;
+        if (DIMS == 3) {
+            z = r / L;
+            y = r - z * L;
+        }
+        const uint32_t p = ((uint32_t)a.c + y + z) & 1u;
+        const uint32_t x = 2u * xh + p;
+        const uint32_t xm = (x == 0u ? L - 1u : x - 1u) >> 1;
+        const uint32_t xp = (x + 1u == L ? 0u : x + 1u) >> 1;
+        const uint32_t plane = z * L;
+        const uint32_t rym = plane + (y == 0u ? L - 1u : y - 1u);
+        const uint32_t ryp = plane + (y + 1u == L ? 0u : y + 1u);
+        int hs = other[r * W + xm] + other[r * W + xp] + other[rym * W + xh] + other[ryp * W + xh];
+        if (DIMS == 3) {
+            const uint32_t rzm = (z == 0u ? L - 1u : z - 1u) * L + y;
+            const uint32_t rzp = (z + 1u == L ? 0u : z + 1u) * L + y;
+            hs += other[rzm * W + xh] + other[rzp * W + xh];
+        }
+        const int s = own[h];
+        const int delta = (s * hs) / 2;  // dims - d
+        const uint32_t rd = r >= a.rot ? r - a.rot : r + rows - a.rot;
+        const uint32_t qi = rd * W + xh;
+        const int qn = (int)dem[qi] - delta;
+        int sn = s;
+        if (qn >= 0 && qn <= a.qmax) {
+            sn = -s;
+            own[h] = (int8_t)sn;
+            dem[qi] = (uint8_t)qn;
+        }
+        if (MEASURE) {
+            m_acc += sn;
+            if (a.c == 1) e_acc -= sn * hs;  // the white pass sums every bond once
+        }
+    }
+    if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
+}
+
+// Demons in canonical order <-> the two storage arrays (storage row of half
+// row r is (r - rot) mod rows).
+__global__ void export_demons_kernel(const uint8_t* d0, const uint8_t* d1, uint8_t* out, int L,
+                                     int dims, int64_t sites, int64_t rows, int64_t rot) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t W = L / 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sites; i += stride) {
+        const int64_t x = i % L, r = i / L;  // r = y + L z
+        const int64_t y = r % L, z = dims == 3 ? r / L : 0;
+        int64_t rd = r - rot;
+        if (rd < 0) rd += rows;
+        out[i] = (((x + y + z) & 1) == 0 ? d0 : d1)[rd * W + (x >> 1)];
+    }
+}
+
+__global__ void import_demons_kernel(uint8_t* d0, uint8_t* d1, const uint8_t* in, int L, int dims,
+                                     int64_t sites) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sites; i += stride) {
+        const int64_t x = i % L, rest = i / L;
+        const int64_t y = rest % L, z = dims == 3 ? rest / L : 0;
+        (((x + y + z) & 1) == 0 ? d0 : d1)[i >> 1] = in[i];
+    }
+}
+
+unsigned grid_for(int64_t n, const DeviceProps& dp) {
+    int64_t b = (n + 255) / 256;
+    const int64_t cap = (int64_t)dp.sm_count * 16;
+    if (b > cap) b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <int DIMS, bool MEASURE>
+cudaError_t launch_demon_t(const PassArgs& a0, int64_t half_sites, const DeviceProps& dp,
+                           cudaStream_t st) {
+    const int threads = 256;
+    if (a0.W % 16 == 0) {
+        PassArgs a = a0;
+        a.nv = a.W >> 4;
+        const int64_t resident =
+            (int64_t)dp.sm_count * dp.blocks_per_sm_demon[DIMS - 2][MEASURE] * threads;
+        int64_t strips = resident / a.nv;
+        if (strips > a.rows) strips = a.rows;
+        if (strips < 1) strips = 1;
+        a.strips = (int)strips;
+        const int64_t blocks = (strips * a.nv + threads - 1) / threads;
+        pass_demon_strip<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a);
+    } else {
+        pass_demon_sites<DIMS, MEASURE>
+            <<<grid_for(half_sites, dp), threads, 0, st>>>(a0, (uint32_t)half_sites);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t demon_query_occupancy(DeviceProps& dp) {
+    cudaError_t e;
+#define ISING_OCC(D, M)                                                                      \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_demon[D - 2][M],      \
+                                                      pass_demon_strip<D, M>, 256, 0);          \
+    if (e != cudaSuccess) return e;
+    ISING_OCC(2, false)
+    ISING_OCC(2, true)
+    ISING_OCC(3, false)
+    ISING_OCC(3, true)
+#undef ISING_OCC
+    return cudaSuccess;
+}
+
+cudaError_t demon_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure,
+                       const DeviceProps& dp, cudaStream_t st) {
+    if (dims == 2)
+        return measure ? launch_demon_t<2, true>(a, half_sites, dp, st)
+                       : launch_demon_t<2, false>(a, half_sites, dp, st);
+    return measure ? launch_demon_t<3, true>(a, half_sites, dp, st)
+                   : launch_demon_t<3, false>(a, half_sites, dp, st);
+}
+
+cudaError_t demon_export(const uint8_t* d0, const uint8_t* d1, uint8_t* out, int L, int dims,
+                         int64_t sites, int64_t rows, int64_t rot, const DeviceProps& dp,
+                         cudaStream_t st) {
+    export_demons_kernel<<<grid_for(sites, dp), 256, 0, st>>>(d0, d1, out, L, dims, sites, rows,
+                                                              rot);
+    return cudaGetLastError();
+}
+
+cudaError_t demon_import(uint8_t* d0, uint8_t* d1, const uint8_t* in, int L, int dims,
+                         int64_t sites, const DeviceProps& dp, cudaStream_t st) {
+    import_demons_kernel<<<grid_for(sites, dp), 256, 0, st>>>(d0, d1, in, L, dims, sites);
+    return cudaGetLastError();
+}
+
+}  // namespace ising

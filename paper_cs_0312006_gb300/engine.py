@@ -20,7 +20,7 @@ from . import _build
 INT8, BITPACK, AUTO = 0, 1, 2
 HOT, COLD_UP, COLD_DOWN = 0, 1, 2
 KERNEL_AUTO, KERNEL_STRIP, KERNEL_TMA = 0, 1, 2
-RULE_METROPOLIS, RULE_HEATBATH = 0, 1
+RULE_METROPOLIS, RULE_HEATBATH, RULE_DEMON = 0, 1, 2
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, ERANGE = 0, -1, -2, -3, -4, -5, -6
 
@@ -83,6 +83,8 @@ def load_library():
             "ising_compute_thresholds_heatbath": ([ctypes.c_int, ctypes.c_double, u32p],
                                                   ctypes.c_int),
             "ising_set_rule": ([P, ctypes.c_int], ctypes.c_int),
+            "ising_set_demons": ([P, P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "ising_get_demons": ([P, P], ctypes.c_int),
             "ising_get_info": ([P, ctypes.POINTER(IsingInfo)], ctypes.c_int),
             "ising_synchronize": ([P], ctypes.c_int),
             "ising_set_kernel": ([P, ctypes.c_int], ctypes.c_int),
@@ -261,8 +263,26 @@ class Lattice:
         return k.value
 
     def set_rule(self, rule: int) -> None:
-        """Local update rule of later sweeps: RULE_METROPOLIS or RULE_HEATBATH."""
+        """Local update rule of later sweeps: RULE_METROPOLIS, RULE_HEATBATH or
+        RULE_DEMON (after set_demons)."""
         _check(self._lib.ising_set_rule(self._h, int(rule)), "ising_set_rule")
+
+    def set_demons(self, q: np.ndarray | None = None, fill: int = 0, qmax: int = 3) -> None:
+        """Demons of the deterministic dynamics: canonical uint8 array ``q``
+        (values <= qmax), or every demon = ``fill``."""
+        if q is None:
+            _check(self._lib.ising_set_demons(self._h, None, int(fill), int(qmax)),
+                   "ising_set_demons")
+            return
+        qq = np.ascontiguousarray(q, dtype=np.uint8).reshape(-1)
+        assert qq.size == self.info().sites
+        _check(self._lib.ising_set_demons(self._h, qq.ctypes.data, 0, int(qmax)),
+               "ising_set_demons")
+
+    def get_demons(self) -> np.ndarray:
+        out = np.empty(self.info().sites, dtype=np.uint8)
+        _check(self._lib.ising_get_demons(self._h, out.ctypes.data), "ising_get_demons")
+        return out
 
     @property
     def handle(self) -> int:

@@ -107,3 +107,19 @@ def poisson_jobs(n: int = 2000, rate_per_s: float = 200.0, seed: int = 1,
         out.append(Job(j, t, LatticeSpec(dims, L, beta, 5000 + j, HOT, nsw,
                                          measure_every, AUTO)))
     return out
+
+
+def demon_field(n: int, qmax: int = 3, beta: float = 0.5, seed: int = BASE_SEED) -> np.ndarray:
+    """Initial demons for the deterministic (demon) dynamics: n values in
+    0..qmax drawn independently with weights exp(-4 beta q), i.e. demons at
+    inverse temperature beta (a demon of level q holds energy 4q).  uint8."""
+    rng = np.random.default_rng(seed)
+    w = np.exp(-4.0 * beta * np.arange(qmax + 1))
+    cdf = np.cumsum(w / w.sum())
+    cdf[-1] = 1.0
+    out = np.empty(n, dtype=np.uint8)
+    chunk = 1 << 24
+    for i in range(0, n, chunk):
+        m = min(chunk, n - i)
+        out[i:i + m] = np.searchsorted(cdf, rng.random(m), side="right")
+    return out
