@@ -62,22 +62,28 @@ DEMON_QMAX = 3
 # DRAM bytes per site update of the pass kernels, from one
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` capture of the
 # bench's own run per workload (profiles/dram_traffic_bench_scan_L8192.md,
-# profiles/dram_traffic_bench_big_L65536.md).  They describe the kernel sources
+# profiles/dram_traffic_bench_big_L65536.md, profiles/dram_traffic_bench_demon.md).  They describe the kernel sources
 # whose hash is recorded; any change to those sources makes the bench report
 # "traffic": null until the capture is redone.
 TRAFFIC = {
-    ("scan", "int8"): {"bytes_per_update": 1.9656,
-                       "sha1": "593903d67fa083d7bf84ff7ab3b969c5774fbb62",
+    ("scan", "int8"): {"bytes_per_update": 1.9647,
+                       "sha1": "6d132b6c90e41675a3a7ebeca52085ceabc84ea6",
                        "sources": ["sweep_int8_tma.cu", "pass_bodies.cuh", "ising_device.cuh"]},
-    ("scan", "bitpack"): {"bytes_per_update": 0.2230,
-                          "sha1": "7eaa6f9995ad8b6cc3269ccc2ec50aaa3a3cf8b8",
+    ("scan", "bitpack"): {"bytes_per_update": 0.2269,
+                          "sha1": "86f42d2317495a12cb5e73c54db6ca2ccc8251fd",
                           "sources": ["sweep_bitpack.cu", "pass_bodies.cuh", "ising_device.cuh"]},
+    ("scan", "demon"): {"bytes_per_update": 4.5424,
+                        "sha1": "a8e4d033a61dab46d0fa336ea9d92e9c200ce87f",
+                        "sources": ["sweep_demon.cu", "pass_bodies.cuh", "ising_device.cuh"]},
     ("big", "int8"): {"bytes_per_update": 3.0038,
                       "sha1": "3510fb0f7769ee1940b19835f50c6f7aa35e3752",
                       "sources": ["sweep_int8.cu", "pass_bodies.cuh", "ising_device.cuh"]},
     ("big", "bitpack"): {"bytes_per_update": 0.3828,
                          "sha1": "2cea39923be5e5d0369d4c02c5b9068936caf58a",
                          "sources": ["sweep_bitpack.cu", "pass_bodies.cuh", "ising_device.cuh"]},
+    ("big", "demon"): {"bytes_per_update": 5.0003,
+                       "sha1": "a8e4d033a61dab46d0fa336ea9d92e9c200ce87f",
+                       "sources": ["sweep_demon.cu", "pass_bodies.cuh", "ising_device.cuh"]},
 }
 
 
