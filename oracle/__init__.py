@@ -4,8 +4,10 @@ TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may import this package.  It shares no code with
 the CUDA engine in ``paper_cs_0312006_gb300`` and neither imports the other.
 
-The arithmetic lives in plain single-threaded C (``ising_oracle.c``); this module
-compiles it with gcc on first use and marshals numpy arrays through ctypes.  The
+The arithmetic lives in plain single-threaded C (``ising_oracle.c`` for the
+Ising model, Sec. 2.2; ``percolation_oracle.c`` for the percolation model,
+Sec. 2.3); this module compiles them with gcc on first use and marshals numpy
+arrays through ctypes.  The
 exact closed forms and enumeration-based averages used to pin the oracle are in
 ``oracle.exact``.
 
@@ -23,6 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ising_oracle.c")
+_SOURCES = [_SRC, os.path.join(_HERE, "percolation_oracle.c")]
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
 
@@ -38,11 +41,11 @@ def build(force: bool = False) -> str:
     """Compile ``ising_oracle.c`` into ``oracle/_build/liboracle.so`` (gcc -O2)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SOURCES)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra",
-           "-o", tmp, _SRC, "-lm"]
+           "-o", tmp, *_SOURCES, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -102,6 +105,15 @@ def _load():
                                       ctypes.c_uint32, ctypes.c_int64, ctypes.c_int, i64p, i64p,
                                       ctypes.c_int64]
         lib.orc_demon_run.restype = ctypes.c_int64
+        lib.orc_perc_threshold.argtypes = [ctypes.c_double, u32p]
+        lib.orc_perc_threshold.restype = ctypes.c_int
+        lib.orc_perc_pores.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                       ctypes.c_uint32, u8p]
+        lib.orc_perc_pores.restype = ctypes.c_int
+        lib.orc_perc_invade.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int,
+                                        ctypes.c_int64, u8p, i64p,
+                                        ctypes.POINTER(ctypes.c_int), i64p]
+        lib.orc_perc_invade.restype = ctypes.c_int
         lib.orc_enumerate.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
         lib.orc_enumerate.restype = ctypes.c_int
         _lib = lib
@@ -275,6 +287,46 @@ def run_demon(dims: int, L: int, s: np.ndarray, q: np.ndarray, qmax: int, nsweep
     if n < 0:
         raise ValueError(f"orc_demon_run -> {n}")
     return s, q, E[:n].copy(), M[:n].copy()
+
+
+# --------------------------------------------------------------------------
+# Percolation (Sec. 2.3)
+# --------------------------------------------------------------------------
+PERC_POINT, PERC_FACE = 0, 1
+
+
+def perc_threshold(P: float) -> int:
+    """floor(P * 2^32) capped at 2^32 - 1: a site is a pore iff its draw u <= this."""
+    thr = ctypes.c_uint32(0)
+    if _load().orc_perc_threshold(float(P), ctypes.byref(thr)) != 0:
+        raise ValueError(f"porosity {P!r} not in [0, 1]")
+    return int(thr.value)
+
+
+def perc_pores(dims: int, L: int, seed: int, P: float) -> np.ndarray:
+    """Porosity field: uint8 1 (pore) / 0 (solid) per site, canonical order."""
+    n = L ** dims
+    pore = np.zeros(n, dtype=np.uint8)
+    rc = _load().orc_perc_pores(dims, L, seed, perc_threshold(P), _ptr(pore, ctypes.c_uint8))
+    if rc != 0:
+        raise ValueError(f"orc_perc_pores -> {rc}")
+    return pore
+
+
+def perc_invade(dims: int, L: int, pore: np.ndarray, source: int = PERC_FACE, site: int = 0):
+    """Invade ``pore`` from one site or the first face; returns
+    (cluster uint8 array, size, spans, steps)."""
+    pore = np.ascontiguousarray(pore, dtype=np.uint8)
+    cluster = np.zeros(pore.size, dtype=np.uint8)
+    size = ctypes.c_int64(0)
+    spans = ctypes.c_int(0)
+    steps = ctypes.c_int64(0)
+    rc = _load().orc_perc_invade(dims, L, _ptr(pore, ctypes.c_uint8), source, int(site),
+                                 _ptr(cluster, ctypes.c_uint8), ctypes.byref(size),
+                                 ctypes.byref(spans), ctypes.byref(steps))
+    if rc != 0:
+        raise ValueError(f"orc_perc_invade -> {rc}")
+    return cluster, int(size.value), bool(spans.value), int(steps.value)
 
 
 def enumerate_states(dims: int, L: int) -> np.ndarray:
