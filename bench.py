@@ -684,6 +684,78 @@ def run_cubic_workload(args):
     return 0
 
 
+def run_percolation_workload(args):
+    """Site percolation (Sec. 2.3), two forms:
+    medium -- one 2D medium L = 16384 (268 M sites) at porosity 0.6 (above the
+              threshold, so the cluster is deep): porosity field, then face
+              invasion by synchronous growth passes to the steady state;
+    batch  -- 8192 media of 2D L = 128 at the paper's threshold 0.592746, one
+              CTA per medium (spanning fraction reported).
+    The oracle runs on bounded samples of both as the CPU baseline."""
+    import torch
+    from paper_cs_0312006_gb300 import _build, percolation
+    _build.build()
+    L, P = args.perc_L, 0.6
+    sites = L * L
+    m = percolation.Medium(2, L, BASE_SEED)
+    m.generate(P)  # warm-up
+    m.invade(percolation.FACE)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    m.generate(P)
+    b.record()
+    torch.cuda.synchronize()
+    gen_ms = a.elapsed_time(b)
+    t0 = time.perf_counter()
+    r = m.invade(percolation.FACE)
+    inv_s = time.perf_counter() - t0
+    m.close()
+    words = L * ((L + 31) // 32)
+    medium = {"L": L, "porosity": P, "generate_ms": gen_ms,
+              "generate_sites_per_s": sites / (gen_ms / 1e3),
+              "invade_s": inv_s, "steps": r.steps, "cluster_sites": r.size,
+              "spans": bool(r.spans),
+              "us_per_pass": inv_s * 1e6 / max(1, r.steps),
+              "site_passes_per_s": sites * r.steps / inv_s,
+              "pass_bytes": 5 * 4 * words,
+              "note": "a growth pass reads the pore, cluster and last-front bitmaps (with "
+                      "halo words from L2) and writes the next front (and the cluster where "
+                      "it grew): ~5 x 4 B per 32-site word"}
+    # batch of small media
+    Lb, Pb, n = 128, 0.592746, args.perc_media
+    seeds = [BASE_SEED + k for k in range(n)]
+    percolation.batch(2, Lb, Pb, seeds[:256])  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = percolation.batch(2, Lb, Pb, seeds)
+    bt = time.perf_counter() - t0
+    frac = sum(x.spans for x in res) / n
+    batch = {"L": Lb, "porosity": Pb, "media": n, "seconds": bt, "media_per_s": n / bt,
+             "sites_per_s": n * Lb * Lb / bt, "spanning_fraction": frac,
+             "mean_steps": sum(x.steps for x in res) / n}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < args.cpu_seconds / 2 and k < n:
+            oracle.perc_invade(2, Lb, oracle.perc_pores(2, Lb, seeds[k], Pb))
+            k += 1
+        ct = time.perf_counter() - t0
+        cpu = {"value": k / ct, "unit": "media/s", "cores": 1, "kind": "oracle",
+               "sample": f"{k} media of 2D L={Lb} at P={Pb} (porosity field + face invasion)"}
+    line = {"metric": "media/s", "value": batch["media_per_s"], "unit": "media/s",
+            "workload": "site percolation, 2D: one L=16384 medium at P=0.6 (porosity field "
+                        "+ face invasion to the steady state) and a batch of L=128 media at "
+                        "P=0.592746",
+            "medium": medium, "batch": batch, "cpu_baseline": cpu,
+            "device": torch.cuda.get_device_name()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_philox_workload(args):
     """Throughput of the device generator alone (ising_philox_fill): the
     ceiling that the Metropolis draws put on any pass kernel."""
@@ -729,7 +801,7 @@ def main():
                     help="int8 pass: register-window strips or shared-memory tiles staged by "
                          "bulk (TMA) copies")
     ap.add_argument("--workload", choices=["scan", "batched", "serving", "philox", "small",
-                                           "cubic", "big"],
+                                           "cubic", "big", "percolation"],
                     default="scan",
                     help="scan: the 2D L=8192 beta scan (default line); batched: 2048 "
                          "lattices in one launch vs one launch per lattice; serving: Poisson "
@@ -740,6 +812,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batched: fixed launch shape")
     ap.add_argument("--big-L", type=int, default=65536,
                     help="big: linear size of the single 2D lattice")
+    ap.add_argument("--perc-L", type=int, default=16384)
+    ap.add_argument("--perc-media", type=int, default=8192)
     ap.add_argument("--cubic-L", type=int, default=256)
     ap.add_argument("--cubic-sweeps", type=int, default=1000)
     ap.add_argument("--serve-jobs", type=int, default=2000)
@@ -769,6 +843,8 @@ def main():
         return run_small_workload(args)
     if args.workload == "cubic" and args.impl != "reference":
         return run_cubic_workload(args)
+    if args.workload == "percolation" and args.impl != "reference":
+        return run_percolation_workload(args)
     if args.workload == "big":  # one lattice far larger than L2
         args.L = args.big_L
         args.lattices = 1

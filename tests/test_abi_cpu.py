@@ -1,5 +1,5 @@
 """The C-ABI library without a GPU: it builds, loads, exports every function
-that include/ising.h declares, validates arguments on the host, and its
+that include/*.h declares (ising.h, percolation.h), validates arguments on the host, and its
 host-side threshold builder agrees with the oracle and with mpmath."""
 import ctypes
 import math
@@ -26,7 +26,8 @@ def _declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", fn)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(ising_\w+)\s*\(", text, flags=re.M)
+        names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b((?:ising|perc)_\w+)\s*\(", text,
+                            flags=re.M)
     return sorted(set(names))
 
 
@@ -34,6 +35,7 @@ def test_header_symbols_exported(lib):
     names = _declared_functions()
     assert "ising_create" in names and "ising_sweep" in names
     assert "ising_observables" in names and "ising_destroy" in names
+    assert "perc_create" in names and "perc_invade" in names and "perc_batch" in names
     for name in names:
         assert hasattr(lib, name), f"{name} declared in include/ but not exported"
 
@@ -101,3 +103,20 @@ def test_engine_heatbath_thresholds_match_oracle_and_mpmath(lib, orc):
 def test_set_rule_rejects_null_and_unknown(lib):
     assert lib.ising_set_rule(None, 0) == -1
     assert lib.ising_compute_thresholds_heatbath(4, ctypes.c_double(0.3), None) == -1
+
+
+def test_percolation_rejects_bad_arguments_on_the_host(lib):
+    from paper_cs_0312006_gb300 import percolation
+    lib = percolation._lib()
+    h = ctypes.c_void_p()
+    assert lib.perc_create(ctypes.byref(h), 4, 16, 1) == -1
+    assert lib.perc_create(ctypes.byref(h), 2, 0, 1) == -1
+    assert lib.perc_create(ctypes.byref(h), 3, 2000, 1) == -1  # more than 2^32 sites
+    assert lib.perc_generate(None, 0.5) == -1
+    assert lib.perc_invade(None, 1, 0, None) == -1
+    seeds = (ctypes.c_uint64 * 1)(1)
+    res = (percolation.PercResult * 1)()
+    assert lib.perc_batch(2, 1024, 0.5, seeds, 1, 1, 0, res, None, None) == -1  # too large
+    assert lib.perc_batch(2, 64, 1.5, seeds, 1, 1, 0, res, None, None) == -1
+    assert lib.perc_batch(2, 64, 0.5, seeds, 0, 1, 0, res, None, None) == -1
+    lib.perc_destroy(None)
