@@ -18,6 +18,14 @@
 //
 // Draws: site i is a pore iff word (i & 3) of Philox4x32-10(seed; i >> 2, 0,
 // 0, 3) is <= floor(P 2^32) (capped at 2^32 - 1).
+//
+// A single medium's passes touch only a band of rows: each pass records the
+// lowest and highest row of the front it writes (Band), and the next pass
+// visits the rows next to that front plus the rows of the front before it
+// (which it must clear from the buffer it overwrites).  The passes are issued
+// as a replayed CUDA graph of kPassesPerGraph launches; after each replay the
+// host reads the per-pass counts and stops at the first pass that added
+// nothing (the rest of that replay are no-ops on an empty front).
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -144,9 +152,35 @@ __global__ void perc_pores_kernel(uint32_t* pore, PercGeom g, uint32_t key0, uin
     }
 }
 
-// Cluster and front start as the invasion sites.
-__global__ void perc_seed_kernel(const uint32_t* pore, uint32_t* C, uint32_t* F, PercGeom g,
-                                 int source, uint64_t site) {
+struct Band {
+    unsigned int lo, hi;  // rows of a front (lo > hi: empty)
+};
+constexpr int kBandSlots = 4;  // pass k writes slot k % 4, reads k-1 and k-2, resets k+1
+constexpr int kPassesPerGraph = 64;
+
+__device__ __forceinline__ void band_add(Band* b, unsigned int lo, unsigned int hi) {
+    // block-wide min / max of the rows that got front bits, then one atomic each
+    __shared__ unsigned int s_lo, s_hi;
+    if (threadIdx.x == 0) {
+        s_lo = 0xFFFFFFFFu;
+        s_hi = 0u;
+    }
+    __syncthreads();
+    if (lo <= hi) {
+        atomicMin(&s_lo, lo);
+        atomicMax(&s_hi, hi);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_lo <= s_hi) {
+        atomicMin(&b->lo, s_lo);
+        atomicMax(&b->hi, s_hi);
+    }
+}
+
+// Cluster and front start as the invasion sites; the other front buffer is
+// cleared.
+__global__ void perc_seed_kernel(const uint32_t* pore, uint32_t* C, uint32_t* F, uint32_t* F1,
+                                 PercGeom g, int source, uint64_t site, Band* bands) {
     const uint64_t words = (uint64_t)g.rows * g.nq;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t site_r = site / g.L, site_x = site - site_r * g.L;
@@ -160,23 +194,58 @@ __global__ void perc_seed_kernel(const uint32_t* pore, uint32_t* C, uint32_t* F,
             v = w == site_w ? pore[w] & (1u << (site_x & 31u)) : 0u;
         C[w] = v;
         F[w] = v;
+        F1[w] = 0u;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < kBandSlots) {
+        // the seed front is "pass -1" (slot 3): every row that may hold a seed;
+        // "pass -2" (slot 2) is empty; slots 0 and 1 are reset for passes 0, 1
+        Band b;
+        if (source == PERC_FACE) {
+            b.lo = 0u;
+            b.hi = g.dims == 2 ? 0u : g.L - 1u;
+        } else {
+            b.lo = b.hi = (unsigned int)(site / g.L);
+        }
+        bands[threadIdx.x] = threadIdx.x == 3 ? b : Band{0xFFFFFFFFu, 0u};
     }
 }
 
-__global__ void __launch_bounds__(256) perc_level_kernel(const uint32_t* pore, uint32_t* C,
-                                                         const uint32_t* Fo, uint32_t* Fn,
-                                                         PercGeom g, unsigned long long* added) {
-    const uint32_t words = g.rows * g.nq;
-    const uint32_t stride = gridDim.x * blockDim.x;
+// One banded growth pass (pass index k within the graph, k % 4 picks slots).
+__global__ void __launch_bounds__(256) perc_band_kernel(const uint32_t* pore, uint32_t* C,
+                                                        const uint32_t* Fo, uint32_t* Fn,
+                                                        PercGeom g, Band* bands, int k,
+                                                        unsigned long long* added) {
+    const Band last = bands[(k + 3) % kBandSlots];   // rows of the front Fo
+    const Band older = bands[(k + 2) % kBandSlots];  // rows of the stale front in Fn
+    if (blockIdx.x == 0 && threadIdx.x == 0) bands[(k + 1) % kBandSlots] = Band{0xFFFFFFFFu, 0u};
+    const unsigned int reach = g.dims == 2 ? 1u : g.L;  // rows a front row touches
+    unsigned int lo = 0xFFFFFFFFu, hi = 0u;
+    if (last.lo <= last.hi) {
+        lo = last.lo > reach ? last.lo - reach : 0u;
+        hi = last.hi + reach < g.rows ? last.hi + reach : g.rows - 1u;
+    }
+    if (older.lo <= older.hi) {
+        lo = older.lo < lo ? older.lo : lo;
+        hi = older.hi > hi ? older.hi : hi;
+    }
     unsigned long long cnt = 0ull;
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < words; w += stride) {
-        const uint32_t add = grow_word(pore, C, Fo, g, w);
-        Fn[w] = add;
-        if (add) {
-            C[w] |= add;
-            cnt += (unsigned long long)__popc(add);
+    unsigned int got_lo = 0xFFFFFFFFu, got_hi = 0u;
+    if (lo <= hi) {
+        const uint32_t w0 = lo * g.nq, w1 = (hi + 1u) * g.nq;
+        const uint32_t stride = gridDim.x * blockDim.x;
+        for (uint32_t w = w0 + blockIdx.x * blockDim.x + threadIdx.x; w < w1; w += stride) {
+            const uint32_t add = grow_word(pore, C, Fo, g, w);
+            Fn[w] = add;
+            if (add) {
+                C[w] |= add;
+                cnt += (unsigned long long)__popc(add);
+                const unsigned int r = w / g.nq;
+                got_lo = r < got_lo ? r : got_lo;
+                got_hi = r > got_hi ? r : got_hi;
+            }
         }
     }
+    band_add(&bands[k % kBandSlots], got_lo, got_hi);
     block_sum_u64(cnt, added);
 }
 
@@ -316,9 +385,10 @@ struct perc_medium {
     uint32_t* pore = nullptr;
     uint32_t* C = nullptr;
     uint32_t* F[2] = {nullptr, nullptr};
-    unsigned long long* counts = nullptr;  // per-pass additions of one chunk
+    unsigned long long* counts = nullptr;  // per-pass additions of one graph replay
     unsigned long long* meas = nullptr;    // size, first face, last face
-    int counts_cap = 0;
+    Band* bands = nullptr;
+    cudaGraphExec_t passes = nullptr;      // kPassesPerGraph banded passes
     cudaStream_t stream = nullptr;
     int sm_count = 0;
 };
@@ -330,6 +400,8 @@ void free_medium(perc_medium* m) {
         if (p) cudaFree(p);
     if (m->counts) cudaFree(m->counts);
     if (m->meas) cudaFree(m->meas);
+    if (m->bands) cudaFree(m->bands);
+    if (m->passes) cudaGraphExecDestroy(m->passes);
     delete m;
 }
 
@@ -378,6 +450,10 @@ int perc_create(perc_medium** out, int dims, int L, uint64_t seed) {
         if (e == cudaSuccess) e = cudaMemset(*p, 0, m->map_bytes);
     }
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&m->meas), 3 * 8);
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void**>(&m->counts), kPassesPerGraph * 8);
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void**>(&m->bands), kBandSlots * sizeof(Band));
     if (e != cudaSuccess) {
         free_medium(m);
         return cuda_fail(e);
@@ -405,37 +481,46 @@ int perc_invade(perc_medium* m, int source, int64_t site, perc_result* out) {
     if (source == PERC_POINT && (site < 0 || (uint64_t)site >= m->sites)) return ISING_EINVAL;
     const uint64_t words = (uint64_t)m->g.rows * m->g.nq;
     const unsigned grid = grid_for(words, m->sm_count);
-    perc_seed_kernel<<<grid, 256, 0, m->stream>>>(m->pore, m->C, m->F[0], m->g, source,
-                                                  source == PERC_POINT ? (uint64_t)site : 0ull);
+    perc_seed_kernel<<<grid, 256, 0, m->stream>>>(m->pore, m->C, m->F[0], m->F[1], m->g, source,
+                                                  source == PERC_POINT ? (uint64_t)site : 0ull,
+                                                  m->bands);
     PERC_CHECK(cudaGetLastError());
-    // growth passes in chunks; after a chunk the host looks for the first
-    // pass that added nothing (later passes of the chunk are then no-ops)
-    int cur = 0, chunk = 32;
+    if (!m->passes) {
+        // capture [zero the counts, kPassesPerGraph banded passes] once; the
+        // buffers and slots it uses belong to the medium, so replays continue
+        cudaStream_t cap = nullptr;
+        PERC_CHECK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = cudaMemsetAsync(m->counts, 0, kPassesPerGraph * 8, cap);
+            for (int k = 0; k < kPassesPerGraph && le == cudaSuccess; ++k) {
+                perc_band_kernel<<<grid, 256, 0, cap>>>(m->pore, m->C, m->F[k & 1],
+                                                        m->F[(k & 1) ^ 1], m->g, m->bands, k,
+                                                        m->counts + k);
+                le = cudaGetLastError();
+            }
+            e = cudaStreamEndCapture(cap, &graph);
+            if (e == cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&m->passes, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    // replay until a pass adds nothing (each replay that continues added at
+    // least kPassesPerGraph sites, so this ends)
     int64_t steps = 0;
-    std::vector<unsigned long long> host;
+    unsigned long long host[kPassesPerGraph];
     while (true) {
-        if (chunk > m->counts_cap) {
-            if (m->counts) PERC_CHECK(cudaFree(m->counts));
-            m->counts = nullptr;
-            PERC_CHECK(cudaMalloc(reinterpret_cast<void**>(&m->counts), (size_t)chunk * 8));
-            m->counts_cap = chunk;
-        }
-        PERC_CHECK(cudaMemsetAsync(m->counts, 0, (size_t)chunk * 8, m->stream));
-        for (int k = 0; k < chunk; ++k) {
-            perc_level_kernel<<<grid, 256, 0, m->stream>>>(m->pore, m->C, m->F[cur],
-                                                           m->F[cur ^ 1], m->g, m->counts + k);
-            cur ^= 1;
-        }
-        PERC_CHECK(cudaGetLastError());
-        host.resize((size_t)chunk);
-        PERC_CHECK(cudaMemcpyAsync(host.data(), m->counts, (size_t)chunk * 8,
-                                   cudaMemcpyDeviceToHost, m->stream));
+        PERC_CHECK(cudaGraphLaunch(m->passes, m->stream));
+        PERC_CHECK(cudaMemcpyAsync(host, m->counts, sizeof(host), cudaMemcpyDeviceToHost,
+                                   m->stream));
         PERC_CHECK(cudaStreamSynchronize(m->stream));
         int k = 0;
-        while (k < chunk && host[(size_t)k] != 0ull) ++k;
+        while (k < kPassesPerGraph && host[k] != 0ull) ++k;
         steps += k;
-        if (k < chunk) break;
-        if (chunk < 4096) chunk *= 2;
+        if (k < kPassesPerGraph) break;
     }
     PERC_CHECK(cudaMemsetAsync(m->meas, 0, 3 * 8, m->stream));
     perc_measure_kernel<<<grid, 256, 0, m->stream>>>(m->C, m->g, m->meas);

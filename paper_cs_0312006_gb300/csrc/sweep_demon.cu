@@ -79,9 +79,13 @@ __device__ __forceinline__ uint4 demon_vec(const uint4& s, uint4& qv, const uint
 }
 
 // W % 16 == 0: the register-window strip walk of the Metropolis strip kernel,
-// with the own demons streamed beside the own spins.
+// with the own demons streamed beside the own spins.  The pass is a memory
+// stream, so occupancy is what keeps loads in flight: in 2D at most 64
+// registers (four CTAs per SM) measured 0.869 of the copy bandwidth at
+// L = 32768 against 0.828 with 73 registers and three CTAs; 3D keeps three
+// CTAs (at 64 registers it would spill).
 template <int DIMS, bool MEASURE>
-__global__ void __launch_bounds__(256) pass_demon_strip(PassArgs a) {
+__global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 3) pass_demon_strip(PassArgs a) {
     const int nv = a.nv, S = a.strips, L = a.L;
     const int rows = (int)a.rows;
     const int lane = threadIdx.x & 31;
