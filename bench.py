@@ -72,17 +72,17 @@ TRAFFIC = {
     ("scan", "bitpack"): {"bytes_per_update": 0.2269,
                           "sha1": "86f42d2317495a12cb5e73c54db6ca2ccc8251fd",
                           "sources": ["sweep_bitpack.cu", "pass_bodies.cuh", "ising_device.cuh"]},
-    ("scan", "demon"): {"bytes_per_update": 4.5424,
-                        "sha1": "a8e4d033a61dab46d0fa336ea9d92e9c200ce87f",
+    ("scan", "demon"): {"bytes_per_update": 4.5103,
+                        "sha1": "b03353c7d650f8c9400148d0b412b50b3b4510b5",
                         "sources": ["sweep_demon.cu", "pass_bodies.cuh", "ising_device.cuh"]},
-    ("big", "int8"): {"bytes_per_update": 3.0038,
-                      "sha1": "3510fb0f7769ee1940b19835f50c6f7aa35e3752",
+    ("big", "int8"): {"bytes_per_update": 3.0037,
+                      "sha1": "bd0d2ee2cb80116005bf54bb4d6d1bfd1518710b",
                       "sources": ["sweep_int8.cu", "pass_bodies.cuh", "ising_device.cuh"]},
-    ("big", "bitpack"): {"bytes_per_update": 0.3828,
-                         "sha1": "2cea39923be5e5d0369d4c02c5b9068936caf58a",
+    ("big", "bitpack"): {"bytes_per_update": 0.3830,
+                         "sha1": "86f42d2317495a12cb5e73c54db6ca2ccc8251fd",
                          "sources": ["sweep_bitpack.cu", "pass_bodies.cuh", "ising_device.cuh"]},
-    ("big", "demon"): {"bytes_per_update": 5.0003,
-                       "sha1": "a8e4d033a61dab46d0fa336ea9d92e9c200ce87f",
+    ("big", "demon"): {"bytes_per_update": 5.0047,
+                       "sha1": "b03353c7d650f8c9400148d0b412b50b3b4510b5",
                        "sources": ["sweep_demon.cu", "pass_bodies.cuh", "ising_device.cuh"]},
 }
 

@@ -81,6 +81,14 @@ def _load():
         lib.orc_site_update.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64, u32p,
                                         ctypes.c_uint32, ctypes.c_int64, ctypes.c_int]
         lib.orc_site_update.restype = ctypes.c_int
+        lib.orc_half_sweep_multihit.argtypes = [ctypes.c_int, ctypes.c_int, i8p,
+                                                ctypes.c_uint64, u32p, ctypes.c_uint32,
+                                                ctypes.c_int, ctypes.c_int]
+        lib.orc_half_sweep_multihit.restype = ctypes.c_int
+        lib.orc_run_multihit.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_uint64, i8p, ctypes.c_uint32, ctypes.c_int64,
+                                         ctypes.c_int, ctypes.c_int, i64p, i64p, ctypes.c_int64]
+        lib.orc_run_multihit.restype = ctypes.c_int64
         lib.orc_thresholds_heatbath.argtypes = [ctypes.c_int, ctypes.c_double, u32p]
         lib.orc_thresholds_heatbath.restype = ctypes.c_int
         lib.orc_sweep.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64,
@@ -188,6 +196,37 @@ def half_sweep(dims: int, L: int, s: np.ndarray, seed: int, thr: np.ndarray,
                                      _ptr(tab, ctypes.c_uint32), t, c, rule)
     if rc != 0:
         raise ValueError(f"orc_half_sweep -> {rc}")
+
+
+def half_sweep_multihit(dims: int, L: int, s: np.ndarray, seed: int, thr: np.ndarray,
+                        t: int, c: int, hits: int) -> None:
+    """One multi-hit Metropolis colour pass in place (hits trials per site)."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    thr = np.ascontiguousarray(np.asarray(thr, dtype=np.uint32)[:3])
+    rc = _load().orc_half_sweep_multihit(dims, L, _ptr(s, ctypes.c_int8), seed,
+                                         _ptr(thr, ctypes.c_uint32), t, c, hits)
+    if rc != 0:
+        raise ValueError(f"orc_half_sweep_multihit -> {rc}")
+
+
+def run_multihit(dims: int, L: int, beta: float, seed: int, nsweeps: int, hits: int,
+                 measure_every: int = 1, start: int = HOT, s: np.ndarray | None = None,
+                 t0: int = 0):
+    """Multi-hit checkerboard Metropolis sweeps numbered t0, t0+1, ...;
+    returns (s, E, M) as run() does."""
+    if s is None:
+        s = init(dims, L, seed, start)
+    else:
+        s = np.ascontiguousarray(s, dtype=np.int8).copy()
+    cap = nsweeps // measure_every + 2
+    E = np.zeros(cap, dtype=np.int64)
+    M = np.zeros(cap, dtype=np.int64)
+    n = _load().orc_run_multihit(dims, L, float(beta), seed, _ptr(s, ctypes.c_int8), t0,
+                                 nsweeps, measure_every, hits, _ptr(E, ctypes.c_int64),
+                                 _ptr(M, ctypes.c_int64), cap)
+    if n < 0:
+        raise ValueError(f"orc_run_multihit -> {n}")
+    return s, E[:n].copy(), M[:n].copy()
 
 
 def site_update(dims: int, L: int, s: np.ndarray, seed: int, thr: np.ndarray, t: int,

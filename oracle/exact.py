@@ -150,14 +150,17 @@ def state_energy(s, nb_fwd) -> int:
 
 
 def half_sweep_matrix(dims: int, L: int, thr, colour: int,
-                      heatbath: bool = False) -> np.ndarray:
+                      heatbath: bool = False, hits: int = 1) -> np.ndarray:
     """P[a, b] = probability that one colour pass maps state a to state b.
 
     Each site of the colour flips independently (its neighbours all have the
     other colour).  Metropolis: with probability 1 if k <= 0 and
     thr[k/2 - 1] / 2^32 if k > 0, k = s_i * (sum of its 2*dims neighbours).
     Heat bath: with probability thr[d] / 2^32, d = (2*dims - k)/2 the number
-    of disagreeing neighbours.
+    of disagreeing neighbours.  Metropolis with ``hits`` trials per visit: the
+    site's own two-state chain (flip with the Metropolis probability of its
+    current state; the flipped state's move back has k <= 0 or k > 0 as its
+    own k says) taken ``hits`` steps by a matrix power.
     """
     n = L ** dims
     coords = _coords(dims, L)
@@ -171,8 +174,13 @@ def half_sweep_matrix(dims: int, L: int, thr, colour: int,
             k = int(s[i] * sum(s[j] for j in nb[i]))
             if heatbath:
                 probs.append(float(thr[(2 * dims - k) // 2]) / 2.0 ** 32)
-            else:
+            elif hits == 1:
                 probs.append(1.0 if k <= 0 else float(thr[k // 2 - 1]) / 2.0 ** 32)
+            else:
+                def acc(kk):
+                    return 1.0 if kk <= 0 else float(thr[kk // 2 - 1]) / 2.0 ** 32
+                T = np.array([[1 - acc(k), acc(k)], [acc(-k), 1 - acc(-k)]])
+                probs.append(float(np.linalg.matrix_power(T, hits)[0, 1]))
         for mask in range(2 ** len(sites)):
             b, pr = a, 1.0
             for bit, i in enumerate(sites):

@@ -350,6 +350,60 @@ int orc_site_update(int dims, int L, const int8_t *s, uint64_t seed,
     return f ? -s[i] : s[i];
 }
 
+/* Multi-hit Metropolis (a variant of Sec. 2.2's rule): each visited site   */
+/* takes `hits` successive Metropolis trials, its neighbours fixed, the     */
+/* spin it holds after a trial being the one the next trial may flip.       */
+/* Trial m draws word hh & 3 of Philox(seed; hh >> 2, t, c + 2m, TAG_SWEEP); */
+/* one hit is exactly the Metropolis pass.                                  */
+int orc_half_sweep_multihit(int dims, int L, int8_t *s, uint64_t seed,
+                            const uint32_t thr[3], uint32_t t, int c, int hits)
+{
+    if (dims != 2 && dims != 3) return -1;
+    if (L < 2 || (L & 1) || (c != 0 && c != 1) || hits < 1 || hits > 64) return -1;
+    int zdim = dims == 3 ? L : 1;
+    int64_t LL = (int64_t)L * L;
+    for (int z = 0; z < zdim; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                if (((x + y + z) & 1) != c) continue;
+                int64_t i = (int64_t)z * LL + (int64_t)y * L + x;
+                int h = neighbour_sum(dims, L, s, x, y, z);
+                int64_t hh = i >> 1;
+                int sigma = s[i];
+                for (int m = 0; m < hits; ++m)
+                    if (accept_flip(sigma * h, thr, seed, (uint32_t)(hh >> 2), t,
+                                    (uint32_t)(c + 2 * m), TAG_SWEEP, (unsigned)(hh & 3)))
+                        sigma = -sigma;
+                s[i] = (int8_t)sigma;
+            }
+    return 0;
+}
+
+int64_t orc_run_multihit(int dims, int L, double beta, uint64_t seed, int8_t *s,
+                         uint32_t t0, int64_t nsweeps, int measure_every, int hits,
+                         int64_t *E, int64_t *M, int64_t cap)
+{
+    uint32_t thr[3];
+    int rc = orc_thresholds(dims, beta, thr);
+    if (rc) return rc;
+    if (measure_every < 1 || nsweeps < 0) return -1;
+    int64_t nrec = 0;
+    for (int64_t n = 0; n < nsweeps; ++n) {
+        uint32_t t = t0 + (uint32_t)n;
+        rc = orc_half_sweep_multihit(dims, L, s, seed, thr, t, 0, hits);
+        if (rc == 0) rc = orc_half_sweep_multihit(dims, L, s, seed, thr, t, 1, hits);
+        if (rc) return rc;
+        if (((uint64_t)t + 1) % (uint64_t)measure_every == 0) {
+            if (nrec < cap) {
+                E[nrec] = orc_energy(dims, L, s);
+                M[nrec] = orc_magnetization(dims, L, s);
+            }
+            ++nrec;
+        }
+    }
+    return nrec;
+}
+
 /* Metropolis colour pass (rule 0). */
 int orc_half_sweep(int dims, int L, int8_t *s, uint64_t seed,
                    const uint32_t thr[3], uint32_t t, int c)

@@ -228,10 +228,13 @@ __global__ void __launch_bounds__(256) perc_band_kernel(const uint32_t* pore, ui
         lo = older.lo < lo ? older.lo : lo;
         hi = older.hi > hi ? older.hi : hi;
     }
+    const uint32_t w0 = lo <= hi ? lo * g.nq : 0u, w1 = lo <= hi ? (hi + 1u) * g.nq : 0u;
+    // the grid covers the whole medium; CTAs past the band leave at once
+    // (a whole CTA at a time, before any barrier)
+    if (w0 + blockIdx.x * blockDim.x >= w1) return;
     unsigned long long cnt = 0ull;
     unsigned int got_lo = 0xFFFFFFFFu, got_hi = 0u;
-    if (lo <= hi) {
-        const uint32_t w0 = lo * g.nq, w1 = (hi + 1u) * g.nq;
+    {
         const uint32_t stride = gridDim.x * blockDim.x;
         for (uint32_t w = w0 + blockIdx.x * blockDim.x + threadIdx.x; w < w1; w += stride) {
             const uint32_t add = grow_word(pore, C, Fo, g, w);
@@ -245,6 +248,7 @@ __global__ void __launch_bounds__(256) perc_band_kernel(const uint32_t* pore, ui
             }
         }
     }
+    if (!__syncthreads_or(cnt != 0ull)) return;  // nothing joined in this CTA's words
     band_add(&bands[k % kBandSlots], got_lo, got_hi);
     block_sum_u64(cnt, added);
 }
