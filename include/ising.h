@@ -64,6 +64,10 @@ enum {
  *       neighbours, P(S') / (P(S) + P(S')) = 1 / (1 + exp(beta dE)) for the
  *       flipped state: every site draws and flips iff
  *       u < floor(2^32 / (1 + exp(4 beta (dims - d)))).
+ *   MULTIHIT: Metropolis with `hits` successive trials per visit, the
+ *       neighbours fixed (each trial as above, on the spin the site then
+ *       holds); trial m draws with counter word 2 = c + 2m instead of c, so
+ *       one hit is exactly METROPOLIS.  Still samples P(S); fewer rejections.
  *   DEMON: Creutz's deterministic dynamics, which Sec. 2.2 cites (checkerboard
  *       sweeps, no random numbers).  Every site carries a demon of energy 4q,
  *       q = 0..qmax; a site flips iff 0 <= q - (dims - d) <= qmax, and its
@@ -76,7 +80,8 @@ enum {
 enum {
     ISING_RULE_METROPOLIS = 0,
     ISING_RULE_HEATBATH = 1,
-    ISING_RULE_DEMON = 2  /* deterministic demon dynamics, int8 layout (ising_set_demons) */
+    ISING_RULE_DEMON = 2,    /* deterministic demon dynamics, int8 layout (ising_set_demons) */
+    ISING_RULE_MULTIHIT = 3  /* Metropolis with several trials per visit (ising_set_hits) */
 };
 
 /* Initial states (Sec. 2.2: spins up with probability p). */
@@ -208,6 +213,10 @@ int ising_compute_thresholds(int dims, double beta, uint32_t out[3]);
  * records are unchanged. */
 int ising_set_rule(ising_lattice *lat, int rule);
 
+/* Trials per visit of ISING_RULE_MULTIHIT, 1 <= hits <= 64 (default 2;
+ * ISING_EINVAL otherwise).  The rule itself is chosen by ising_set_rule. */
+int ising_set_hits(ising_lattice *lat, int hits);
+
 /* Load the demons of ISING_RULE_DEMON (int8 layout only; ISING_EINVAL for the
  * bit-packed layout).  host_q: L^dims bytes in canonical order, each <= qmax;
  * or NULL, every demon = fill (0 <= fill <= qmax).  1 <= qmax <= 63.  The
@@ -269,8 +278,8 @@ typedef struct ising_batch_opts {
  * ising_batch_launch and ising_batch_sync they must not be used directly, and
  * they must outlive the batch.  Device memory: a job table (96 B per lattice).
  * Lattices of each update rule (ISING_RULE_*) form their own queues, run by
- * one persistent launch per rule present; demon-dynamics lattices are
- * advanced by the per-lattice kernels like the huge ones.  A lattice's rule
+ * one persistent launch per rule present; demon-dynamics and multi-hit
+ * lattices are advanced by the per-lattice kernels like the huge ones.  A lattice's rule
  * must not change while the batch exists (ising_batch_launch then returns
  * ISING_EINVAL).
  */
@@ -318,7 +327,8 @@ void ising_batch_destroy(ising_batch *b);
  *   opts           block_threads, cluster_size and big_sites as for
  *                  ising_batch_create (NULL: defaults); every lattice runs in
  *                  the persistent kernel (huge_sites and use_graph are ignored),
- *                  so ISING_RULE_DEMON lattices are refused (ISING_EINVAL).
+ *                  so ISING_RULE_DEMON and ISING_RULE_MULTIHIT lattices are
+ *                  refused (ISING_EINVAL).
  * The spins and sweep counters of the handles advance as with ising_sweep.
  * The first call on a device looks up the array's device address and the
  * resident grid size; make that first call before any stream capture.

@@ -361,10 +361,10 @@ int ising_batch_create(ising_batch** out, ising_lattice* const* lats, int n,
     for (int i = 0; i < n; ++i) {
         const int r = b->lats[i]->rule == ISING_RULE_HEATBATH ? 1 : 0;
         b->rule[i] = b->lats[i]->rule;
-        // the largest lattices, and the demon dynamics (no persistent-kernel form), go
-        // through the per-lattice kernels
+        // the largest lattices, and the rules without a persistent-kernel form
+        // (demon dynamics, multi-hit), go through the per-lattice kernels
         if ((o.huge_sites > 0 && b->lats[i]->sites >= o.huge_sites) ||
-            b->lats[i]->rule == ISING_RULE_DEMON) {
+            b->lats[i]->rule == ISING_RULE_DEMON || b->lats[i]->rule == ISING_RULE_MULTIHIT) {
             b->huge.push_back(i);
             b->in_table[i] = 0;
         } else {
@@ -585,7 +585,8 @@ int ising_batch_run_static(ising_lattice* const* lats, int n, const int64_t* swe
     for (int i = 0; i < n; ++i) {
         const ising_lattice* h = lats[i];
         if (!h || sweeps[i] < 0 || sweeps[i] > 0x7FFFFFFF) return ISING_EINVAL;
-        if (h->rule == ISING_RULE_DEMON) return ISING_EINVAL;  // not in the persistent kernel
+        if (h->rule == ISING_RULE_DEMON || h->rule == ISING_RULE_MULTIHIT)
+            return ISING_EINVAL;  // not in the persistent kernel
         const int every = measure_every ? measure_every[i] : 1;
         if (every < 1) return ISING_EINVAL;
         if (sweeps[i] > 0 && h->t + (uint64_t)sweeps[i] - 1 > kMaxSweep) return ISING_ERANGE;

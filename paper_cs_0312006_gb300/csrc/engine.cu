@@ -20,6 +20,7 @@ using ising::PassArgs;
 static_assert(ising::kRuleMetropolis == ISING_RULE_METROPOLIS, "rule values");
 static_assert(ising::kRuleHeatBath == ISING_RULE_HEATBATH, "rule values");
 static_assert(ising::kRuleDemon == ISING_RULE_DEMON, "rule values");
+static_assert(ising::kRuleMultiHit == ISING_RULE_MULTIHIT, "rule values");
 
 namespace {
 
@@ -232,6 +233,7 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     a.dem = nullptr;
     a.qmax = 0;
     a.rot = 0;
+    a.hits = h->hits;
     if (h->rule == ISING_RULE_DEMON) {
         a.dem = h->dem[c];
         a.qmax = h->qmax;
@@ -359,7 +361,8 @@ int ising_sweep(ising_lattice* h, int64_t n, int measure_every) {
         if (rc != ISING_OK) return rc;
     }
     int64_t rec = h->n_rec;
-    if (h->sites <= kSmallSites && n >= 2 && n <= 0x7FFFFFFF && h->rule != ISING_RULE_DEMON) {
+    if (h->sites <= kSmallSites && n >= 2 && n <= 0x7FFFFFFF &&
+        (h->rule == ISING_RULE_METROPOLIS || h->rule == ISING_RULE_HEATBATH)) {
         const int rc = small_sweep(h, n, measure_every, h->obs ? h->obs + 2 * rec : nullptr);
         if (rc != ISING_OK) return rc;
         h->t += (uint64_t)n;
@@ -483,10 +486,17 @@ int ising_compute_thresholds_heatbath(int dims, double beta, uint32_t out[7]) {
 
 int ising_set_rule(ising_lattice* h, int rule) {
     if (!h) return ISING_EINVAL;
-    if (rule != ISING_RULE_METROPOLIS && rule != ISING_RULE_HEATBATH && rule != ISING_RULE_DEMON)
+    if (rule != ISING_RULE_METROPOLIS && rule != ISING_RULE_HEATBATH && rule != ISING_RULE_DEMON &&
+        rule != ISING_RULE_MULTIHIT)
         return ISING_EINVAL;
     if (rule == ISING_RULE_DEMON && !h->dem[0]) return ISING_EINVAL;  // ising_set_demons first
     h->rule = rule;
+    return ISING_OK;
+}
+
+int ising_set_hits(ising_lattice* h, int hits) {
+    if (!h || hits < 1 || hits > 64) return ISING_EINVAL;
+    h->hits = hits;
     return ISING_OK;
 }
 

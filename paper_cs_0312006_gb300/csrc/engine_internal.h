@@ -36,6 +36,7 @@ struct ising_lattice {
     void* dem[2] = {nullptr, nullptr};  // demons per colour (int8 layout), or null
     int qmax = 0;                       // demon capacity: q = 0..qmax
     int64_t dem_rot = 0;                // half rows the demons have moved on, mod rows
+    int hits = 2;                       // multi-hit Metropolis: trials per visit
 };
 
 namespace ising {
@@ -43,10 +44,9 @@ namespace ising {
 struct DeviceProps {
     int device = -1;
     int sm_count = 0;
-    // resident CTAs per SM of the int8 strip pass and the bit-packed pass,
-    // indexed [rule][dims - 2][measure]
-    int blocks_per_sm_vec[2][2][2] = {{{1, 1}, {1, 1}}, {{1, 1}, {1, 1}}};
-    int blocks_per_sm_packed[2][2][2] = {{{1, 1}, {1, 1}}, {{1, 1}, {1, 1}}};
+    // resident CTAs per SM of the int8 strip pass and the bit-packed pass
+    int blocks_per_sm_vec[4][2][2] = {};     // [rule][dims - 2][measure]; rule 2 unused
+    int blocks_per_sm_packed[4][2][2] = {};
     int blocks_per_sm_demon[2][2] = {{1, 1}, {1, 1}};  // demon strip pass [dims-2][measure]
     int* d_err = nullptr;  // raised by a kernel whose bounded wait ran out
 };

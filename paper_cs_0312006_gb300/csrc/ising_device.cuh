@@ -27,6 +27,7 @@ constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
 constexpr int kRuleMetropolis = 0;
 constexpr int kRuleHeatBath = 1;
 constexpr int kRuleDemon = 2;
+constexpr int kRuleMultiHit = 3;
 
 // Counter word 3 ("tag") separates the uses of the stream.
 constexpr uint32_t kTagSweep = 0u;
@@ -78,6 +79,7 @@ struct PassArgs {
     void* dem;
     int qmax;
     uint32_t rot;
+    int hits;  // multi-hit Metropolis: trials per visit (hit m draws with word 2 = c + 2m)
 };
 
 // Block-wide sum of two ints followed by one 64-bit atomic each into the

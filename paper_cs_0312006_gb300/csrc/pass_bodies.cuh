@@ -111,6 +111,27 @@ __device__ __forceinline__ uint32_t heatbath_threshold(int d, const PassArgs& a)
     return t;
 }
 
+// Multi-hit Metropolis on one 4-site word: a.hits successive trials, the
+// neighbours fixed; after a trial the flipped sites' D becomes 2(2 dims - d).
+// Trial m draws Philox(seed; group, t, c + 2m, 0).  Returns the net flip mask.
+template <int DIMS>
+__device__ __forceinline__ uint32_t multihit_word(uint32_t D, uint32_t group, const PassArgs& a) {
+    constexpr uint32_t q2 = 4u * DIMS * kByteOnes;
+    uint32_t net = 0u;
+#pragma unroll 1
+    for (int m = 0; m < a.hits; ++m) {
+        uint32_t X = downhill_mask<DIMS>(D);
+        if (X != 0xFEFEFEFEu) {
+            const Philox4 u = philox4x32_10(group, a.t, (uint32_t)a.c + 2u * (uint32_t)m,
+                                            kTagSweep, a.key0, a.key1);
+            X |= uphill_count<DIMS>(D, u, a);
+        }
+        D = (D & ~X) | ((q2 - D) & X);
+        net ^= X;
+    }
+    return net;
+}
+
 template <int DIMS>
 __device__ __forceinline__ uint32_t disagreements(uint32_t s, uint32_t n0, uint32_t n1,
                                                   uint32_t n2, uint32_t n3, uint32_t n4,
@@ -175,6 +196,8 @@ __device__ __forceinline__ void int8_word(const PassArgs& a, const WordGeom& g, 
         if (RULE == kRuleHeatBath) {
             const Philox4 u = philox4x32_10(w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
             X = heatbath_count<DIMS>(D, u, a);
+        } else if (RULE == kRuleMultiHit) {
+            X = multihit_word<DIMS>(D, w, a);
         } else {
             X = downhill_mask<DIMS>(D);
             if (X != 0xFEFEFEFEu) {
@@ -235,6 +258,52 @@ __device__ __forceinline__ void int8_word(const PassArgs& a, const WordGeom& g, 
         d_val[j] = (2 * DIMS - s * hsum) >> 1;  // k = s*h = 2*(dims - d)
         if (d_val[j] < DIMS || RULE == kRuleHeatBath) need = true;
     }
+    if (RULE == kRuleMultiHit) {
+        int d_cur[4], flips[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d_cur[j] = d_val[j];
+#pragma unroll 1
+        for (int m = 0; m < a.hits; ++m) {
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) any |= valid[j] && d_cur[j] < DIMS;
+            uint32_t uu[4] = {0u, 0u, 0u, 0u};
+            if (any) {
+                const Philox4 q = philox4x32_10(w, a.t, (uint32_t)a.c + 2u * (uint32_t)m,
+                                                kTagSweep, a.key0, a.key1);
+                uu[0] = q.w0;
+                uu[1] = q.w1;
+                uu[2] = q.w2;
+                uu[3] = q.w3;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                bool f = d_cur[j] >= DIMS;
+                if (!f) {
+                    const int dj = d_cur[j];
+                    const uint32_t t = DIMS == 2 ? (dj == 0 ? a.thr[1] : a.thr[0])
+                                                 : (dj == 0 ? a.thr[2] : (dj == 1 ? a.thr[1] : a.thr[0]));
+                    f = uu[j] < t;
+                }
+                if (f) {
+                    d_cur[j] = 2 * DIMS - d_cur[j];
+                    flips[j] ^= 1;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!valid[j]) continue;
+            const int sn = flips[j] ? -s_val[j] : s_val[j];
+            if (flips[j]) own_b[h0 + j] = (int8_t)sn;
+            if (MEASURE) {
+                m_neg += sn < 0;
+                n_sites += 1;
+                if (a.c == 1) e_acc += 2 * d_cur[j] - 2 * DIMS;
+            }
+        }
+        return;
+    }
     uint32_t u[4] = {0u, 0u, 0u, 0u};
     if (need) {
         const Philox4 q = philox4x32_10(w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
@@ -285,7 +354,36 @@ __device__ __forceinline__ uint4 update_vec(const uint4& s, const uint4& x, cons
     D[1] = disagreements<DIMS>(s.y, x.y, xs.y, ym.y, yp.y, zm.y, zp.y);
     D[2] = disagreements<DIMS>(s.z, x.z, xs.z, ym.z, yp.z, zm.z, zp.z);
     D[3] = disagreements<DIMS>(s.w, x.w, xs.w, ym.w, yp.w, zm.w, zp.w);
-    if (RULE == kRuleHeatBath) {  // every site draws
+    if (RULE == kRuleMultiHit) {
+        constexpr uint32_t q2 = 4u * DIMS * kByteOnes;
+        uint32_t Dc[4] = {D[0], D[1], D[2], D[3]};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) X[w] = 0u;
+#pragma unroll 1
+        for (int m = 0; m < a.hits; ++m) {
+            uint32_t Y[4];
+            bool need = false;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                Y[w] = downhill_mask<DIMS>(Dc[w]);
+                need |= Y[w] != 0xFEFEFEFEu;
+            }
+            if (need) {
+                Philox4 u[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    u[w] = philox4x32_10(g0 + (uint32_t)w, a.t, (uint32_t)a.c + 2u * (uint32_t)m,
+                                         kTagSweep, a.key0, a.key1);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) Y[w] |= uphill_count<DIMS>(Dc[w], u[w], a);
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                Dc[w] = (Dc[w] & ~Y[w]) | ((q2 - Dc[w]) & Y[w]);
+                X[w] ^= Y[w];
+            }
+        }
+    } else if (RULE == kRuleHeatBath) {  // every site draws
         Philox4 u[4];
 #pragma unroll
         for (int w = 0; w < 4; ++w)
@@ -495,7 +593,7 @@ __device__ __forceinline__ uint32_t group_accept(const K& k, const Philox4& u, i
 // which raises register pressure in the batched kernel).
 template <int DIMS, typename K>
 __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uint32_t hbase,
-                                                  const PassArgs& a) {
+                                                  const PassArgs& a, uint32_t c2) {
     uint32_t acc = 0u;
     const uint32_t m = hbase & 3u, g0 = hbase >> 2;
     if (m == 0u) {
@@ -506,7 +604,7 @@ __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uin
             for (int i = 0; i < 4; ++i) {
                 const int gi = 4 * half + i;
                 if ((need >> (4 * gi)) & 0xFu)
-                    u[i] = philox4x32_10(g0 + (uint32_t)gi, a.t, (uint32_t)a.c, kTagSweep,
+                    u[i] = philox4x32_10(g0 + (uint32_t)gi, a.t, c2, kTagSweep,
                                          a.key0, a.key1);
                 else
                     u[i] = Philox4{0u, 0u, 0u, 0u};
@@ -521,7 +619,7 @@ __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uin
         const int lo = 4 * g - (int)m;  // bit of the group's word 0 (may be < 0)
         const uint32_t gmask = lo >= 0 ? (0xFu << lo) : (0xFu >> (-lo));
         if (!(need & gmask)) continue;
-        const Philox4 u = philox4x32_10(g0 + (uint32_t)g, a.t, (uint32_t)a.c, kTagSweep, a.key0,
+        const Philox4 u = philox4x32_10(g0 + (uint32_t)g, a.t, c2, kTagSweep, a.key0,
                                         a.key1);
         const uint32_t w[4] = {u.w0, u.w1, u.w2, u.w3};
 #pragma unroll
@@ -590,7 +688,25 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
     if constexpr (RULE == kRuleHeatBath) {  // every valid site draws
         const Digits k = DIMS == 2 ? digits2(s ^ o, s ^ sh, s ^ oym, s ^ oyp)
                                    : digits3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
-        flip = packed_accept<DIMS>(k, valid, r * W + 32u * q, a);
+        flip = packed_accept<DIMS>(k, valid, r * W + 32u * q, a, (uint32_t)a.c);
+    } else if constexpr (RULE == kRuleMultiHit) {  // a.hits trials, neighbours fixed
+        uint32_t cur = s;
+#pragma unroll 1
+        for (int m = 0; m < a.hits; ++m) {
+            Counts k;
+            if (DIMS == 2) {
+                k = count2(cur ^ o, cur ^ sh, cur ^ oym, cur ^ oyp);
+            } else {
+                k = count3(cur ^ o, cur ^ sh, cur ^ oym, cur ^ oyp, cur ^ ozm, cur ^ ozp);
+            }
+            uint32_t f = k.always;
+            const uint32_t need = ~k.always & valid;
+            if (need)
+                f |= packed_accept<DIMS>(k, need, r * W + 32u * q, a,
+                                         (uint32_t)a.c + 2u * (uint32_t)m);
+            cur ^= f & valid;
+        }
+        flip = cur ^ s;
     } else {
         Counts k;
         if (DIMS == 2) {
@@ -600,7 +716,7 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
         }
         flip = k.always;
         const uint32_t need = ~k.always & valid;
-        if (need) flip |= packed_accept<DIMS>(k, need, r * W + 32u * q, a);
+        if (need) flip |= packed_accept<DIMS>(k, need, r * W + 32u * q, a, (uint32_t)a.c);
     }
     const uint32_t snew = s ^ (flip & valid);
     own[row + q] = snew;

@@ -139,6 +139,10 @@ cudaError_t packed_query_occupancy(DeviceProps& dp) {
     ISING_OCC(kRuleHeatBath, 2, true)
     ISING_OCC(kRuleHeatBath, 3, false)
     ISING_OCC(kRuleHeatBath, 3, true)
+    ISING_OCC(kRuleMultiHit, 2, false)
+    ISING_OCC(kRuleMultiHit, 2, true)
+    ISING_OCC(kRuleMultiHit, 3, false)
+    ISING_OCC(kRuleMultiHit, 3, true)
 #undef ISING_OCC
     return cudaSuccess;
 }
@@ -155,8 +159,9 @@ static cudaError_t packed_pass_rule(const PassArgs& a, int dims, bool measure,
 
 cudaError_t packed_pass(const PassArgs& a, int dims, bool measure, int rule,
                         const DeviceProps& dp, cudaStream_t st) {
-    return rule == kRuleHeatBath ? packed_pass_rule<kRuleHeatBath>(a, dims, measure, dp, st)
-                                 : packed_pass_rule<kRuleMetropolis>(a, dims, measure, dp, st);
+    if (rule == kRuleHeatBath) return packed_pass_rule<kRuleHeatBath>(a, dims, measure, dp, st);
+    if (rule == kRuleMultiHit) return packed_pass_rule<kRuleMultiHit>(a, dims, measure, dp, st);
+    return packed_pass_rule<kRuleMetropolis>(a, dims, measure, dp, st);
 }
 
 cudaError_t packed_init(uint32_t* col0, uint32_t* col1, int L, int dims, int64_t rows, int start,

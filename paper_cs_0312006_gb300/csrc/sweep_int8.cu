@@ -261,6 +261,10 @@ cudaError_t int8_query_occupancy(DeviceProps& dp) {
     ISING_OCC(kRuleHeatBath, 2, true)
     ISING_OCC(kRuleHeatBath, 3, false)
     ISING_OCC(kRuleHeatBath, 3, true)
+    ISING_OCC(kRuleMultiHit, 2, false)
+    ISING_OCC(kRuleMultiHit, 2, true)
+    ISING_OCC(kRuleMultiHit, 3, false)
+    ISING_OCC(kRuleMultiHit, 3, true)
 #undef ISING_OCC
     return cudaSuccess;
 }
@@ -291,9 +295,11 @@ cudaError_t int8_pass_rule(const PassArgs& a, int dims, int64_t half_sites, bool
 
 cudaError_t int8_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure, int rule,
                       const DeviceProps& dp, cudaStream_t st) {
-    return rule == kRuleHeatBath
-               ? int8_pass_rule<kRuleHeatBath>(a, dims, half_sites, measure, dp, st)
-               : int8_pass_rule<kRuleMetropolis>(a, dims, half_sites, measure, dp, st);
+    if (rule == kRuleHeatBath)
+        return int8_pass_rule<kRuleHeatBath>(a, dims, half_sites, measure, dp, st);
+    if (rule == kRuleMultiHit)
+        return int8_pass_rule<kRuleMultiHit>(a, dims, half_sites, measure, dp, st);
+    return int8_pass_rule<kRuleMetropolis>(a, dims, half_sites, measure, dp, st);
 }
 
 static unsigned grid_for(int64_t n, const DeviceProps& dp) {

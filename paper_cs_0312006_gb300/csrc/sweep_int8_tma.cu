@@ -299,9 +299,11 @@ bool int8_tma_preferred(int dims, int L) {
 
 cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, int rule,
                           const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st) {
-    return rule == kRuleHeatBath
-               ? int8_pass_tma_rule<kRuleHeatBath>(a, dims, measure, dp, err, extra_tx, st)
-               : int8_pass_tma_rule<kRuleMetropolis>(a, dims, measure, dp, err, extra_tx, st);
+    if (rule == kRuleHeatBath)
+        return int8_pass_tma_rule<kRuleHeatBath>(a, dims, measure, dp, err, extra_tx, st);
+    if (rule == kRuleMultiHit)
+        return int8_pass_tma_rule<kRuleMultiHit>(a, dims, measure, dp, err, extra_tx, st);
+    return int8_pass_tma_rule<kRuleMetropolis>(a, dims, measure, dp, err, extra_tx, st);
 }
 
 }  // namespace ising

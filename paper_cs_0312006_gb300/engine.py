@@ -20,7 +20,7 @@ from . import _build
 INT8, BITPACK, AUTO = 0, 1, 2
 HOT, COLD_UP, COLD_DOWN = 0, 1, 2
 KERNEL_AUTO, KERNEL_STRIP, KERNEL_TMA = 0, 1, 2
-RULE_METROPOLIS, RULE_HEATBATH, RULE_DEMON = 0, 1, 2
+RULE_METROPOLIS, RULE_HEATBATH, RULE_DEMON, RULE_MULTIHIT = 0, 1, 2, 3
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, ERANGE = 0, -1, -2, -3, -4, -5, -6
 
@@ -84,6 +84,7 @@ def load_library():
                                                   ctypes.c_int),
             "ising_set_rule": ([P, ctypes.c_int], ctypes.c_int),
             "ising_set_demons": ([P, P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "ising_set_hits": ([P, ctypes.c_int], ctypes.c_int),
             "ising_get_demons": ([P, P], ctypes.c_int),
             "ising_get_info": ([P, ctypes.POINTER(IsingInfo)], ctypes.c_int),
             "ising_synchronize": ([P], ctypes.c_int),
@@ -266,6 +267,10 @@ class Lattice:
         """Local update rule of later sweeps: RULE_METROPOLIS, RULE_HEATBATH or
         RULE_DEMON (after set_demons)."""
         _check(self._lib.ising_set_rule(self._h, int(rule)), "ising_set_rule")
+
+    def set_hits(self, hits: int) -> None:
+        """Trials per visit of RULE_MULTIHIT."""
+        _check(self._lib.ising_set_hits(self._h, int(hits)), "ising_set_hits")
 
     def set_demons(self, q: np.ndarray | None = None, fill: int = 0, qmax: int = 3) -> None:
         """Demons of the deterministic dynamics: canonical uint8 array ``q``
