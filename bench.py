@@ -258,6 +258,22 @@ def oracle_sample_rate(budget_s: float, L: int, betas, n_lattices: int, heatbath
                        + (", heat-bath rule" if heatbath else ""))
 
 
+def host_description() -> dict:
+    """The host the CPU baseline ran on: logical cores and the CPU model."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -313,7 +329,7 @@ def _reference_line(args, world, L, dt, what):
         "vs_baseline": None, "dtype": "int8", "data": "synthetic",
         "config": workload_config(args.L, args.steps, args.lattices, args.rule),
         "cpu_baseline": {"value": value, "unit": "site updates/s", "cores": 1,
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle", "sample": sample, "host": host_description()},
         "e2e": {"value": value, "unit": "site updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -516,12 +532,12 @@ def run_gpu(args, world, rank, local):
     if world == 1 and not args.no_cpu_baseline and args.rule == "demon":
         rate, sample = oracle_demon_rate(args.cpu_seconds, L_SCAN, betas, 64)
         cpu = {"value": rate, "unit": "site updates/s", "cores": 1, "kind": "oracle",
-               "sample": sample}
+               "sample": sample, "host": host_description()}
     elif world == 1 and not args.no_cpu_baseline:
         rate, sample = oracle_sample_rate(args.cpu_seconds, L_SCAN, betas, 64,
                                           heatbath=args.rule == "heatbath")
         cpu = {"value": rate, "unit": "site updates/s", "cores": 1, "kind": "oracle",
-               "sample": sample}
+               "sample": sample, "host": host_description()}
 
     line = {
         "metric": "site updates/s", "value": value, "unit": "site updates/s", "n_gpus": world,
@@ -745,7 +761,8 @@ def run_percolation_workload(args):
             k += 1
         ct = time.perf_counter() - t0
         cpu = {"value": k / ct, "unit": "media/s", "cores": 1, "kind": "oracle",
-               "sample": f"{k} media of 2D L={Lb} at P={Pb} (porosity field + face invasion)"}
+               "sample": f"{k} media of 2D L={Lb} at P={Pb} (porosity field + face invasion)",
+               "host": host_description()}
     line = {"metric": "media/s", "value": batch["media_per_s"], "unit": "media/s",
             "workload": "site percolation, 2D: one L=16384 medium at P=0.6 (porosity field "
                         "+ face invasion to the steady state) and a batch of L=128 media at "

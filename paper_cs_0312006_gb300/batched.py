@@ -68,6 +68,22 @@ def run_plain(specs, launches: int = 1, layout_policy="auto", stream=None):
     return time.perf_counter() - t0, lats
 
 
+def run_plain_streams(specs, n_streams: int = 8, layout_policy="auto"):
+    """The plain form spread over ``n_streams`` CUDA streams (lattice j on
+    stream j mod n_streams), so that small lattices' launches can overlap."""
+    import torch
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
+    lats = []
+    for j, sp in enumerate(specs):
+        lats += make_lattices([sp], layout_policy, streams[j % n_streams])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sp, lat in zip(specs, lats):
+        lat.sweep(sp.sweeps, sp.measure_every)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, lats
+
+
 def lattice_result(lat):
     E, M = lat.observables()
     return lat.get_spins(), E, M
@@ -83,16 +99,21 @@ def compare_forms(specs, opts=None, layout_policy="auto"):
     upd = total_updates(specs)
     tb, lats_b = run_batched(specs, opts, 1, layout_policy)
     tp, lats_p = run_plain(specs, 1, layout_policy)
+    ts, lats_s = run_plain_streams(specs, 8, layout_policy)
     mismatches = 0
-    for a, b in zip(lats_b, lats_p):
-        if not same_result(lattice_result(a), lattice_result(b)):
+    for a, b, c in zip(lats_b, lats_p, lats_s):
+        ra = lattice_result(a)
+        if not (same_result(ra, lattice_result(b)) and same_result(ra, lattice_result(c))):
             mismatches += 1
         a.close()
         b.close()
+        c.close()
     return {"lattices": len(specs), "site_updates": upd,
             "batched_s": tb, "batched_updates_per_s": upd / tb,
             "plain_s": tp, "plain_updates_per_s": upd / tp,
-            "batched_over_plain": tp / tb, "mismatches": mismatches}
+            "plain_8_streams_s": ts, "plain_8_streams_updates_per_s": upd / ts,
+            "batched_over_plain": tp / tb, "batched_over_plain_8_streams": ts / tb,
+            "mismatches": mismatches}
 
 
 def scaled(specs, sweeps: int):

@@ -89,3 +89,34 @@ def test_critical_energy_approaches_minus_sqrt2():
     scaled = [L * d[L] for L in (32, 64, 128)]
     assert abs(scaled[2] - scaled[1]) < 0.02 * scaled[2]
     assert d[128] < 6e-3
+
+
+def _onsager_integral_minus_beta_f(beta, n=256):
+    """-beta f from Onsager's double integral (periodic trapezoid rule, which
+    converges exponentially for the smooth integrand away from beta_c):
+    ln 2 / 2 + (1 / 8 pi^2) int int ln[cosh^2 2b - sinh 2b (cos t1 + cos t2)]."""
+    t = 2 * np.pi * np.arange(n) / n
+    c = np.cos(t)
+    arg = np.cosh(2 * beta) ** 2 - np.sinh(2 * beta) * (c[:, None] + c[None, :])
+    return math.log(2.0) / 2 + np.log(arg).mean() / 2
+
+
+@pytest.mark.parametrize("beta", [0.30, 0.50, 0.60])
+def test_onsager_energy_against_the_free_energy_integral(beta):
+    """The elliptic-integral form of u(beta) that the equilibrium pins use
+    equals -d(-beta f)/d beta of Onsager's double integral (an independent
+    form), and the printed values u(0.30) = -0.704499, u(0.50) = -1.745565."""
+    h = 1e-5
+    u_int = -(_onsager_integral_minus_beta_f(beta + h) -
+              _onsager_integral_minus_beta_f(beta - h)) / (2 * h)
+    assert abs(u_int - exact.onsager_energy_per_site(beta)) < 1e-7
+    if beta in (0.30, 0.50):
+        assert abs(exact.onsager_energy_per_site(beta) - {0.30: -0.704499, 0.50: -1.745565}[beta]) < 1e-6
+
+
+def test_kaufman_large_torus_tends_to_onsager():
+    """Away from beta_c the finite torus converges exponentially fast: at
+    L = 64 Kaufman's exact <E>/N equals Onsager's u(beta) to 1e-9."""
+    for beta in (0.30, 0.60):
+        assert abs(exact.kaufman_mean_energy(beta, 64) / 64 ** 2 -
+                   exact.onsager_energy_per_site(beta)) < 1e-9
