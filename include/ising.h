@@ -147,12 +147,27 @@ int ising_sweep(ising_lattice *lat, int64_t n, int measure_every);
 
 /*
  * Read the pending E/M records (oldest first) and clear them.  Synchronises
- * the stream.  *count receives the number pending.  With E == NULL or
- * M == NULL only the count is reported.  If cap < pending nothing is copied,
- * nothing is cleared and ISING_ERANGE is returned.
+ * the stream once (the records are copied through a pinned staging buffer
+ * that the handle keeps).  *count receives the number pending.  With
+ * E == NULL or M == NULL only the count is reported.  If cap < pending
+ * nothing is copied, nothing is cleared and ISING_ERANGE is returned.  On
+ * ISING_ETIMEOUT (a bounded wait gave up since the last check) the records of
+ * this read are dropped.
  */
 int ising_observables(ising_lattice *lat, int64_t *E, int64_t *M, int64_t cap,
                       int64_t *count);
+
+/*
+ * The same read without waiting: enqueue on the handle's stream a copy of the
+ * pending records into `pairs` (host memory, pinned for an asynchronous copy:
+ * cap pairs of int64 (E, M), oldest first) and clear them; *count receives
+ * their number at once.  The values are in place once the stream has passed
+ * this point (an event, ising_synchronize, or any call that syncs), so a
+ * caller can read sweep k's records while sweep k+1 runs.  No timeout check
+ * is made here (ising_synchronize makes it).  If cap < pending nothing is
+ * copied or cleared and ISING_ERANGE is returned.
+ */
+int ising_observables_async(ising_lattice *lat, int64_t *pairs, int64_t cap, int64_t *count);
 
 /* Copy the spins to host memory in canonical order (L^dims int8).  Syncs. */
 int ising_get_spins(ising_lattice *lat, int8_t *host_out);

@@ -54,8 +54,11 @@ int device_props(const DeviceProps** out) {
         ISING_CHECK(ising::int8_query_occupancy(q));
         ISING_CHECK(ising::packed_query_occupancy(q));
         ISING_CHECK(ising::demon_query_occupancy(q));
-        ISING_CHECK(cudaMalloc(reinterpret_cast<void**>(&q.d_err), sizeof(int)));
-        ISING_CHECK(cudaMemset(q.d_err, 0, sizeof(int)));
+        void* flag = nullptr;
+        ISING_CHECK(cudaHostAlloc(&flag, sizeof(int), cudaHostAllocMapped));
+        q.h_err = static_cast<volatile int*>(flag);
+        *q.h_err = 0;
+        ISING_CHECK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&q.d_err), flag, 0));
         p = q;
     }
     *out = &p;
@@ -169,6 +172,9 @@ void free_device(ising_lattice* h) {
     }
     if (h->obs) cudaFree(h->obs);
     h->obs = nullptr;
+    if (h->host_obs) cudaFreeHost(h->host_obs);
+    h->host_obs = nullptr;
+    h->host_obs_cap = 0;
     h->obs_cap = 0;
 
 }
@@ -202,12 +208,10 @@ int clear_records(ising_lattice* h) {
 
 std::atomic<int> g_inject_timeout{0};
 
-// Read and clear the device's bounded-wait flag.
+// Read and clear the device's bounded-wait flag (after a synchronisation).
 int check_timeout(ising_lattice* h) {
-    int flag = 0;
-    ISING_CHECK(cudaMemcpy(&flag, h->dp->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag == 0) return ISING_OK;
-    ISING_CHECK(cudaMemset(h->dp->d_err, 0, sizeof(int)));
+    if (*h->dp->h_err == 0) return ISING_OK;
+    *h->dp->h_err = 0;
     return ISING_ETIMEOUT;
 }
 
@@ -384,21 +388,48 @@ int ising_sweep(ising_lattice* h, int64_t n, int measure_every) {
 
 int ising_observables(ising_lattice* h, int64_t* E, int64_t* M, int64_t cap, int64_t* count) {
     if (!h) return ISING_EINVAL;
+    const int64_t n = h->n_rec;
+    // the copy into pinned staging and the clearing memset go ahead of the one
+    // synchronisation, so a read costs a single round trip
+    const bool copy = E && M && n > 0 && cap >= n;
+    if (copy) {
+        if (h->host_obs_cap < n) {
+            if (h->host_obs) ISING_CHECK(cudaFreeHost(h->host_obs));
+            h->host_obs = nullptr;
+            h->host_obs_cap = 0;
+            int64_t c = n < 64 ? 64 : n;
+            ISING_CHECK(cudaMallocHost(reinterpret_cast<void**>(&h->host_obs), (size_t)c * 16));
+            h->host_obs_cap = c;
+        }
+        ISING_CHECK(cudaMemcpyAsync(h->host_obs, h->obs, (size_t)n * 16, cudaMemcpyDeviceToHost,
+                                    h->stream));
+        ISING_CHECK(cudaMemsetAsync(h->obs, 0, (size_t)n * 16, h->stream));
+    }
     ISING_CHECK(cudaStreamSynchronize(h->stream));
+    if (copy) h->n_rec = 0;  // the slots are zero again
     const int trc = check_timeout(h);
     if (trc != ISING_OK) return trc;
-    if (count) *count = h->n_rec;
+    if (count) *count = n;
     if (!E || !M) return ISING_OK;
-    if (cap < h->n_rec) return ISING_ERANGE;
-    if (h->n_rec > 0) {
-        std::vector<long long> buf((size_t)h->n_rec * 2);
-        ISING_CHECK(cudaMemcpy(buf.data(), h->obs, buf.size() * 8, cudaMemcpyDeviceToHost));
-        for (int64_t r = 0; r < h->n_rec; ++r) {
-            E[r] = buf[2 * r];
-            M[r] = buf[2 * r + 1];
-        }
+    if (cap < n) return ISING_ERANGE;
+    for (int64_t r = 0; r < n; ++r) {
+        E[r] = h->host_obs[2 * r];
+        M[r] = h->host_obs[2 * r + 1];
     }
-    return clear_records(h);
+    return ISING_OK;
+}
+
+int ising_observables_async(ising_lattice* h, int64_t* pairs, int64_t cap, int64_t* count) {
+    if (!h || !count || (!pairs && h->n_rec > 0)) return ISING_EINVAL;
+    const int64_t n = h->n_rec;
+    *count = n;
+    if (n == 0) return ISING_OK;
+    if (cap < n) return ISING_ERANGE;
+    ISING_CHECK(cudaMemcpyAsync(pairs, h->obs, (size_t)n * 16, cudaMemcpyDeviceToHost,
+                                h->stream));
+    ISING_CHECK(cudaMemsetAsync(h->obs, 0, (size_t)n * 16, h->stream));
+    h->n_rec = 0;
+    return ISING_OK;
 }
 
 int ising_export_device(ising_lattice* h, int8_t* dev_out) {
@@ -433,8 +464,14 @@ int ising_get_spins(ising_lattice* h, int8_t* host_out) {
 int ising_set_spins(ising_lattice* h, const int8_t* host_in, uint64_t t) {
     if (!h || !host_in) return ISING_EINVAL;
     if (t > kMaxSweep + 1) return ISING_ERANGE;
-    for (int64_t i = 0; i < h->sites; ++i)
-        if (host_in[i] != 1 && host_in[i] != -1) return ISING_EINVAL;
+    // every value must be +1 or -1; checked in chunks without early exits inside
+    // a chunk, so the compiler can vectorise the test
+    for (int64_t i0 = 0; i0 < h->sites; i0 += 65536) {
+        const int64_t i1 = i0 + 65536 < h->sites ? i0 + 65536 : h->sites;
+        int bad = 0;
+        for (int64_t i = i0; i < i1; ++i) bad |= (host_in[i] != 1) & (host_in[i] != -1);
+        if (bad) return ISING_EINVAL;
+    }
     int8_t* tmp = nullptr;
     ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
     cudaError_t e = cudaMemcpyAsync(tmp, host_in, (size_t)h->sites, cudaMemcpyHostToDevice,

@@ -37,6 +37,8 @@ struct ising_lattice {
     int qmax = 0;                       // demon capacity: q = 0..qmax
     int64_t dem_rot = 0;                // half rows the demons have moved on, mod rows
     int hits = 2;                       // multi-hit Metropolis: trials per visit
+    long long* host_obs = nullptr;      // pinned staging for ising_observables
+    int64_t host_obs_cap = 0;           // in records
 };
 
 namespace ising {
@@ -48,7 +50,10 @@ struct DeviceProps {
     int blocks_per_sm_vec[4][2][2] = {};     // [rule][dims - 2][measure]; rule 2 unused
     int blocks_per_sm_packed[4][2][2] = {};
     int blocks_per_sm_demon[2][2] = {{1, 1}, {1, 1}};  // demon strip pass [dims-2][measure]
-    int* d_err = nullptr;  // raised by a kernel whose bounded wait ran out
+    // raised by a kernel whose bounded wait ran out: one int of mapped pinned
+    // host memory (device view d_err, host view h_err), read without a copy
+    int* d_err = nullptr;
+    volatile int* h_err = nullptr;
 };
 
 // engine.cu helpers shared with batch.cu

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
             // a phase never completed: raise the flag, let this CTA's copies in
             // flight land (bounded), and leave without a reduction
             if (threadIdx.x == 0) {
-                atomicExch(err, 1);
+                *reinterpret_cast<volatile int*>(err) = 1;  // host-mapped flag: a plain store
                 for (int k2 = k; k2 < my_tiles && k2 < k + kStages; ++k2)
                     (void)mbar_wait(&bars[k2 % kStages], (uint32_t)(k2 / kStages) & 1u);
             }

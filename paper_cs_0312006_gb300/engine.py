@@ -74,6 +74,7 @@ def load_library():
             "ising_init": ([P, ctypes.c_int], ctypes.c_int),
             "ising_sweep": ([P, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
             "ising_observables": ([P, i64p, i64p, ctypes.c_int64, i64p], ctypes.c_int),
+            "ising_observables_async": ([P, P, ctypes.c_int64, i64p], ctypes.c_int),
             "ising_get_spins": ([P, P], ctypes.c_int),
             "ising_set_spins": ([P, P, ctypes.c_uint64], ctypes.c_int),
             "ising_export_device": ([P, P], ctypes.c_int),
@@ -213,6 +214,18 @@ class Lattice:
                                            M.ctypes.data_as(i64p), len(E), ctypes.byref(cnt)),
                "ising_observables")
         return E[:n].copy(), M[:n].copy()
+
+    def observables_async(self, pairs: np.ndarray) -> int:
+        """Enqueue the pending records' copy into ``pairs`` (a pinned int64
+        array of shape (cap, 2) or a view of one) and clear them; returns their
+        number at once.  The values are valid after the stream passes this
+        point (e.g. an event recorded next)."""
+        assert pairs.dtype == np.int64 and pairs.flags.c_contiguous
+        cnt = ctypes.c_int64(0)
+        _check(self._lib.ising_observables_async(self._h, pairs.ctypes.data, pairs.size // 2,
+                                                 ctypes.byref(cnt)),
+               "ising_observables_async")
+        return cnt.value
 
     def get_spins(self, out: np.ndarray | None = None) -> np.ndarray:
         info = self.info()

@@ -279,3 +279,25 @@ def test_device_philox_matches_oracle(eng):
         key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
         for i in list(rng.integers(0, n, size=64)) + [0, n - 1]:
             assert got[i].tolist() == oracle.philox4x32_10([i, c1, c2, c3], key).tolist()
+
+
+def test_observables_async_matches_the_oracle(eng):
+    """ising_observables_async: the records land in pinned host memory once the
+    stream passes the call, equal to the oracle's, and are cleared."""
+    import torch
+    lat = eng.Lattice(2, 96, 0.43, 17, layout=INT8)
+    pairs = torch.zeros((8, 2), dtype=torch.int64).pin_memory().numpy()
+    lat.sweep(5, 1)
+    n = lat.observables_async(pairs)
+    assert n == 5
+    lat.synchronize()
+    s_o, E_o, M_o = oracle.run(2, 96, 0.43, 17, 5, measure_every=1)
+    assert np.array_equal(pairs[:5, 0], E_o) and np.array_equal(pairs[:5, 1], M_o)
+    assert lat.observables_async(pairs) == 0  # cleared
+    lat.sweep(3, 1)
+    small = torch.zeros((2, 2), dtype=torch.int64).pin_memory().numpy()
+    with pytest.raises(eng.IsingError):
+        lat.observables_async(small)  # 3 pending, room for 2: nothing copied or cleared
+    E, M = lat.observables()
+    assert len(E) == 3
+    lat.close()
