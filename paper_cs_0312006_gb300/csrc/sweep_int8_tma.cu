@@ -181,7 +181,57 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
         const uint4* oth16 = reinterpret_cast<const uint4*>(oth);
         const uint4* zm16 = reinterpret_cast<const uint4*>(oth + (R + 2u) * W);
         const uint4* zp16 = zm16 + R * nv;
-        for (uint32_t i = 0; i < R; ++i) {
+        uint32_t i0 = 0;
+        if (RULE == kRuleMetropolis) {
+            // two rows per step: eight Philox calls in flight per thread
+            for (; i0 + 1u < R; i0 += 2u) {
+                for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
+                    uint4 S[2], X[2], XS[2], YM[2], YP[2], ZM[2], ZP[2];
+                    uint32_t g0[2], rowg[2];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const uint32_t i = i0 + (uint32_t)q;
+                        const uint32_t y = y0 + i;
+                        const int p = (a.c + (int)y + (int)z) & 1;
+                        const uint32_t* row32 =
+                            reinterpret_cast<const uint32_t*>(oth + (i + 1u) * W);
+                        const uint4 oc = oth16[(i + 1u) * nv + v];
+                        X[q] = oc;
+                        YM[q] = oth16[i * nv + v];
+                        YP[q] = oth16[(i + 2u) * nv + v];
+                        ZM[q] = make_uint4(0u, 0u, 0u, 0u);
+                        ZP[q] = ZM[q];
+                        if (DIMS == 3) {
+                            ZM[q] = zm16[i * nv + v];
+                            ZP[q] = zp16[i * nv + v];
+                        }
+                        if (p == 0) {
+                            const uint32_t prev = row32[(v == 0u ? nv - 1u : v - 1u) * 4u + 3u];
+                            XS[q] = make_uint4(__funnelshift_l(prev, oc.x, 8),
+                                               __funnelshift_l(oc.x, oc.y, 8),
+                                               __funnelshift_l(oc.y, oc.z, 8),
+                                               __funnelshift_l(oc.z, oc.w, 8));
+                        } else {
+                            const uint32_t next = row32[(v + 1u == nv ? 0u : v + 1u) * 4u];
+                            XS[q] = make_uint4(__funnelshift_r(oc.x, oc.y, 8),
+                                               __funnelshift_r(oc.y, oc.z, 8),
+                                               __funnelshift_r(oc.z, oc.w, 8),
+                                               __funnelshift_r(oc.w, next, 8));
+                        }
+                        S[q] = own_s[i * nv + v];
+                        rowg[q] = (z * (uint32_t)a.L + y) * nv + v;
+                        g0[q] = rowg[q] * 4u;
+                    }
+                    int e_vec = 0;
+                    update_vec_pair<DIMS, MEASURE>(S, X, XS, YM, YP, ZM, ZP, g0, a, e_vec, m_neg);
+                    own_g[rowg[0]] = S[0];
+                    own_g[rowg[1]] = S[1];
+                    e_acc += e_vec;
+                    n_vec += 2;
+                }
+            }
+        }
+        for (uint32_t i = i0; i < R; ++i) {
             const uint32_t y = y0 + i;
             const int p = (a.c + (int)y + (int)z) & 1;
             const uint32_t* row32 = reinterpret_cast<const uint32_t*>(oth + (i + 1u) * W);
