@@ -651,16 +651,12 @@ __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uin
     if (m == 0u) {
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
+            if (!((need >> (16 * half)) & 0xFFFFu)) continue;
             Philox4 u[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int gi = 4 * half + i;
-                if ((need >> (4 * gi)) & 0xFu)
-                    u[i] = philox4x32_10(g0 + (uint32_t)gi, a.t, c2, kTagSweep,
-                                         a.key0, a.key1);
-                else
-                    u[i] = Philox4{0u, 0u, 0u, 0u};
-            }
+            for (int i = 0; i < 4; ++i)
+                u[i] = philox4x32_10(g0 + (uint32_t)(4 * half + i), a.t, c2, kTagSweep, a.key0,
+                                     a.key1);
 #pragma unroll
             for (int i = 0; i < 4; ++i) acc |= group_accept<DIMS>(k, u[i], 4 * half + i, a);
         }
