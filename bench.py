@@ -31,8 +31,9 @@ offset by 16 * rank), no collective on the data path; scaling "weak".
 --rule heatbath runs the same workload with the heat-bath update rule (every
 site draws; flip iff u < floor(2^32 / (1 + exp(beta dE)))) instead of the
 Metropolis rule, in the engine and in the oracle arms alike.  --rule demon
-runs Creutz's deterministic demon dynamics (int8 layout only): cold spins and
-demons (qmax 3) drawn at each lattice's beta; no draws, 5 bytes per update.
+runs Creutz's deterministic demon dynamics: cold spins and demons (qmax 3)
+drawn at each lattice's beta; no draws; 5 bytes per update in int8, 7 bits
+in the bit-packed layout.
 """
 from __future__ import annotations
 
@@ -56,6 +57,7 @@ N_BETA = 16
 BASE_SEED = 20031109
 BYTES_PER_UPDATE_INT8 = 3  # per colour pass: read own N/2, read other N/2, write own N/2
 BYTES_PER_UPDATE_DEMON = 5  # and read + write the own colour's demons (1 byte per site)
+BYTES_PER_UPDATE_DEMON_PACKED = 7 / 8  # bits: own, other, 2 demon planes read; own, 2 written
 DEMON_QMAX = 3
 
 
@@ -367,8 +369,7 @@ def run_gpu(args, world, rank, local):
     layouts = [("int8", engine.INT8), ("bitpack", engine.BITPACK)]
     if args.layout != "both":
         layouts = [x for x in layouts if x[0] == args.layout]
-    if args.rule == "demon":  # the demon dynamics runs on the int8 layout
-        layouts = [("int8", engine.INT8)]
+
     stream = torch.cuda.current_stream()
     int8_kernel = {"auto": engine.KERNEL_AUTO, "strip": engine.KERNEL_STRIP,
                    "tma": engine.KERNEL_TMA}[args.int8_kernel]
@@ -381,10 +382,13 @@ def run_gpu(args, world, rank, local):
 
     if args.rule == "demon":
         from paper_cs_0312006_gb300 import workloads
-        for j, lat in enumerate(sets["int8"]):
-            lat.set_demons(workloads.demon_field(n_sites, DEMON_QMAX, betas[j],
-                                                 BASE_SEED + 16 * rank + j), qmax=DEMON_QMAX)
-            lat.set_rule(engine.RULE_DEMON)
+        fields = [workloads.demon_field(n_sites, DEMON_QMAX, b, BASE_SEED + 16 * rank + j)
+                  for j, b in enumerate(betas)]
+        for lats in sets.values():
+            for j, lat in enumerate(lats):
+                lat.set_demons(fields[j], qmax=DEMON_QMAX)
+                lat.set_rule(engine.RULE_DEMON)
+        del fields
     int8_ran = sets["int8"][0].kernel() if "int8" in sets else -1
 
     def barrier():
@@ -474,6 +478,16 @@ def run_gpu(args, world, rank, local):
                                "frac": achieved / peak_hbm,
                                "traffic": measured_traffic(args.workload, "int8",
                                                            updates_per_pass, args.rule),
+                               "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
+                               "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+        elif args.rule == "demon":  # bit-packed demons: 7 bits per update, no draws
+            bytes_per_pass = BYTES_PER_UPDATE_DEMON_PACKED * updates_per_pass
+            achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
+            rooflines[name] = {"kernel": "pass_demon_packed<2,measure>", "bound": "hbm",
+                               "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                               "frac": achieved / peak_hbm,
+                               "traffic": measured_traffic(args.workload, "demon_packed",
+                                                           updates_per_pass),
                                "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
                                "peak_source": f"{peak_kind} hbm_gbs (copy)"}
         else:

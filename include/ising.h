@@ -80,7 +80,7 @@ enum {
 enum {
     ISING_RULE_METROPOLIS = 0,
     ISING_RULE_HEATBATH = 1,
-    ISING_RULE_DEMON = 2,    /* deterministic demon dynamics, int8 layout (ising_set_demons) */
+    ISING_RULE_DEMON = 2,    /* deterministic demon dynamics (ising_set_demons) */
     ISING_RULE_MULTIHIT = 3  /* Metropolis with several trials per visit (ising_set_hits) */
 };
 
@@ -232,11 +232,13 @@ int ising_set_rule(ising_lattice *lat, int rule);
  * ISING_EINVAL otherwise).  The rule itself is chosen by ising_set_rule. */
 int ising_set_hits(ising_lattice *lat, int hits);
 
-/* Load the demons of ISING_RULE_DEMON (int8 layout only; ISING_EINVAL for the
- * bit-packed layout).  host_q: L^dims bytes in canonical order, each <= qmax;
- * or NULL, every demon = fill (0 <= fill <= qmax).  1 <= qmax <= 63.  The
- * first call allocates two device arrays the size of the spin arrays.  Syncs.
- * The spins, the sweep counter and the rule are unchanged. */
+/* Load the demons of ISING_RULE_DEMON.  host_q: L^dims bytes in canonical
+ * order, each <= qmax; or NULL, every demon = fill (0 <= fill <= qmax).
+ * int8 layout: 1 <= qmax <= 63, one byte per site.  Bit-packed layout:
+ * qmax must be 3 (two demon bit planes; ISING_EINVAL otherwise).  The first
+ * call allocates the demon arrays (the size of the spin arrays, twice that
+ * when packed).  Syncs.  The spins, the sweep counter and the rule are
+ * unchanged. */
 int ising_set_demons(ising_lattice *lat, const uint8_t *host_q, int fill, int qmax);
 
 /* The demons in canonical order (L^dims bytes of host memory), as the next

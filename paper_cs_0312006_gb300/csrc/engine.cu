@@ -242,8 +242,11 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
         a.dem = h->dem[c];
         a.qmax = h->qmax;
         a.rot = (uint32_t)h->dem_rot;
-        ISING_CHECK(ising::demon_pass(a, h->dims, h->half_sites, slot != nullptr, *h->dp,
-                                      h->stream));
+        if (h->layout == ISING_BITPACK)
+            ISING_CHECK(ising::demon_packed_pass(a, h->dims, slot != nullptr, *h->dp, h->stream));
+        else
+            ISING_CHECK(ising::demon_pass(a, h->dims, h->half_sites, slot != nullptr, *h->dp,
+                                          h->stream));
         if (c == 1) h->dem_rot = h->dem_rot + 1 == h->rows ? 0 : h->dem_rot + 1;
         return ISING_OK;
     }
@@ -538,18 +541,27 @@ int ising_set_hits(ising_lattice* h, int hits) {
 }
 
 int ising_set_demons(ising_lattice* h, const uint8_t* host_q, int fill, int qmax) {
-    if (!h || h->layout != ISING_INT8) return ISING_EINVAL;
+    if (!h) return ISING_EINVAL;
     if (qmax < 1 || qmax > 63) return ISING_EINVAL;
+    const bool packed = h->layout == ISING_BITPACK;
+    if (packed && qmax != 3) return ISING_EINVAL;  // two demon bit planes
     if (host_q) {
         for (int64_t i = 0; i < h->sites; ++i)
             if (host_q[i] > qmax) return ISING_EINVAL;
     } else if (fill < 0 || fill > qmax) {
         return ISING_EINVAL;
     }
+    // int8: one byte per site like the spins; packed: two planes of spin words
+    const size_t dem_bytes = packed ? 2 * h->col_bytes : h->col_bytes;
     for (int c = 0; c < 2; ++c) {
         if (h->dem[c]) continue;
-        ISING_CHECK(cudaMalloc(&h->dem[c], h->col_bytes));
-        ISING_CHECK(cudaMemsetAsync(h->dem[c], 0, h->col_bytes, h->stream));
+        ISING_CHECK(cudaMalloc(&h->dem[c], dem_bytes));
+        ISING_CHECK(cudaMemsetAsync(h->dem[c], 0, dem_bytes, h->stream));
+    }
+    if (!host_q && packed && fill != 0) {
+        // a uniform fill of the planes: bits set in every valid position
+        std::vector<uint8_t> tmp((size_t)h->sites, (uint8_t)fill);
+        return ising_set_demons(h, tmp.data(), 0, qmax);
     }
     if (host_q) {
         uint8_t* tmp = nullptr;
@@ -557,11 +569,17 @@ int ising_set_demons(ising_lattice* h, const uint8_t* host_q, int fill, int qmax
         cudaError_t e = cudaMemcpyAsync(tmp, host_q, (size_t)h->sites, cudaMemcpyHostToDevice,
                                         h->stream);
         if (e == cudaSuccess)
-            e = ising::demon_import(static_cast<uint8_t*>(h->dem[0]),
-                                    static_cast<uint8_t*>(h->dem[1]), tmp, h->L, h->dims,
-                                    h->sites, *h->dp, h->stream);
+            e = packed ? ising::demon_packed_import(static_cast<uint32_t*>(h->dem[0]),
+                                                    static_cast<uint32_t*>(h->dem[1]), tmp, h->L,
+                                                    h->dims, h->rows, *h->dp, h->stream)
+                       : ising::demon_import(static_cast<uint8_t*>(h->dem[0]),
+                                             static_cast<uint8_t*>(h->dem[1]), tmp, h->L,
+                                             h->dims, h->sites, *h->dp, h->stream);
         cudaFreeAsync(tmp, h->stream);
         if (e != cudaSuccess) return cuda_fail(e);
+    } else if (packed) {
+        for (int c = 0; c < 2; ++c)  // fill == 0 here
+            ISING_CHECK(cudaMemsetAsync(h->dem[c], 0, dem_bytes, h->stream));
     } else {
         for (int c = 0; c < 2; ++c)
             ISING_CHECK(cudaMemsetAsync(h->dem[c], fill, (size_t)h->half_sites, h->stream));
@@ -576,10 +594,15 @@ int ising_get_demons(ising_lattice* h, uint8_t* host_out) {
     if (!h || !host_out || !h->dem[0]) return ISING_EINVAL;
     uint8_t* tmp = nullptr;
     ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
-    cudaError_t e = ising::demon_export(static_cast<const uint8_t*>(h->dem[0]),
-                                        static_cast<const uint8_t*>(h->dem[1]), tmp, h->L,
-                                        h->dims, h->sites, h->rows, h->dem_rot, *h->dp,
-                                        h->stream);
+    cudaError_t e =
+        h->layout == ISING_BITPACK
+            ? ising::demon_packed_export(static_cast<const uint32_t*>(h->dem[0]),
+                                         static_cast<const uint32_t*>(h->dem[1]), tmp, h->L,
+                                         h->dims, h->sites, h->rows, h->dem_rot, *h->dp,
+                                         h->stream)
+            : ising::demon_export(static_cast<const uint8_t*>(h->dem[0]),
+                                  static_cast<const uint8_t*>(h->dem[1]), tmp, h->L, h->dims,
+                                  h->sites, h->rows, h->dem_rot, *h->dp, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_out, tmp, (size_t)h->sites, cudaMemcpyDeviceToHost, h->stream);
     cudaFreeAsync(tmp, h->stream);
@@ -599,7 +622,8 @@ int ising_get_info(const ising_lattice* h, ising_info_t* out) {
     out->seed = h->seed;
     out->sweeps_done = h->t;
     out->sites = (uint64_t)h->sites;
-    out->device_bytes = (uint64_t)((h->dem[0] ? 4 : 2) * h->col_bytes);
+    out->device_bytes = (uint64_t)(
+        (h->dem[0] ? (h->layout == ISING_BITPACK ? 6 : 4) : 2) * h->col_bytes);
     out->pending_records = h->n_rec;
     return ISING_OK;
 }

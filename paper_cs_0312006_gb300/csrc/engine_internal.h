@@ -97,6 +97,14 @@ cudaError_t demon_export(const uint8_t* d0, const uint8_t* d1, uint8_t* out, int
                          cudaStream_t st);
 cudaError_t demon_import(uint8_t* d0, uint8_t* d1, const uint8_t* in, int L, int dims,
                          int64_t sites, const DeviceProps& dp, cudaStream_t st);
+// bit-packed layout, qmax = 3: two demon planes per colour (plane 1 after plane 0)
+cudaError_t demon_packed_pass(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
+                              cudaStream_t st);
+cudaError_t demon_packed_import(uint32_t* d0, uint32_t* d1, const uint8_t* in, int L, int dims,
+                                int64_t rows, const DeviceProps& dp, cudaStream_t st);
+cudaError_t demon_packed_export(const uint32_t* d0, const uint32_t* d1, uint8_t* out, int L,
+                                int dims, int64_t sites, int64_t rows, int64_t rot,
+                                const DeviceProps& dp, cudaStream_t st);
 
 // bit-packed layout (sweep_bitpack.cu)
 cudaError_t packed_query_occupancy(DeviceProps& dp);

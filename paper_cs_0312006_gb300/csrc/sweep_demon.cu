@@ -20,6 +20,13 @@
 // bytes): D = 2d per byte as in the Metropolis pass; v = q + d per byte; the
 // flip condition dims <= v <= dims + qmax is bit 7 of v + (0x80 - dims) and
 // not bit 7 of v + (0x80 - dims - qmax - 1); the new demon is v - dims.
+//
+// Bit-packed layout (multispin coding, as Creutz's own code): qmax = 3, the
+// demons held as two bit planes (q = q0 + 2 q1) laid out like the spin words;
+// d comes as three bit planes from the bit-sliced neighbour count, v = q + d
+// by a bit-sliced adder, and the range test and v - dims are fixed logic on
+// the bits of v.  Per site update a pass moves 7 bits: own spin, other
+// colour's spin and two demon bits read, own spin and two demon bits written.
 #include <cstdint>
 
 #include "engine_internal.h"
@@ -272,6 +279,136 @@ __global__ void import_demons_kernel(uint8_t* d0, uint8_t* d1, const uint8_t* in
     }
 }
 
+// Bit-packed demon pass: one 32-site word per item (the neighbour words as in
+// packed_word of pass_bodies.cuh).  a.dem is the own colour's two demon
+// planes, plane 1 at a word offset of rows * nq.
+template <int DIMS, bool MEASURE>
+__global__ void __launch_bounds__(256) pass_demon_packed(PassArgs a) {
+    const uint32_t W = (uint32_t)a.W, L = (uint32_t)a.L, rows = (uint32_t)a.rows;
+    const uint32_t nq = (W + 31u) >> 5;
+    const uint32_t items = rows * nq;
+    uint32_t* own = static_cast<uint32_t*>(a.own);
+    const uint32_t* other = static_cast<const uint32_t*>(a.other);
+    uint32_t* Q0 = static_cast<uint32_t*>(a.dem);
+    uint32_t* Q1 = Q0 + items;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    int e_acc = 0, m_acc = 0;
+    for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < items; item += stride) {
+        const uint32_t r = item / nq, q = item - r * nq;
+        uint32_t y = r, z = 0u;
+        if (DIMS == 3) {
+            z = r / L;
+            y = r - z * L;
+        }
+        const uint32_t nb = W - 32u * q < 32u ? W - 32u * q : 32u;
+        const uint32_t valid = nb == 32u ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+        const uint32_t plane = z * L, row = r * nq;
+        const uint32_t o = __ldg(other + row + q);
+        const uint32_t oym = __ldg(other + (plane + (y == 0u ? L - 1u : y - 1u)) * nq + q);
+        const uint32_t oyp = __ldg(other + (plane + (y + 1u == L ? 0u : y + 1u)) * nq + q);
+        uint32_t ozm = 0u, ozp = 0u;
+        if (DIMS == 3) {
+            ozm = __ldg(other + ((z == 0u ? L - 1u : z - 1u) * L + y) * nq + q);
+            ozp = __ldg(other + ((z + 1u == L ? 0u : z + 1u) * L + y) * nq + q);
+        }
+        const uint32_t s = own[row + q];
+        const int p = (a.c + (int)y + (int)z) & 1;
+        uint32_t sh;
+        if (p == 0) {  // bit b <- neighbour xh - 1
+            const uint32_t prev = q == 0u ? __ldg(other + row + nq - 1u) << (31u - ((W - 1u) & 31u))
+                                          : __ldg(other + row + q - 1u);
+            sh = __funnelshift_l(prev, o, 1);
+        } else {       // bit b <- neighbour xh + 1
+            if (q + 1u == nq) {
+                const uint32_t first = q == 0u ? o : __ldg(other + row);
+                const uint32_t top = 1u << (nb - 1u);
+                sh = ((o >> 1) & ~top) | ((first & 1u) ? top : 0u);
+            } else {
+                sh = __funnelshift_r(o, __ldg(other + row + q + 1u), 1);
+            }
+        }
+        const Digits d = DIMS == 2 ? digits2(s ^ o, s ^ sh, s ^ oym, s ^ oyp)
+                                   : digits3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
+        const uint32_t rd = r >= a.rot ? r - a.rot : r + rows - a.rot;  // storage row
+        const uint32_t qw = rd * nq + q;
+        const uint32_t q0 = Q0[qw], q1 = Q1[qw];
+        // v = q + d, bit-sliced
+        const uint32_t v0 = q0 ^ d.d0, c0 = q0 & d.d0;
+        const uint32_t v1 = q1 ^ d.d1 ^ c0, c1 = (q1 & d.d1) | (c0 & (q1 ^ d.d1));
+        const uint32_t v2 = d.d2 ^ c1, v3 = d.d2 & c1;
+        uint32_t flip, n0, n1;
+        if (DIMS == 2) {  // 2 <= v <= 5 (v <= 7 here: v3 = 0); q' = v - 2
+            flip = (v1 | v2) & ~(v1 & v2);
+            n0 = v0;
+            n1 = v2;
+        } else {          // 3 <= v <= 6; q' = v - 3
+            flip = (v3 | v2 | (v1 & v0)) & ~(v3 | (v2 & v1 & v0));
+            n0 = ~v0;
+            n1 = v2 & (v0 | v1);
+        }
+        flip &= valid;
+        const uint32_t snew = s ^ flip;
+        own[row + q] = snew;
+        if (flip) {
+            Q0[qw] = (q0 & ~flip) | (n0 & flip);
+            Q1[qw] = (q1 & ~flip) | (n1 & flip);
+        }
+        if (MEASURE) {
+            m_acc += 2 * __popc(snew & valid) - (int)nb;
+            if (a.c == 1) {
+                int dsum = __popc((snew ^ o) & valid) + __popc((snew ^ sh) & valid) +
+                           __popc((snew ^ oym) & valid) + __popc((snew ^ oyp) & valid);
+                if (DIMS == 3) dsum += __popc((snew ^ ozm) & valid) + __popc((snew ^ ozp) & valid);
+                e_acc += 2 * dsum - (int)nb * 2 * DIMS;
+            }
+        }
+    }
+    if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
+}
+
+// Packed demons: canonical q (0..3) <-> two planes per colour, storage row
+// of half row r = (r - rot) mod rows (rot = 0 when loading).
+__global__ void import_demons_packed(uint32_t* d0, uint32_t* d1, const uint8_t* in, int L,
+                                     int dims, int64_t rows) {
+    const int W = L / 2, nq = (W + 31) / 32;
+    const int64_t words = rows * nq;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w2 < 2 * words;
+         w2 += stride) {
+        const int c = (int)(w2 / words);
+        const int64_t w = w2 - (int64_t)c * words;
+        const int64_t r = w / nq;
+        const int q = (int)(w - r * nq);
+        const int64_t y = r % L, z = dims == 3 ? r / L : 0;
+        const int p = (int)((c + y + z) & 1);
+        const int nb = W - 32 * q < 32 ? W - 32 * q : 32;
+        uint32_t b0 = 0u, b1 = 0u;
+        for (int b = 0; b < nb; ++b) {
+            const uint8_t v = in[(int64_t)L * r + 2 * (32 * q + b) + p];
+            b0 |= (uint32_t)(v & 1u) << b;
+            b1 |= (uint32_t)((v >> 1) & 1u) << b;
+        }
+        uint32_t* dst = c == 0 ? d0 : d1;
+        dst[w] = b0;
+        dst[words + w] = b1;
+    }
+}
+
+__global__ void export_demons_packed(const uint32_t* d0, const uint32_t* d1, uint8_t* out, int L,
+                                     int dims, int64_t sites, int64_t rows, int64_t rot) {
+    const int64_t nq = (L / 2 + 31) / 32, words = rows * nq;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sites; i += stride) {
+        const int64_t x = i % L, r = i / L;
+        const int64_t y = r % L, z = dims == 3 ? r / L : 0;
+        int64_t rd = r - rot;
+        if (rd < 0) rd += rows;
+        const int64_t xh = x >> 1, w = rd * nq + (xh >> 5);
+        const uint32_t* src = ((x + y + z) & 1) == 0 ? d0 : d1;
+        out[i] = (uint8_t)(((src[w] >> (xh & 31)) & 1u) | (((src[words + w] >> (xh & 31)) & 1u) << 1));
+    }
+}
+
 unsigned grid_for(int64_t n, const DeviceProps& dp) {
     int64_t b = (n + 255) / 256;
     const int64_t cap = (int64_t)dp.sm_count * 16;
@@ -324,6 +461,42 @@ cudaError_t demon_pass(const PassArgs& a, int dims, int64_t half_sites, bool mea
                        : launch_demon_t<2, false>(a, half_sites, dp, st);
     return measure ? launch_demon_t<3, true>(a, half_sites, dp, st)
                    : launch_demon_t<3, false>(a, half_sites, dp, st);
+}
+
+cudaError_t demon_packed_pass(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
+                              cudaStream_t st) {
+    const int64_t items = a.rows * (int64_t)((a.W + 31) >> 5);
+    int64_t blocks = (items + 255) / 256;
+    const int64_t cap = (int64_t)dp.sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (dims == 2) {
+        if (measure)
+            pass_demon_packed<2, true><<<(unsigned)blocks, 256, 0, st>>>(a);
+        else
+            pass_demon_packed<2, false><<<(unsigned)blocks, 256, 0, st>>>(a);
+    } else {
+        if (measure)
+            pass_demon_packed<3, true><<<(unsigned)blocks, 256, 0, st>>>(a);
+        else
+            pass_demon_packed<3, false><<<(unsigned)blocks, 256, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t demon_packed_import(uint32_t* d0, uint32_t* d1, const uint8_t* in, int L, int dims,
+                                int64_t rows, const DeviceProps& dp, cudaStream_t st) {
+    import_demons_packed<<<grid_for(2 * rows * ((L / 2 + 31) / 32), dp), 256, 0, st>>>(
+        d0, d1, in, L, dims, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t demon_packed_export(const uint32_t* d0, const uint32_t* d1, uint8_t* out, int L,
+                                int dims, int64_t sites, int64_t rows, int64_t rot,
+                                const DeviceProps& dp, cudaStream_t st) {
+    export_demons_packed<<<grid_for(sites, dp), 256, 0, st>>>(d0, d1, out, L, dims, sites, rows,
+                                                              rot);
+    return cudaGetLastError();
 }
 
 cudaError_t demon_export(const uint8_t* d0, const uint8_t* d1, uint8_t* out, int L, int dims,

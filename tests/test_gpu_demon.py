@@ -2,8 +2,9 @@
 
 Creutz's deterministic checkerboard dynamics (Sec. 2.2 cites it): no draws,
 so the spins, the demons and the E/M records after every sweep are fixed by
-the initial spins and demons alone.  Covered: the strip kernel (L/2 % 16 == 0)
-and the per-site kernel (any even L) in 2D and 3D, runs long enough for the
+the initial spins and demons alone.  Covered: the int8 strip kernel
+(L/2 % 16 == 0), the int8 per-site kernel (any even L) and the bit-packed
+kernel (qmax 3, two demon bit planes; padded rows) in 2D and 3D, runs long enough for the
 demons to go all the way round (their storage offset wraps), calls split
 into chunks, a switch from Metropolis to demon dynamics mid-run, the batched
 form (demon lattices take the per-lattice path), the refusals, and the full-
@@ -40,8 +41,8 @@ def random_state(dims, L, qmax, seed, hot=True):
     return s, q
 
 
-def gpu_demon(eng, dims, L, s, q, qmax, chunks, every=1):
-    lat = eng.Lattice(dims, L, 0.4, 1, layout=INT8)
+def gpu_demon(eng, dims, L, s, q, qmax, chunks, every=1, layout=INT8):
+    lat = eng.Lattice(dims, L, 0.4, 1, layout=layout)
     lat.set_spins(s, 0)
     lat.set_demons(q, qmax=qmax)
     lat.set_rule(RULE_DEMON)
@@ -74,6 +75,9 @@ def test_demon_2d(eng, L, qmax):
     assert_same(got, want, f"2D L={L} qmax={qmax}")
     got = gpu_demon(eng, 2, L, s, q, qmax, [1] * 3 + [n - 3])
     assert_same(got, want, f"2D L={L} qmax={qmax} chunked")
+    if qmax == 3:
+        got = gpu_demon(eng, 2, L, s, q, qmax, [2, n - 2], layout=BITPACK)
+        assert_same(got, want, f"2D L={L} bit-packed")
 
 
 @pytest.mark.parametrize("L", [2, 4, 6, 32, 34, 64])
@@ -84,6 +88,10 @@ def test_demon_3d(eng, L):
     want = oracle.run_demon(3, L, s, q, qmax, n, measure_every=2)
     got = gpu_demon(eng, 3, L, s, q, qmax, [n], every=2)
     assert_same(got, want, f"3D L={L}")
+    s, q = random_state(3, L, 3, 11 * L)
+    want = oracle.run_demon(3, L, s, q, 3, n, measure_every=2)
+    got = gpu_demon(eng, 3, L, s, q, 3, [n], every=2, layout=BITPACK)
+    assert_same(got, want, f"3D L={L} bit-packed")
 
 
 def test_demon_cold_start_and_uniform_demons(eng):
@@ -136,7 +144,9 @@ def test_demon_refusals(eng):
     lat.close()
     packed = eng.Lattice(2, 32, 0.4, 1, layout=BITPACK)
     with pytest.raises(eng.IsingError):
-        packed.set_demons(None, fill=0, qmax=3)
+        packed.set_demons(None, fill=0, qmax=7)  # the packed layout holds qmax = 3
+    packed.set_demons(None, fill=2, qmax=3)
+    assert np.all(packed.get_demons() == 2)
     packed.close()
 
 
@@ -177,7 +187,8 @@ def test_demon_L8192(eng):
     s = np.ones(L * L, dtype=np.int8)
     n = 12
     want = oracle.run_demon(2, L, s, q, qmax, n)
-    got = gpu_demon(eng, 2, L, s, q, qmax, [n])
-    assert_same(got, want, "2D L=8192 demons")
     total = oracle.energy(2, L, s) + 4 * int(q.astype(np.int64).sum())
-    assert int(got[2][-1]) + 4 * int(got[1].astype(np.int64).sum()) == total
+    for layout in (INT8, BITPACK):
+        got = gpu_demon(eng, 2, L, s, q, qmax, [n], layout=layout)
+        assert_same(got, want, f"2D L=8192 demons layout={layout}")
+        assert int(got[2][-1]) + 4 * int(got[1].astype(np.int64).sum()) == total
