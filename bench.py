@@ -483,7 +483,9 @@ def run_gpu(args, world, rank, local):
         elif args.rule == "demon":  # bit-packed demons: 7 bits per update, no draws
             bytes_per_pass = BYTES_PER_UPDATE_DEMON_PACKED * updates_per_pass
             achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
-            rooflines[name] = {"kernel": "pass_demon_packed<2,measure>", "bound": "hbm",
+            kname = ("pass_demon_packed4<2,measure>" if (L // 2) % 128 == 0 else
+                     "pass_demon_packed<2,measure>")
+            rooflines[name] = {"kernel": kname, "bound": "hbm",
                                "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                                "frac": achieved / peak_hbm,
                                "traffic": measured_traffic(args.workload, "demon_packed",

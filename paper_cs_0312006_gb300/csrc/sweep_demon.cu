@@ -279,6 +279,123 @@ __global__ void import_demons_kernel(uint8_t* d0, uint8_t* d1, const uint8_t* in
     }
 }
 
+// The demon rule on one packed word: spins s, neighbour words, demon planes
+// q0 / q1 (updated in place); returns the flip mask (within `valid`).
+template <int DIMS>
+__device__ __forceinline__ uint32_t demon_packed_bits(uint32_t s, uint32_t o, uint32_t sh,
+                                                      uint32_t oym, uint32_t oyp, uint32_t ozm,
+                                                      uint32_t ozp, uint32_t valid, uint32_t& q0,
+                                                      uint32_t& q1) {
+    const Digits d = DIMS == 2 ? digits2(s ^ o, s ^ sh, s ^ oym, s ^ oyp)
+                               : digits3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
+    // v = q + d, bit-sliced
+    const uint32_t v0 = q0 ^ d.d0, c0 = q0 & d.d0;
+    const uint32_t v1 = q1 ^ d.d1 ^ c0, c1 = (q1 & d.d1) | (c0 & (q1 ^ d.d1));
+    const uint32_t v2 = d.d2 ^ c1, v3 = d.d2 & c1;
+    uint32_t flip, n0, n1;
+    if (DIMS == 2) {  // 2 <= v <= 5 (v <= 7 here: v3 = 0); q' = v - 2
+        flip = (v1 | v2) & ~(v1 & v2);
+        n0 = v0;
+        n1 = v2;
+    } else {          // 3 <= v <= 6; q' = v - 3
+        flip = (v3 | v2 | (v1 & v0)) & ~(v3 | (v2 & v1 & v0));
+        n0 = ~v0;
+        n1 = v2 & (v0 | v1);
+    }
+    flip &= valid;
+    q0 = (q0 & ~flip) | (n0 & flip);
+    q1 = (q1 & ~flip) | (n1 & flip);
+    return flip;
+}
+
+template <int DIMS>
+__device__ __forceinline__ void demon_packed_measure(uint32_t snew, uint32_t o, uint32_t sh,
+                                                     uint32_t oym, uint32_t oyp, uint32_t ozm,
+                                                     uint32_t ozp, uint32_t valid, uint32_t nb,
+                                                     int c, int& e_acc, int& m_acc) {
+    m_acc += 2 * __popc(snew & valid) - (int)nb;
+    if (c == 1) {
+        int dsum = __popc((snew ^ o) & valid) + __popc((snew ^ sh) & valid) +
+                   __popc((snew ^ oym) & valid) + __popc((snew ^ oyp) & valid);
+        if (DIMS == 3) dsum += __popc((snew ^ ozm) & valid) + __popc((snew ^ ozp) & valid);
+        e_acc += 2 * dsum - (int)nb * 2 * DIMS;
+    }
+}
+
+// Rows of whole 16-byte groups (W % 128 == 0): four consecutive words per
+// item, every stream read and written as 16-byte vectors.
+template <int DIMS, bool MEASURE>
+__global__ void __launch_bounds__(256) pass_demon_packed4(PassArgs a) {
+    const uint32_t W = (uint32_t)a.W, L = (uint32_t)a.L, rows = (uint32_t)a.rows;
+    const uint32_t nq = W >> 5, n4 = nq >> 2;
+    const uint32_t items = rows * n4, words = rows * nq;
+    uint4* own = static_cast<uint4*>(a.own);
+    const uint4* other = static_cast<const uint4*>(a.other);
+    const uint32_t* other_w = static_cast<const uint32_t*>(a.other);
+    uint4* Q0 = static_cast<uint4*>(a.dem);
+    uint4* Q1 = reinterpret_cast<uint4*>(static_cast<uint32_t*>(a.dem) + words);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    int e_acc = 0, m_acc = 0;
+    for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < items; item += stride) {
+        const uint32_t r = item / n4, g = item - r * n4;
+        uint32_t y = r, z = 0u;
+        if (DIMS == 3) {
+            z = r / L;
+            y = r - z * L;
+        }
+        const uint32_t plane = z * L;
+        const uint4 o = __ldg(other + r * n4 + g);
+        const uint4 oym = __ldg(other + (plane + (y == 0u ? L - 1u : y - 1u)) * n4 + g);
+        const uint4 oyp = __ldg(other + (plane + (y + 1u == L ? 0u : y + 1u)) * n4 + g);
+        uint4 ozm = make_uint4(0u, 0u, 0u, 0u), ozp = ozm;
+        if (DIMS == 3) {
+            ozm = __ldg(other + ((z == 0u ? L - 1u : z - 1u) * L + y) * n4 + g);
+            ozp = __ldg(other + ((z + 1u == L ? 0u : z + 1u) * L + y) * n4 + g);
+        }
+        const uint4 sv = own[r * n4 + g];
+        const uint32_t rd = r >= a.rot ? r - a.rot : r + rows - a.rot;  // storage row
+        uint4 qa = Q0[rd * n4 + g], qb = Q1[rd * n4 + g];
+        const int p = (a.c + (int)y + (int)z) & 1;
+        const uint32_t row = r * nq;
+        uint4 sh;
+        if (p == 0) {  // bit b <- neighbour xh - 1; word 0 takes the previous word's bit 31
+            const uint32_t prev = g == 0u ? __ldg(other_w + row + nq - 1u)
+                                          : __ldg(other_w + row + 4u * g - 1u);
+            sh = make_uint4(__funnelshift_l(prev, o.x, 1), __funnelshift_l(o.x, o.y, 1),
+                            __funnelshift_l(o.y, o.z, 1), __funnelshift_l(o.z, o.w, 1));
+        } else {       // bit b <- neighbour xh + 1
+            const uint32_t next = g + 1u == n4 ? __ldg(other_w + row) : __ldg(other_w + row + 4u * g + 4u);
+            sh = make_uint4(__funnelshift_r(o.x, o.y, 1), __funnelshift_r(o.y, o.z, 1),
+                            __funnelshift_r(o.z, o.w, 1), __funnelshift_r(o.w, next, 1));
+        }
+        const uint32_t fx = demon_packed_bits<DIMS>(sv.x, o.x, sh.x, oym.x, oyp.x, ozm.x, ozp.x,
+                                                    0xFFFFFFFFu, qa.x, qb.x);
+        const uint32_t fy = demon_packed_bits<DIMS>(sv.y, o.y, sh.y, oym.y, oyp.y, ozm.y, ozp.y,
+                                                    0xFFFFFFFFu, qa.y, qb.y);
+        const uint32_t fz = demon_packed_bits<DIMS>(sv.z, o.z, sh.z, oym.z, oyp.z, ozm.z, ozp.z,
+                                                    0xFFFFFFFFu, qa.z, qb.z);
+        const uint32_t fw = demon_packed_bits<DIMS>(sv.w, o.w, sh.w, oym.w, oyp.w, ozm.w, ozp.w,
+                                                    0xFFFFFFFFu, qa.w, qb.w);
+        const uint4 sn = make_uint4(sv.x ^ fx, sv.y ^ fy, sv.z ^ fz, sv.w ^ fw);
+        own[r * n4 + g] = sn;
+        if (fx | fy | fz | fw) {
+            Q0[rd * n4 + g] = qa;
+            Q1[rd * n4 + g] = qb;
+        }
+        if (MEASURE) {
+            demon_packed_measure<DIMS>(sn.x, o.x, sh.x, oym.x, oyp.x, ozm.x, ozp.x, 0xFFFFFFFFu,
+                                       32u, a.c, e_acc, m_acc);
+            demon_packed_measure<DIMS>(sn.y, o.y, sh.y, oym.y, oyp.y, ozm.y, ozp.y, 0xFFFFFFFFu,
+                                       32u, a.c, e_acc, m_acc);
+            demon_packed_measure<DIMS>(sn.z, o.z, sh.z, oym.z, oyp.z, ozm.z, ozp.z, 0xFFFFFFFFu,
+                                       32u, a.c, e_acc, m_acc);
+            demon_packed_measure<DIMS>(sn.w, o.w, sh.w, oym.w, oyp.w, ozm.w, ozp.w, 0xFFFFFFFFu,
+                                       32u, a.c, e_acc, m_acc);
+        }
+    }
+    if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
+}
+
 // Bit-packed demon pass: one 32-site word per item (the neighbour words as in
 // packed_word of pass_bodies.cuh).  a.dem is the own colour's two demon
 // planes, plane 1 at a word offset of rows * nq.
@@ -465,11 +582,26 @@ cudaError_t demon_pass(const PassArgs& a, int dims, int64_t half_sites, bool mea
 
 cudaError_t demon_packed_pass(const PassArgs& a, int dims, bool measure, const DeviceProps& dp,
                               cudaStream_t st) {
-    const int64_t items = a.rows * (int64_t)((a.W + 31) >> 5);
+    const bool vec = a.W % 128 == 0;
+    const int64_t items = a.rows * (int64_t)((a.W + 31) >> 5) / (vec ? 4 : 1);
     int64_t blocks = (items + 255) / 256;
     const int64_t cap = (int64_t)dp.sm_count * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    if (vec) {
+        if (dims == 2) {
+            if (measure)
+                pass_demon_packed4<2, true><<<(unsigned)blocks, 256, 0, st>>>(a);
+            else
+                pass_demon_packed4<2, false><<<(unsigned)blocks, 256, 0, st>>>(a);
+        } else {
+            if (measure)
+                pass_demon_packed4<3, true><<<(unsigned)blocks, 256, 0, st>>>(a);
+            else
+                pass_demon_packed4<3, false><<<(unsigned)blocks, 256, 0, st>>>(a);
+        }
+        return cudaGetLastError();
+    }
     if (dims == 2) {
         if (measure)
             pass_demon_packed<2, true><<<(unsigned)blocks, 256, 0, st>>>(a);

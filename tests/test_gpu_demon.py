@@ -192,3 +192,13 @@ def test_demon_L8192(eng):
         got = gpu_demon(eng, 2, L, s, q, qmax, [n], layout=layout)
         assert_same(got, want, f"2D L=8192 demons layout={layout}")
         assert int(got[2][-1]) + 4 * int(got[1].astype(np.int64).sum()) == total
+
+
+@pytest.mark.parametrize("dims,L,n", [(2, 256, 261), (2, 512, 20), (3, 256, 3)])
+def test_demon_packed_vector_rows(eng, dims, L, n):
+    """Rows of whole 16-byte groups (L % 256 == 0) take the four-word path of
+    the bit-packed demon pass; 2D L = 256 runs long enough to wrap the demons."""
+    s, q = random_state(dims, L, 3, 3 * L + dims)
+    want = oracle.run_demon(dims, L, s, q, 3, n, measure_every=1)
+    got = gpu_demon(eng, dims, L, s, q, 3, [1, n - 1], layout=BITPACK)
+    assert_same(got, want, f"{dims}D L={L} bit-packed vectors")
