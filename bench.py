@@ -609,6 +609,8 @@ def run_batched_workload(args):
     else:
         tuned = autotune.tune(specs, use_cache=not args.retune)
     opts, layout = tuned["opts"], tuned["layout"]
+    if args.batch_layout:
+        layout = args.batch_layout
     batched.run_batched(batched.scaled(specs[:64], 2), opts, 1, layout)  # warm-up
     res = batched.compare_forms(specs, opts, layout)
     line = {"metric": "site updates/s", "value": res["batched_updates_per_s"],
@@ -858,6 +860,8 @@ def main():
                          "job stream")
     ap.add_argument("--batch-lattices", type=int, default=2048)
     ap.add_argument("--batch-sweeps", type=int, default=500)
+    ap.add_argument("--batch-layout", choices=["auto", "int8", "bitpack", "mixed"], default=None,
+                    help="batched: override the tuned layout policy")
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batched: fixed launch shape")
     ap.add_argument("--big-L", type=int, default=65536,

@@ -16,17 +16,26 @@ from . import engine
 from .workloads import AUTO, INT8, LatticeSpec
 
 
+def layout_for(sp, layout_policy: str) -> int:
+    """``layout_policy``: "auto" (the engine's choice, bit-packed), "int8",
+    "bitpack", or "mixed": bit-packed where a half row fills whole words and
+    starts on a Philox group (L/2 >= 32 and L % 8 == 0), int8 otherwise
+    (short or unaligned rows waste bits and draw nine groups per word)."""
+    if layout_policy == "int8":
+        return INT8
+    if layout_policy == "bitpack":
+        return engine.BITPACK
+    if layout_policy == "mixed":
+        return engine.BITPACK if sp.L // 2 >= 32 and sp.L % 8 == 0 else INT8
+    return AUTO
+
+
 def make_lattices(specs, layout_policy: str = "auto", stream=None):
-    """Create one handle per spec (hot start).  ``layout_policy``: "auto"
-    (the engine's choice, bit-packed), "int8" or "bitpack"."""
+    """Create one handle per spec (hot start) in the layout the policy gives
+    (see layout_for)."""
     lats = []
     for sp in specs:
-        if layout_policy == "int8":
-            lay = INT8
-        elif layout_policy == "bitpack":
-            lay = engine.BITPACK
-        else:
-            lay = AUTO
+        lay = layout_for(sp, layout_policy)
         lats.append(engine.Lattice(sp.dims, sp.L, sp.beta, sp.seed, layout=lay, start=sp.start,
                                    stream=stream))
     return lats
