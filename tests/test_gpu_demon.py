@@ -202,3 +202,16 @@ def test_demon_packed_vector_rows(eng, dims, L, n):
     want = oracle.run_demon(dims, L, s, q, 3, n, measure_every=1)
     got = gpu_demon(eng, dims, L, s, q, 3, [1, n - 1], layout=BITPACK)
     assert_same(got, want, f"{dims}D L={L} bit-packed vectors")
+
+
+def test_demon_L32768_both_layouts(eng):
+    """The out-of-L2 demon workload's size (2D L = 32768, 2^30 sites): two
+    sweeps in full in both layouts, from cold spins and demons at beta 0.30."""
+    from paper_cs_0312006_gb300 import workloads
+    L, qmax, n = 32768, 3, 2
+    q = workloads.demon_field(L * L, qmax, 0.30, 20031109)
+    s = np.ones(L * L, dtype=np.int8)
+    want = oracle.run_demon(2, L, s, q, qmax, n)
+    for layout in (INT8, BITPACK):
+        got = gpu_demon(eng, 2, L, s, q, qmax, [n], layout=layout)
+        assert_same(got, want, f"2D L=32768 demons layout={layout}")

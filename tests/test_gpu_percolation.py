@@ -121,3 +121,19 @@ def test_refusals(perc):
     m.close()
     with pytest.raises(IsingError):
         perc.batch(3, 65, 0.3, [1])
+
+
+def test_bench_configurations(perc):
+    """The bench's two percolation workloads in the launch configuration it
+    times: the L = 16384 medium at P = 0.6 in full (porosity field, cluster,
+    size, spanning and all 34,572 passes), and its batch of 8192 media of
+    L = 128 at 0.592746 (seeds 20031109 + k) checked medium by medium on a
+    sample."""
+    L, P, seed = 16384, 0.6, 20031109
+    check_medium(perc, 2, L, seed, P, sources=(FACE,))
+    n, Lb, Pb = 8192, 128, 0.592746
+    seeds = [seed + k for k in range(n)]
+    res = perc.batch(2, Lb, Pb, seeds, FACE, 0)
+    for k in range(0, n, 257):
+        _, size, spans, steps = oracle.perc_invade(2, Lb, oracle.perc_pores(2, Lb, seeds[k], Pb))
+        assert (res[k].size, bool(res[k].spans), res[k].steps) == (size, spans, steps), k
