@@ -204,8 +204,11 @@ int ising_philox_fill(uint32_t *dev_out, uint32_t n, uint32_t c1, uint32_t c2, u
 /* Test hook for the bounded waits: while `on` is nonzero, every staged (TMA)
  * pass expects more bytes on its first tile than are ever copied, so its wait
  * runs out after about a second, the kernel returns early and the next
- * ising_synchronize / ising_observables reports ISING_ETIMEOUT.  The spins of
- * such a pass are not defined.  Off by default. */
+ * ising_synchronize / ising_observables reports ISING_ETIMEOUT; and every
+ * persistent percolation launch (perc_invade) has one CTA leave before the
+ * first grid barrier, so the others' waits run out and perc_invade returns
+ * ISING_ETIMEOUT.  The results of such a pass or invasion are not defined.
+ * Off by default. */
 int ising_test_inject_timeout(int on);
 
 /* Use this CUDA stream (a cudaStream_t, may be NULL = legacy default stream)

@@ -70,6 +70,18 @@ int perc_invade(perc_medium *m, int source, int64_t site, perc_result *out);
 int perc_get_pores(perc_medium *m, uint8_t *host_out);
 int perc_get_cluster(perc_medium *m, uint8_t *host_out);
 
+/* How perc_invade runs its passes (same results either way):
+ *   PERC_PASSES_AUTO (default): PERC_PASSES_GRAPH (measured the faster);
+ *   PERC_PASSES_GRAPH: a CUDA graph of 64 pass launches replayed until a pass
+ *       adds nothing;
+ *   PERC_PASSES_PERSISTENT: one cooperative launch (two CTAs per SM), the
+ *       passes separated by a grid barrier whose every wait is bounded (about
+ *       a second); a wait that runs out makes perc_invade return
+ *       ISING_ETIMEOUT.
+ * ISING_EINVAL for another value, or PERSISTENT where it cannot launch. */
+enum { PERC_PASSES_AUTO = 0, PERC_PASSES_GRAPH = 1, PERC_PASSES_PERSISTENT = 2 };
+int perc_set_passes(perc_medium *m, int mode);
+
 /* Use this CUDA stream (a cudaStream_t, may be NULL) for later work. */
 int perc_set_stream(perc_medium *m, void *stream);
 

@@ -208,6 +208,8 @@ int clear_records(ising_lattice* h) {
 
 std::atomic<int> g_inject_timeout{0};
 
+bool injecting_timeout() { return g_inject_timeout.load() != 0; }
+
 // Read and clear the device's bounded-wait flag (after a synchronisation).
 int check_timeout(ising_lattice* h) {
     if (*h->dp->h_err == 0) return ISING_OK;

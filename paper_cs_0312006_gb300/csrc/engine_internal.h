@@ -58,6 +58,8 @@ struct DeviceProps {
 
 // engine.cu helpers shared with batch.cu
 int cuda_fail(cudaError_t e);
+// the test hook of ising_test_inject_timeout is on
+bool injecting_timeout();
 // the threshold table of the lattice's rule, as the kernels take it (PassArgs::thr)
 void rule_thresholds(const ising_lattice* h, uint32_t out[7]);
 int device_props(const DeviceProps** out);

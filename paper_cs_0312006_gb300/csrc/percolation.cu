@@ -22,10 +22,16 @@
 // A single medium's passes touch only a band of rows: each pass records the
 // lowest and highest row of the front it writes (Band), and the next pass
 // visits the rows next to that front plus the rows of the front before it
-// (which it must clear from the buffer it overwrites).  The passes are issued
-// as a replayed CUDA graph of kPassesPerGraph launches; after each replay the
-// host reads the per-pass counts and stops at the first pass that added
-// nothing (the rest of that replay are no-ops on an empty front).
+// (which it must clear from the buffer it overwrites).  Two ways to run the
+// passes, with the same results (the graph is the default: measured faster):
+//   - one cooperative persistent launch: every CTA resident, the passes
+//     separated by a grid barrier (an arrival counter and a generation word;
+//     every wait on it bounded by %globaltimer, a CTA that gives up raises
+//     the error flag and leaves, and the others then give up at their next
+//     wait), the stop decided on the device from the pass's added count;
+//   - a replayed CUDA graph of kPassesPerGraph launches; after each replay
+//     the host reads the per-pass counts and stops at the first pass that
+//     added nothing (the rest of that replay are no-ops on an empty front).
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -157,6 +163,7 @@ struct Band {
 };
 constexpr int kBandSlots = 4;  // pass k writes slot k % 4, reads k-1 and k-2, resets k+1
 constexpr int kPassesPerGraph = 64;
+constexpr size_t kCoopBytes = 128;  // 4 counters, barrier, steps, error flag
 
 __device__ __forceinline__ void band_add(Band* b, unsigned int lo, unsigned int hi) {
     // block-wide min / max of the rows that got front bits, then one atomic each
@@ -210,16 +217,14 @@ __global__ void perc_seed_kernel(const uint32_t* pore, uint32_t* C, uint32_t* F,
     }
 }
 
-// One banded growth pass (pass index k within the graph, k % 4 picks slots).
-__global__ void __launch_bounds__(256) perc_band_kernel(const uint32_t* pore, uint32_t* C,
-                                                        const uint32_t* Fo, uint32_t* Fn,
-                                                        PercGeom g, Band* bands, int k,
-                                                        unsigned long long* added) {
+// The rows the banded pass k visits (empty when lo > hi).
+__device__ __forceinline__ void pass_rows(const Band* bands, int k, const PercGeom& g,
+                                          unsigned int& lo, unsigned int& hi) {
     const Band last = bands[(k + 3) % kBandSlots];   // rows of the front Fo
     const Band older = bands[(k + 2) % kBandSlots];  // rows of the stale front in Fn
-    if (blockIdx.x == 0 && threadIdx.x == 0) bands[(k + 1) % kBandSlots] = Band{0xFFFFFFFFu, 0u};
     const unsigned int reach = g.dims == 2 ? 1u : g.L;  // rows a front row touches
-    unsigned int lo = 0xFFFFFFFFu, hi = 0u;
+    lo = 0xFFFFFFFFu;
+    hi = 0u;
     if (last.lo <= last.hi) {
         lo = last.lo > reach ? last.lo - reach : 0u;
         hi = last.hi + reach < g.rows ? last.hi + reach : g.rows - 1u;
@@ -228,6 +233,16 @@ __global__ void __launch_bounds__(256) perc_band_kernel(const uint32_t* pore, ui
         lo = older.lo < lo ? older.lo : lo;
         hi = older.hi > hi ? older.hi : hi;
     }
+}
+
+// One banded growth pass (pass index k within the graph, k % 4 picks slots).
+__global__ void __launch_bounds__(256) perc_band_kernel(const uint32_t* pore, uint32_t* C,
+                                                        const uint32_t* Fo, uint32_t* Fn,
+                                                        PercGeom g, Band* bands, int k,
+                                                        unsigned long long* added) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) bands[(k + 1) % kBandSlots] = Band{0xFFFFFFFFu, 0u};
+    unsigned int lo, hi;
+    pass_rows(bands, k, g, lo, hi);
     const uint32_t w0 = lo <= hi ? lo * g.nq : 0u, w1 = lo <= hi ? (hi + 1u) * g.nq : 0u;
     // the grid covers the whole medium; CTAs past the band leave at once
     // (a whole CTA at a time, before any barrier)
@@ -251,6 +266,99 @@ __global__ void __launch_bounds__(256) perc_band_kernel(const uint32_t* pore, ui
     if (!__syncthreads_or(cnt != 0ull)) return;  // nothing joined in this CTA's words
     band_add(&bands[k % kBandSlots], got_lo, got_hi);
     block_sum_u64(cnt, added);
+}
+
+struct GridBar {
+    unsigned int count;  // CTAs arrived at the current barrier
+    unsigned int gen;    // barriers completed
+};
+constexpr uint64_t kBarrierLimitNs = 1000000000ull;  // give up a barrier wait after ~1 s
+
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch; false if this CTA's wait ran out.
+__device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* vgen = &gb->gen;
+        const unsigned int g0 = *vgen;  // read before arriving: the release comes after
+        __threadfence();
+        if (atomicAdd(&gb->count, 1u) == nblocks - 1u) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            const uint64_t t0 = now_ns();
+            while (*vgen == g0) {
+                if (now_ns() - t0 > kBarrierLimitNs) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// All growth passes in one cooperative launch (see the header comment).
+// cnt: four per-pass added counters (zero at launch); out_steps: passes that
+// added sites; err: raised when a barrier wait ran out.
+__global__ void __launch_bounds__(256) perc_persistent_kernel(const uint32_t* pore, uint32_t* C,
+                                                              uint32_t* F0, uint32_t* F1,
+                                                              PercGeom g, Band* bands,
+                                                              unsigned long long* cnt,
+                                                              GridBar* gb,
+                                                              unsigned long long* out_steps,
+                                                              int* err, int drop_last_block) {
+    // test hook: the last CTA leaves before the first barrier, so every other
+    // CTA's wait there runs out (nothing else ever makes a CTA leave early)
+    if (drop_last_block && blockIdx.x == gridDim.x - 1u) return;
+    unsigned long long steps = 0ull;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (int k = 0;; ++k) {
+        const uint32_t* Fo = (k & 1) ? F1 : F0;
+        uint32_t* Fn = (k & 1) ? F0 : F1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            bands[(k + 1) % kBandSlots] = Band{0xFFFFFFFFu, 0u};  // for pass k + 1
+            cnt[(k + 1) % kBandSlots] = 0ull;
+        }
+        unsigned int lo, hi;
+        pass_rows(bands, k, g, lo, hi);
+        const uint32_t w0 = lo <= hi ? lo * g.nq : 0u, w1 = lo <= hi ? (hi + 1u) * g.nq : 0u;
+        unsigned long long c = 0ull;
+        unsigned int got_lo = 0xFFFFFFFFu, got_hi = 0u;
+        for (uint32_t w = w0 + blockIdx.x * blockDim.x + threadIdx.x; w < w1; w += stride) {
+            const uint32_t add = grow_word(pore, C, Fo, g, w);
+            Fn[w] = add;
+            if (add) {
+                C[w] |= add;
+                c += (unsigned long long)__popc(add);
+                const unsigned int r = w / g.nq;
+                got_lo = r < got_lo ? r : got_lo;
+                got_hi = r > got_hi ? r : got_hi;
+            }
+        }
+        if (__syncthreads_or(c != 0ull)) {
+            band_add(&bands[k % kBandSlots], got_lo, got_hi);
+            block_sum_u64(c, &cnt[k % kBandSlots]);
+        }
+        if (!grid_barrier(gb, gridDim.x)) {
+            if (threadIdx.x == 0) *reinterpret_cast<volatile int*>(err) = 1;
+            return;
+        }
+        if (*reinterpret_cast<volatile unsigned long long*>(&cnt[k % kBandSlots]) == 0ull) break;
+        ++steps;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *out_steps = steps;
 }
 
 // out[0] = cluster size, out[1] = touches the first face, out[2] = the last.
@@ -393,6 +501,9 @@ struct perc_medium {
     unsigned long long* meas = nullptr;    // size, first face, last face
     Band* bands = nullptr;
     cudaGraphExec_t passes = nullptr;      // kPassesPerGraph banded passes
+    int mode = PERC_PASSES_AUTO;
+    int coop_grid = 0;                     // resident CTAs of the persistent kernel (0: none)
+    void* coop = nullptr;                  // counters, barrier, steps, error flag
     cudaStream_t stream = nullptr;
     int sm_count = 0;
 };
@@ -405,6 +516,7 @@ void free_medium(perc_medium* m) {
     if (m->counts) cudaFree(m->counts);
     if (m->meas) cudaFree(m->meas);
     if (m->bands) cudaFree(m->bands);
+    if (m->coop) cudaFree(m->coop);
     if (m->passes) cudaGraphExecDestroy(m->passes);
     delete m;
 }
@@ -458,6 +570,20 @@ int perc_create(perc_medium** out, int dims, int L, uint64_t seed) {
         e = cudaMalloc(reinterpret_cast<void**>(&m->counts), kPassesPerGraph * 8);
     if (e == cudaSuccess)
         e = cudaMalloc(reinterpret_cast<void**>(&m->bands), kBandSlots * sizeof(Band));
+    if (e == cudaSuccess) e = cudaMalloc(&m->coop, kCoopBytes);
+    if (e == cudaSuccess) {
+        int dev = 0, coop = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, perc_persistent_kernel,
+                                                              256, 0);
+        if (e == cudaSuccess && coop && per_sm > 0) {
+            const uint64_t need = ((uint64_t)g.rows * g.nq + 255) / 256;
+            const uint64_t resident = (uint64_t)(per_sm < 2 ? per_sm : 2) * dp->sm_count;
+            m->coop_grid = (int)(need < resident ? (need < 1 ? 1 : need) : resident);
+        }
+    }
     if (e != cudaSuccess) {
         free_medium(m);
         return cuda_fail(e);
@@ -479,6 +605,15 @@ int perc_generate(perc_medium* m, double porosity) {
     return ISING_OK;
 }
 
+int perc_set_passes(perc_medium* m, int mode) {
+    if (!m) return ISING_EINVAL;
+    if (mode != PERC_PASSES_AUTO && mode != PERC_PASSES_GRAPH && mode != PERC_PASSES_PERSISTENT)
+        return ISING_EINVAL;
+    if (mode == PERC_PASSES_PERSISTENT && m->coop_grid == 0) return ISING_EINVAL;
+    m->mode = mode;
+    return ISING_OK;
+}
+
 int perc_invade(perc_medium* m, int source, int64_t site, perc_result* out) {
     if (!m || !out) return ISING_EINVAL;
     if (source != PERC_POINT && source != PERC_FACE) return ISING_EINVAL;
@@ -489,6 +624,38 @@ int perc_invade(perc_medium* m, int source, int64_t site, perc_result* out) {
                                                   source == PERC_POINT ? (uint64_t)site : 0ull,
                                                   m->bands);
     PERC_CHECK(cudaGetLastError());
+    int64_t steps = 0;
+    // AUTO takes the graph: on GB300 it measured 6.4 us per pass at L = 16384
+    // against 8.5 us for the persistent launch (2 - 4 CTAs per SM; 12 us with one,
+    // 14 us with all that fit): the pass's own work needs the wide grid, and
+    // the barrier costs about as much as a graph node's launch
+    if (m->mode == PERC_PASSES_PERSISTENT && m->coop_grid > 0) {
+        unsigned char* cb = static_cast<unsigned char*>(m->coop);
+        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(cb);
+        GridBar* gb = reinterpret_cast<GridBar*>(cb + kBandSlots * 8);
+        unsigned long long* d_steps = reinterpret_cast<unsigned long long*>(cb + 64);
+        int* d_err = reinterpret_cast<int*>(cb + 72);
+        PERC_CHECK(cudaMemsetAsync(m->coop, 0, kCoopBytes, m->stream));
+        const uint32_t* pore = m->pore;
+        PercGeom g = m->g;
+        int drop = ising::injecting_timeout() && m->coop_grid > 1 ? 1 : 0;
+        void* args[] = {(void*)&pore, (void*)&m->C, (void*)&m->F[0], (void*)&m->F[1], (void*)&g,
+                        (void*)&m->bands, (void*)&cnt, (void*)&gb, (void*)&d_steps,
+                        (void*)&d_err, (void*)&drop};
+        PERC_CHECK(cudaLaunchCooperativeKernel((const void*)perc_persistent_kernel,
+                                               dim3((unsigned)m->coop_grid), dim3(256), args, 0,
+                                               m->stream));
+        struct {
+            unsigned long long steps;
+            int err;
+        } host_out;
+        PERC_CHECK(cudaMemcpyAsync(&host_out.steps, d_steps, 8, cudaMemcpyDeviceToHost,
+                                   m->stream));
+        PERC_CHECK(cudaMemcpyAsync(&host_out.err, d_err, 4, cudaMemcpyDeviceToHost, m->stream));
+        PERC_CHECK(cudaStreamSynchronize(m->stream));
+        if (host_out.err) return ISING_ETIMEOUT;
+        steps = (int64_t)host_out.steps;
+    } else {
     if (!m->passes) {
         // capture [zero the counts, kPassesPerGraph banded passes] once; the
         // buffers and slots it uses belong to the medium, so replays continue
@@ -514,7 +681,6 @@ int perc_invade(perc_medium* m, int source, int64_t site, perc_result* out) {
     }
     // replay until a pass adds nothing (each replay that continues added at
     // least kPassesPerGraph sites, so this ends)
-    int64_t steps = 0;
     unsigned long long host[kPassesPerGraph];
     while (true) {
         PERC_CHECK(cudaGraphLaunch(m->passes, m->stream));
@@ -525,6 +691,7 @@ int perc_invade(perc_medium* m, int source, int64_t site, perc_result* out) {
         while (k < kPassesPerGraph && host[k] != 0ull) ++k;
         steps += k;
         if (k < kPassesPerGraph) break;
+    }
     }
     PERC_CHECK(cudaMemsetAsync(m->meas, 0, 3 * 8, m->stream));
     perc_measure_kernel<<<grid, 256, 0, m->stream>>>(m->C, m->g, m->meas);

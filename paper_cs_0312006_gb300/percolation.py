@@ -12,6 +12,7 @@ import numpy as np
 from .engine import IsingError, load_library
 
 POINT, FACE = 0, 1
+PASSES_AUTO, PASSES_GRAPH, PASSES_PERSISTENT = 0, 1, 2
 
 
 class PercResult(ctypes.Structure):
@@ -36,6 +37,7 @@ def _lib():
             "perc_get_pores": ([P, P], ctypes.c_int),
             "perc_get_cluster": ([P, P], ctypes.c_int),
             "perc_set_stream": ([P, P], ctypes.c_int),
+            "perc_set_passes": ([P, ctypes.c_int], ctypes.c_int),
             "perc_destroy": ([P], None),
             "perc_batch": ([ctypes.c_int, ctypes.c_int, ctypes.c_double,
                             ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_int,
@@ -77,6 +79,10 @@ class Medium:
         _check(self._lib.perc_invade(self._h, int(source), int(site), ctypes.byref(out)),
                "perc_invade")
         return out
+
+    def set_passes(self, mode: int) -> None:
+        """PASSES_AUTO, PASSES_GRAPH or PASSES_PERSISTENT (same results)."""
+        _check(self._lib.perc_set_passes(self._h, int(mode)), "perc_set_passes")
 
     def pores(self) -> np.ndarray:
         out = np.empty(self.L ** self.dims, dtype=np.uint8)

@@ -137,3 +137,42 @@ def test_bench_configurations(perc):
     for k in range(0, n, 257):
         _, size, spans, steps = oracle.perc_invade(2, Lb, oracle.perc_pores(2, Lb, seeds[k], Pb))
         assert (res[k].size, bool(res[k].spans), res[k].steps) == (size, spans, steps), k
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_pass_modes_agree(perc, mode):
+    """The graph-replayed passes (the default) and the persistent cooperative
+    launch give the oracle's results."""
+    for dims, L, P in ((2, 257, 0.6), (2, 1024, 0.592746), (3, 40, 0.3116)):
+        m = perc.Medium(dims, L, 77 + L)
+        m.set_passes(mode)
+        m.generate(P)
+        pore = oracle.perc_pores(dims, L, 77 + L, P)
+        for source in (POINT, FACE):
+            site = centre(dims, L)
+            r = m.invade(source, site)
+            c_o, size, spans, steps = oracle.perc_invade(dims, L, pore, source, site)
+            assert np.array_equal(m.cluster(), c_o), (dims, L, source, mode)
+            assert (r.size, bool(r.spans), r.steps) == (size, spans, steps)
+        m.close()
+
+
+def test_persistent_barrier_timeout_is_reported(perc):
+    """With the test hook on, one CTA of the persistent launch leaves before
+    the first grid barrier: the others' bounded waits run out, perc_invade
+    returns ISING_ETIMEOUT, nothing hangs, and the next invasion is right."""
+    from paper_cs_0312006_gb300 import engine
+    m = perc.Medium(2, 2048, 5)
+    m.set_passes(perc.PASSES_PERSISTENT)
+    m.generate(0.6)
+    engine.test_inject_timeout(True)
+    try:
+        with pytest.raises(engine.IsingError) as ei:
+            m.invade(FACE)
+        assert ei.value.code == engine.ETIMEOUT
+    finally:
+        engine.test_inject_timeout(False)
+    r = m.invade(FACE)
+    _, size, spans, steps = oracle.perc_invade(2, 2048, oracle.perc_pores(2, 2048, 5, 0.6))
+    assert (r.size, bool(r.spans), r.steps) == (size, spans, steps)
+    m.close()
