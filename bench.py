@@ -863,7 +863,10 @@ def main():
                     default="scan",
                     help="scan: the 2D L=8192 beta scan (default line); batched: 2048 "
                          "lattices in one launch vs one launch per lattice; serving: Poisson "
-                         "job stream")
+                         "job stream; philox: the device generator alone; small: 2D L=64, "
+                         "1000 sweeps; cubic: 3D L=256; big: one 2D lattice of --big-L "
+                         "(default 65536, out of L2); percolation: an L=16384 medium and a "
+                         "batch of L=128 media")
     ap.add_argument("--batch-lattices", type=int, default=2048)
     ap.add_argument("--batch-sweeps", type=int, default=500)
     ap.add_argument("--batch-layout", choices=["auto", "int8", "bitpack", "mixed"], default=None,
