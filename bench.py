@@ -747,7 +747,10 @@ def run_percolation_workload(args):
               threshold, so the cluster is deep): porosity field, then face
               invasion by synchronous growth passes to the steady state;
     batch  -- 8192 media of 2D L = 128 at the paper's threshold 0.592746, one
-              CTA per medium (spanning fraction reported).
+              CTA per medium (spanning fraction reported);
+    scan   -- spanning fractions over seven porosities around the threshold
+              for L = 64, 128, 256, 512 and the fitted porosity where half
+              the media span.
     The oracle runs on bounded samples of both as the CPU baseline."""
     import torch
     from paper_cs_0312006_gb300 import _build, percolation
@@ -791,6 +794,25 @@ def run_percolation_workload(args):
     batch = {"L": Lb, "porosity": Pb, "media": n, "seconds": bt, "media_per_s": n / bt,
              "sites_per_s": n * Lb * Lb / bt, "spanning_fraction": frac,
              "mean_steps": sum(x.steps for x in res) / n}
+    # spanning probability against porosity for growing L: where half the media
+    # span approaches the threshold (0.592746 in Sec. 5) as L grows; the
+    # porosities are spread over the transition, whose width falls as L^(-3/4)
+    scan = []
+    pc = 0.592746
+    for k_L, Ls in enumerate((64, 128, 256, 512)):
+        width = 0.012 * (Ls / 128) ** -0.75
+        Ps = [pc + width * x for x in (-2.0, -1.0, -0.5, 0.0, 0.5, 1.0, 2.0)]
+        ns = args.perc_scan_media
+        t0 = time.perf_counter()
+        fr = []
+        for j, Pj in enumerate(Ps):
+            sd_seeds = [BASE_SEED + 10_000_000 * (k_L + 1) + 100_000 * j + q for q in range(ns)]
+            fr.append(sum(x.spans for x in percolation.batch(2, Ls, Pj, sd_seeds)) / ns)
+        st = time.perf_counter() - t0
+        p_half, p_sd = percolation.spanning_threshold(Ps, fr, ns)
+        scan.append({"L": Ls, "media_per_porosity": ns, "porosities": Ps,
+                     "spanning_fraction": fr, "p_half": p_half, "p_half_sd": p_sd,
+                     "seconds": st})
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -808,7 +830,7 @@ def run_percolation_workload(args):
             "workload": "site percolation, 2D: one L=16384 medium at P=0.6 (porosity field "
                         "+ face invasion to the steady state) and a batch of L=128 media at "
                         "P=0.592746",
-            "medium": medium, "batch": batch, "cpu_baseline": cpu,
+            "medium": medium, "batch": batch, "threshold_scan": scan, "cpu_baseline": cpu,
             "device": torch.cuda.get_device_name()}
     print(json.dumps(line), flush=True)
     return 0
@@ -877,6 +899,8 @@ def main():
                     help="big: linear size of the single 2D lattice")
     ap.add_argument("--perc-L", type=int, default=16384)
     ap.add_argument("--perc-media", type=int, default=8192)
+    ap.add_argument("--perc-scan-media", type=int, default=8192,
+                    help="media per porosity in the percolation threshold scan")
     ap.add_argument("--cubic-L", type=int, default=256)
     ap.add_argument("--cubic-sweeps", type=int, default=1000)
     ap.add_argument("--serve-jobs", type=int, default=2000)

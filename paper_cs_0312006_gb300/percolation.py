@@ -1,11 +1,14 @@
 """Python binding of the percolation engine (C ABI of include/percolation.h).
 
 Argument marshalling only: the porosity field, the invasion passes and the
-measurements all run in the library's kernels (csrc/percolation.cu).
+measurements all run in the library's kernels (csrc/percolation.cu).  The one
+piece of host arithmetic is spanning_threshold, a fit over the spanning
+fractions those kernels report.
 """
 from __future__ import annotations
 
 import ctypes
+import math
 
 import numpy as np
 
@@ -120,3 +123,29 @@ def batch(dims: int, L: int, porosity: float, seeds, source: int = FACE, site: i
                           ctypes.c_void_p(int(raw) if raw else 0)),
            "perc_batch")
     return list(res)
+
+
+def spanning_threshold(porosities, fractions, n: int):
+    """Finite-size estimate of the porosity threshold from spanning fractions
+    (host statistics on results the kernels produced; Sec. 2.3 asks whether a
+    spanning cluster forms, Sec. 5 prints the 2D threshold).
+
+    Weighted least squares of logit(f) = a (P - P0) + b over the points with
+    0 < f < 1, each weighted by its binomial information n f (1 - f); P0 is
+    the mean porosity.  Returns (p_half, sd): the porosity where half the
+    media span, P0 - b / a, and its standard error by the delta method.
+    Raises ValueError with fewer than two usable points."""
+    P = np.asarray(porosities, dtype=np.float64)
+    f = np.asarray(fractions, dtype=np.float64)
+    keep = (f > 0.0) & (f < 1.0)
+    if np.count_nonzero(keep) < 2:
+        raise ValueError("need two spanning fractions strictly between 0 and 1")
+    P, f = P[keep], f[keep]
+    P0 = float(P.mean())
+    y = np.log(f / (1.0 - f))
+    w = n * f * (1.0 - f)
+    A = np.vstack([P - P0, np.ones_like(P)]).T
+    cov = np.linalg.inv(A.T @ (w[:, None] * A))
+    a, b = cov @ (A.T @ (w * y))
+    grad = np.array([b / a ** 2, -1.0 / a])
+    return P0 - b / a, math.sqrt(float(grad @ cov @ grad))

@@ -176,3 +176,28 @@ def test_persistent_barrier_timeout_is_reported(perc):
     _, size, spans, steps = oracle.perc_invade(2, 2048, oracle.perc_pores(2, 2048, 5, 0.6))
     assert (r.size, bool(r.spans), r.steps) == (size, spans, steps)
     m.close()
+
+
+def test_spanning_threshold_at_L512(perc):
+    """Sec. 5's 2D threshold from the GPU batch: 5 x 4096 media of L = 512
+    around 0.592746; the fitted porosity where half of them span equals the
+    paper's value within 5 standard errors plus 5e-4 for the finite size, and
+    the transition is steeper than at L = 64 (its width falls with L)."""
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "paper_values.txt")) as f:
+        pc = next(float(ln.split("#")[0].split("=")[1]) for ln in f
+                  if ln.startswith("percolation_threshold_2d"))
+    n = 4096
+
+    def fractions(L, Ps, base):
+        return [sum(r.spans for r in perc.batch(2, L, P, [base + 10_000 * j + k for k in range(n)]))
+                / n for j, P in enumerate(Ps)]
+
+    Ps = [pc + d for d in (-0.008, -0.004, 0.0, 0.004, 0.008)]
+    f512 = fractions(512, Ps, 5_000_000)
+    assert all(b > a for a, b in zip(f512, f512[1:]))
+    p_half, sd = perc.spanning_threshold(Ps, f512, n)
+    assert abs(p_half - pc) <= 5 * sd + 5e-4, (p_half, sd)
+    f64 = fractions(64, [Ps[0], Ps[-1]], 6_000_000)
+    assert f512[-1] - f512[0] > f64[1] - f64[0]
