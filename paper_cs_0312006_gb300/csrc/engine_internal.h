@@ -56,6 +56,25 @@ struct DeviceProps {
     volatile int* h_err = nullptr;
 };
 
+// Launch `kernel` on `st` with programmatic stream serialisation: it may be
+// scheduled before the previous kernel of the stream completes, and must call
+// grid_dependency_wait() (ising_device.cuh) before touching global memory.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                           cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // engine.cu helpers shared with batch.cu
 int cuda_fail(cudaError_t e);
 // the test hook of ising_test_inject_timeout is on

@@ -54,6 +54,23 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
     return Philox4{c0, c1, c2, c3};
 }
 
+// Programmatic dependent launch (griddepcontrol, sm_90 and later).  The
+// per-lattice pass kernels are launched with programmatic stream
+// serialisation (launch_chained), so the next kernel in the stream can be
+// scheduled onto SMs while this one finishes.  Every such kernel calls
+// grid_dependency_wait() before its first global memory access: it returns
+// once all earlier kernels of the stream have completed and their writes are
+// visible (a pass reads the colour the previous pass wrote and writes the
+// colour it read), and it is a no-op for a kernel launched without the
+// attribute.  launch_dependents() then lets the next pass's CTAs be placed as
+// SMs free up; they in turn wait before touching memory.
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Arguments of one colour pass.  The colour-c array is updated in place; it
 // reads only the colour-(1-c) array, so no site reads a value written by the
 // same pass (Sec. 2.2: a pass through all sites of one colour).

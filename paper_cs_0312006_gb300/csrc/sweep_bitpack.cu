@@ -33,6 +33,8 @@ __global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a) {
     const uint32_t items = (uint32_t)a.rows * (((uint32_t)a.W + 31u) >> 5);
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_acc = 0;
+    grid_dependency_wait();
+    launch_dependents();
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride)
         packed_word<DIMS, MEASURE, 1, RULE>(a, g, e_acc, m_acc);
     if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
@@ -119,8 +121,7 @@ cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream
     const int64_t cap = (int64_t)dp.sm_count * dp.blocks_per_sm_packed[RULE][DIMS - 2][MEASURE];
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    pass_packed<DIMS, MEASURE, RULE><<<(unsigned)blocks, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_chained(pass_packed<DIMS, MEASURE, RULE>, (unsigned)blocks, 256u, 0, st, a);
 }
 
 }  // namespace

@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 3) pass_demon_strip(PassA
     uint4 om = zero, oc = zero, op = zero, sc = zero, qc = zero, zm = zero, zp = zero;
     bool reload = true;
     int e_acc = 0, m_neg = 0, n_rows = 0;
+    grid_dependency_wait();
+    launch_dependents();
 
     for (int i = 0; i < max_len; ++i) {
         const bool valid = i < len;
@@ -215,6 +217,8 @@ __global__ void __launch_bounds__(256) pass_demon_sites(PassArgs a, uint32_t hal
     const uint32_t W = (uint32_t)a.W, L = (uint32_t)a.L, rows = (uint32_t)a.rows;
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_acc = 0;
+    grid_dependency_wait();
+    launch_dependents();
     for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < half; h += stride) {
         const uint32_t r = h / W, xh = h - r * W;
         uint32_t y = r, z = 0;
@@ -336,6 +340,8 @@ __global__ void __launch_bounds__(256) pass_demon_packed4(PassArgs a) {
     uint4* Q1 = reinterpret_cast<uint4*>(static_cast<uint32_t*>(a.dem) + words);
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_acc = 0;
+    grid_dependency_wait();
+    launch_dependents();
     for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < items; item += stride) {
         const uint32_t r = item / n4, g = item - r * n4;
         uint32_t y = r, z = 0u;
@@ -410,6 +416,8 @@ __global__ void __launch_bounds__(256) pass_demon_packed(PassArgs a) {
     uint32_t* Q1 = Q0 + items;
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_acc = 0;
+    grid_dependency_wait();
+    launch_dependents();
     for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < items; item += stride) {
         const uint32_t r = item / nq, q = item - r * nq;
         uint32_t y = r, z = 0u;
@@ -547,12 +555,11 @@ cudaError_t launch_demon_t(const PassArgs& a0, int64_t half_sites, const DeviceP
         if (strips < 1) strips = 1;
         a.strips = (int)strips;
         const int64_t blocks = (strips * a.nv + threads - 1) / threads;
-        pass_demon_strip<DIMS, MEASURE><<<(unsigned)blocks, threads, 0, st>>>(a);
-    } else {
-        pass_demon_sites<DIMS, MEASURE>
-            <<<grid_for(half_sites, dp), threads, 0, st>>>(a0, (uint32_t)half_sites);
+        return launch_chained(pass_demon_strip<DIMS, MEASURE>, (unsigned)blocks,
+                              (unsigned)threads, 0, st, a);
     }
-    return cudaGetLastError();
+    return launch_chained(pass_demon_sites<DIMS, MEASURE>, grid_for(half_sites, dp),
+                          (unsigned)threads, 0, st, a0, (uint32_t)half_sites);
 }
 
 }  // namespace
@@ -588,32 +595,19 @@ cudaError_t demon_packed_pass(const PassArgs& a, int dims, bool measure, const D
     const int64_t cap = (int64_t)dp.sm_count * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    const unsigned g = (unsigned)blocks;
     if (vec) {
-        if (dims == 2) {
-            if (measure)
-                pass_demon_packed4<2, true><<<(unsigned)blocks, 256, 0, st>>>(a);
-            else
-                pass_demon_packed4<2, false><<<(unsigned)blocks, 256, 0, st>>>(a);
-        } else {
-            if (measure)
-                pass_demon_packed4<3, true><<<(unsigned)blocks, 256, 0, st>>>(a);
-            else
-                pass_demon_packed4<3, false><<<(unsigned)blocks, 256, 0, st>>>(a);
-        }
-        return cudaGetLastError();
+        if (dims == 2)
+            return measure ? launch_chained(pass_demon_packed4<2, true>, g, 256u, 0, st, a)
+                           : launch_chained(pass_demon_packed4<2, false>, g, 256u, 0, st, a);
+        return measure ? launch_chained(pass_demon_packed4<3, true>, g, 256u, 0, st, a)
+                       : launch_chained(pass_demon_packed4<3, false>, g, 256u, 0, st, a);
     }
-    if (dims == 2) {
-        if (measure)
-            pass_demon_packed<2, true><<<(unsigned)blocks, 256, 0, st>>>(a);
-        else
-            pass_demon_packed<2, false><<<(unsigned)blocks, 256, 0, st>>>(a);
-    } else {
-        if (measure)
-            pass_demon_packed<3, true><<<(unsigned)blocks, 256, 0, st>>>(a);
-        else
-            pass_demon_packed<3, false><<<(unsigned)blocks, 256, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    if (dims == 2)
+        return measure ? launch_chained(pass_demon_packed<2, true>, g, 256u, 0, st, a)
+                       : launch_chained(pass_demon_packed<2, false>, g, 256u, 0, st, a);
+    return measure ? launch_chained(pass_demon_packed<3, true>, g, 256u, 0, st, a)
+                   : launch_chained(pass_demon_packed<3, false>, g, 256u, 0, st, a);
 }
 
 cudaError_t demon_packed_import(uint32_t* d0, uint32_t* d1, const uint8_t* in, int L, int dims,

@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 2) pass_int8_strip(PassAr
     uint4 om = zero, oc = zero, op = zero, sc = zero, zm = zero, zp = zero;
     bool reload = true;
     int e_acc = 0, m_neg = 0, n_rows = 0;
+    grid_dependency_wait();
+    launch_dependents();
 
     for (int i = 0; i < max_len; ++i) {
         const bool valid = i < len;
@@ -155,6 +157,8 @@ __global__ void __launch_bounds__(256) pass_int8_vecs(PassArgs a, WordGeom g) {
     const uint32_t vecs = (g.half + 15u) >> 4;
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_neg = 0, n_sites = 0;
+    grid_dependency_wait();
+    launch_dependents();
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < vecs; v += stride)
         int8_vec<DIMS, MEASURE, 1, RULE>(a, g, v, e_acc, m_neg, n_sites);
     if (MEASURE) block_reduce_add(e_acc, n_sites - 2 * m_neg, a.obs, a.c == 1);
@@ -216,7 +220,8 @@ cudaError_t launch_pass_t(const PassArgs& a0, int64_t half_sites, bool vec, cons
         if (strips < 1) strips = 1;
         a.strips = (int)strips;
         const int64_t blocks = (strips * a.nv + threads - 1) / threads;
-        pass_int8_strip<DIMS, MEASURE, RULE><<<(unsigned)blocks, threads, 0, st>>>(a);
+        return launch_chained(pass_int8_strip<DIMS, MEASURE, RULE>, (unsigned)blocks,
+                              (unsigned)threads, 0, st, a);
     } else {
         const int64_t vecs = (half_sites + 15) >> 4;
         int64_t blocks = (vecs + threads - 1) / threads;
@@ -228,9 +233,9 @@ cudaError_t launch_pass_t(const PassArgs& a0, int64_t half_sites, bool vec, cons
         g.L = (uint32_t)a0.L;
         g.rows = (uint32_t)a0.rows;
         g.half = (uint32_t)half_sites;
-        pass_int8_vecs<DIMS, MEASURE, RULE><<<(unsigned)blocks, threads, 0, st>>>(a0, g);
+        return launch_chained(pass_int8_vecs<DIMS, MEASURE, RULE>, (unsigned)blocks,
+                              (unsigned)threads, 0, st, a0, g);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace

@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
         for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    grid_dependency_wait();  // the previous pass has completed (no global access before)
     __syncthreads();
+    launch_dependents();
     if (threadIdx.x == 0)
         for (int k = 0; k < kStages && k < my_tiles; ++k)
             issue_tile<DIMS>(a, tg, first + k * gridDim.x, smem + k * tg.stage_bytes, &bars[k],
@@ -308,8 +310,8 @@ cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uin
     if (per_sm < 1) per_sm = 1;
     int grid = dp.sm_count * per_sm;
     if (grid > tg.tiles) grid = tg.tiles;
-    pass_int8_tma<DIMS, MEASURE, RULE><<<grid, threads, smem, st>>>(a, tg, err);
-    return cudaGetLastError();
+    return launch_chained(pass_int8_tma<DIMS, MEASURE, RULE>, (unsigned)grid, (unsigned)threads,
+                          smem, st, a, tg, err);
 }
 
 }  // namespace
