@@ -29,9 +29,11 @@
 //     every wait on it bounded by %globaltimer, a CTA that gives up raises
 //     the error flag and leaves, and the others then give up at their next
 //     wait), the stop decided on the device from the pass's added count;
-//   - a replayed CUDA graph of kPassesPerGraph launches; after each replay
-//     the host reads the per-pass counts and stops at the first pass that
-//     added nothing (the rest of that replay are no-ops on an empty front).
+//   - a replayed CUDA graph of kPassesPerGraph chained launches (each pass
+//     is placed on the SMs while the previous one drains, and waits for it
+//     before touching memory); after each replay the host reads the per-pass
+//     counts and stops at the first pass that added nothing (the rest of that
+//     replay are no-ops on an empty front).
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -240,6 +242,8 @@ __global__ void __launch_bounds__(256) perc_band_kernel(const uint32_t* pore, ui
                                                         const uint32_t* Fo, uint32_t* Fn,
                                                         PercGeom g, Band* bands, int k,
                                                         unsigned long long* added) {
+    grid_dependency_wait();  // the previous pass has completed (chained launches)
+    launch_dependents();
     if (blockIdx.x == 0 && threadIdx.x == 0) bands[(k + 1) % kBandSlots] = Band{0xFFFFFFFFu, 0u};
     unsigned int lo, hi;
     pass_rows(bands, k, g, lo, hi);
@@ -625,10 +629,11 @@ int perc_invade(perc_medium* m, int source, int64_t site, perc_result* out) {
                                                   m->bands);
     PERC_CHECK(cudaGetLastError());
     int64_t steps = 0;
-    // AUTO takes the graph: on GB300 it measured 6.4 us per pass at L = 16384
-    // against 8.5 us for the persistent launch (2 - 4 CTAs per SM; 12 us with one,
-    // 14 us with all that fit): the pass's own work needs the wide grid, and
-    // the barrier costs about as much as a graph node's launch
+    // AUTO takes the graph: on GB300 it measured 4.6 us per pass at L = 16384
+    // (chained launches, eight CTAs per SM) against 8.5 us for the persistent
+    // launch (2 - 4 CTAs per SM; 12 us with one, 14 us with all that fit): the
+    // pass's own work needs the wide grid, and the grid barrier costs more than
+    // a chained graph node
     if (m->mode == PERC_PASSES_PERSISTENT && m->coop_grid > 0) {
         unsigned char* cb = static_cast<unsigned char*>(m->coop);
         unsigned long long* cnt = reinterpret_cast<unsigned long long*>(cb);
@@ -657,6 +662,11 @@ int perc_invade(perc_medium* m, int source, int64_t site, perc_result* out) {
         steps = (int64_t)host_out.steps;
     } else {
     if (!m->passes) {
+        // eight CTAs per SM walk the band (grid-stride): at L = 16384 on GB300
+        // 4.6 us per pass, against 4.8 us with four, 6.4 us with two and 6.1 us
+        // with sixteen (most of whose CTAs find no band words and leave)
+        const unsigned cap8 = (unsigned)m->sm_count * 8u;
+        const unsigned pass_grid = grid < cap8 ? grid : cap8;
         // capture [zero the counts, kPassesPerGraph banded passes] once; the
         // buffers and slots it uses belong to the medium, so replays continue
         cudaStream_t cap = nullptr;
@@ -666,10 +676,11 @@ int perc_invade(perc_medium* m, int source, int64_t site, perc_result* out) {
         if (e == cudaSuccess) {
             cudaError_t le = cudaMemsetAsync(m->counts, 0, kPassesPerGraph * 8, cap);
             for (int k = 0; k < kPassesPerGraph && le == cudaSuccess; ++k) {
-                perc_band_kernel<<<grid, 256, 0, cap>>>(m->pore, m->C, m->F[k & 1],
-                                                        m->F[(k & 1) ^ 1], m->g, m->bands, k,
-                                                        m->counts + k);
-                le = cudaGetLastError();
+                // chained: a pass is placed on the SMs while the previous one drains
+                le = launch_chained(perc_band_kernel, pass_grid, 256u, 0, cap,
+                                    static_cast<const uint32_t*>(m->pore), m->C,
+                                    static_cast<const uint32_t*>(m->F[k & 1]),
+                                    m->F[(k & 1) ^ 1], m->g, m->bands, k, m->counts + k);
             }
             e = cudaStreamEndCapture(cap, &graph);
             if (e == cudaSuccess) e = le;
