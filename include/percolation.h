@@ -72,8 +72,9 @@ int perc_get_cluster(perc_medium *m, uint8_t *host_out);
 
 /* How perc_invade runs its passes (same results either way):
  *   PERC_PASSES_AUTO (default): PERC_PASSES_GRAPH (measured the faster);
- *   PERC_PASSES_GRAPH: a CUDA graph of 64 pass launches replayed until a pass
- *       adds nothing;
+ *   PERC_PASSES_GRAPH: a CUDA graph of 64 chained pass launches (each placed
+ *       on the SMs while the previous one drains) replayed until a pass adds
+ *       nothing;
  *   PERC_PASSES_PERSISTENT: one cooperative launch (two CTAs per SM), the
  *       passes separated by a grid barrier whose every wait is bounded (about
  *       a second); a wait that runs out makes perc_invade return
