@@ -539,8 +539,9 @@ def run_gpu(args, world, rank, local):
                 for lat in lats:
                     lat.sweep(1, 1)
                 half = k % 2
-                for j, lat in enumerate(lats):
-                    d2h += 16 * lat.observables_async(pairs[half, j])  # D2H of (E, M)
+                # D2H of every lattice's (E, M): one gather kernel writes them
+                # into the pinned buffer
+                d2h += 16 * int(engine.observables_gather(lats, pairs[half]).sum())
                 ready[half].record(stream)
                 if last is not None:
                     ready[last].synchronize()
@@ -561,9 +562,9 @@ def run_gpu(args, world, rank, local):
                "unit": "site updates/s", "h2d_bytes_per_step": h2d_total / e2e_steps,
                "d2h_bytes_per_step": d2h / e2e_steps, "steps": e2e_steps,
                "note": "per layout: ising_set_spins from pinned host memory, then per step one "
-                       "sweep of each lattice and ising_observables_async of its (E, M) into "
-                       "pinned host memory, read on the host while the next step runs, then "
-                       "ising_get_spins"}
+                       "sweep of each lattice and one ising_observables_gather of every "
+                       "lattice's (E, M) into pinned host memory, read on the host while the "
+                       "next step runs, then ising_get_spins"}
 
     for lats in sets.values():
         for lat in lats:

@@ -169,6 +169,24 @@ int ising_observables(ising_lattice *lat, int64_t *E, int64_t *M, int64_t cap,
  */
 int ising_observables_async(ising_lattice *lat, int64_t *pairs, int64_t cap, int64_t *count);
 
+/*
+ * The same asynchronous read for n lattices at once, with one queued kernel
+ * instead of a copy and a clear per lattice (the per-sweep records of Sec. 2.2
+ * for a whole set of lattices).  All n lattices must use the same stream; the
+ * work goes there.  counts[i] (host, n entries) receives lattice i's number of
+ * pending records at once, and its records go to pairs[2 * off_i ...] (int64
+ * (E, M) pairs, oldest first) with off_i = counts[0] + ... + counts[i - 1];
+ * they are cleared on the device.  `pairs` must be pinned host memory the
+ * device can write (cudaHostAlloc, cudaMallocHost or cudaHostRegister, as
+ * torch's pin_memory is); the kernel stores into it directly.  The values are
+ * in place once the stream has passed this point.  ISING_EINVAL for n < 1, a
+ * NULL argument or lattice, lattices on different streams, or `pairs` not
+ * device-writable (nothing is queued or cleared then); ISING_ERANGE if cap
+ * (pairs) is below the total pending, likewise with nothing queued.
+ */
+int ising_observables_gather(ising_lattice *const *lats, int n, int64_t *pairs, int64_t cap,
+                             int64_t *counts);
+
 /* Copy the spins to host memory in canonical order (L^dims int8).  Syncs. */
 int ising_get_spins(ising_lattice *lat, int8_t *host_out);
 

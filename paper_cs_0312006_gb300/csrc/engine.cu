@@ -217,6 +217,29 @@ int check_timeout(ising_lattice* h) {
     return ISING_ETIMEOUT;
 }
 
+// Records of several lattices in one launch (ising_observables_gather): CTA i
+// copies lattice i's pending (E, M) pairs to `out` (mapped pinned host memory)
+// at its offset and zeroes them, restoring the zero invariant of the slots.
+constexpr int kGatherChunk = 64;
+struct GatherChunk {
+    unsigned long long* src[kGatherChunk];
+    int64_t n[kGatherChunk];
+    int64_t off[kGatherChunk];
+    int count;
+};
+
+__global__ void gather_records_kernel(GatherChunk c, long long* out) {
+    grid_dependency_wait();  // the sweeps that wrote the records have completed
+    launch_dependents();
+    const int i = blockIdx.x;
+    unsigned long long* src = c.src[i];
+    long long* dst = out + 2 * c.off[i];
+    for (int64_t j = threadIdx.x; j < 2 * c.n[i]; j += blockDim.x) {
+        dst[j] = (long long)src[j];
+        src[j] = 0ull;
+    }
+}
+
 bool uses_tma(const ising_lattice* h) {
     return h->layout != ISING_BITPACK && ising::int8_tma_ok(h->dims, h->L) &&
            (h->kernel == ISING_KERNEL_TMA ||
@@ -434,6 +457,51 @@ int ising_observables_async(ising_lattice* h, int64_t* pairs, int64_t cap, int64
                                 h->stream));
     ISING_CHECK(cudaMemsetAsync(h->obs, 0, (size_t)n * 16, h->stream));
     h->n_rec = 0;
+    return ISING_OK;
+}
+
+int ising_observables_gather(ising_lattice* const* lats, int n, int64_t* pairs, int64_t cap,
+                             int64_t* counts) {
+    if (!lats || n < 1 || !counts) return ISING_EINVAL;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!lats[i] || lats[i]->stream != lats[0]->stream) return ISING_EINVAL;
+        total += lats[i]->n_rec;
+    }
+    if (total > 0 && !pairs) return ISING_EINVAL;
+    if (total > cap) return ISING_ERANGE;
+    long long* out = nullptr;
+    if (total > 0) {
+        // the kernel writes the host buffer directly: it must be pinned (mapped)
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, pairs) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return ISING_EINVAL;
+        }
+        if (attr.type != cudaMemoryTypeHost || !attr.devicePointer) return ISING_EINVAL;
+        out = static_cast<long long*>(attr.devicePointer);
+    }
+    for (int i = 0; i < n; ++i) counts[i] = lats[i]->n_rec;
+    if (total == 0) return ISING_OK;
+    GatherChunk chunk;
+    chunk.count = 0;
+    int64_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        ising_lattice* h = lats[i];
+        if (h->n_rec > 0) {
+            chunk.src[chunk.count] = h->obs;
+            chunk.n[chunk.count] = h->n_rec;
+            chunk.off[chunk.count] = off;
+            ++chunk.count;
+            off += h->n_rec;
+            h->n_rec = 0;
+        }
+        if (chunk.count == kGatherChunk || (i == n - 1 && chunk.count > 0)) {
+            ISING_CHECK(launch_chained(gather_records_kernel, (unsigned)chunk.count, 64u, 0,
+                                       lats[0]->stream, chunk, out));
+            chunk.count = 0;
+        }
+    }
     return ISING_OK;
 }
 

@@ -75,6 +75,8 @@ def load_library():
             "ising_sweep": ([P, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
             "ising_observables": ([P, i64p, i64p, ctypes.c_int64, i64p], ctypes.c_int),
             "ising_observables_async": ([P, P, ctypes.c_int64, i64p], ctypes.c_int),
+            "ising_observables_gather": ([ctypes.POINTER(P), ctypes.c_int, P, ctypes.c_int64,
+                                          i64p], ctypes.c_int),
             "ising_get_spins": ([P, P], ctypes.c_int),
             "ising_set_spins": ([P, P, ctypes.c_uint64], ctypes.c_int),
             "ising_export_device": ([P, P], ctypes.c_int),
@@ -388,3 +390,24 @@ def batch_run_static(lattices, sweeps, measure_every, records_ptr: int, records_
                                       ctypes.byref(opts),
                                       ctypes.c_void_p(int(raw) if raw else 0)),
            "ising_batch_run_static")
+
+
+def observables_gather(lattices, pairs: np.ndarray, counts: np.ndarray | None = None) -> np.ndarray:
+    """``ising_observables_gather``: enqueue, with one kernel on the lattices'
+    common stream, the copy of every lattice's pending (E, M) records into
+    ``pairs`` (a pinned int64 array of shape (cap, 2), written by the device
+    directly) and clear them.  Returns the per-lattice record counts at once;
+    lattice i's records start at row counts[:i].sum().  The values are valid
+    once the stream passes this point (e.g. an event recorded next)."""
+    lib = load_library()
+    assert pairs.dtype == np.int64 and pairs.flags.c_contiguous
+    n = len(lattices)
+    if counts is None:
+        counts = np.zeros(n, dtype=np.int64)
+    assert counts.dtype == np.int64 and counts.size >= n and counts.flags.c_contiguous
+    handles = (ctypes.c_void_p * n)(*[lat.handle for lat in lattices])
+    _check(lib.ising_observables_gather(handles, n, ctypes.c_void_p(pairs.ctypes.data),
+                                        pairs.size // 2,
+                                        counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+           "ising_observables_gather")
+    return counts

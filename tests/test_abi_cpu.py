@@ -120,3 +120,13 @@ def test_percolation_rejects_bad_arguments_on_the_host(lib):
     assert lib.perc_batch(2, 64, 1.5, seeds, 1, 1, 0, res, None, None) == -1
     assert lib.perc_batch(2, 64, 0.5, seeds, 0, 1, 0, res, None, None) == -1
     lib.perc_destroy(None)
+
+
+def test_observables_gather_rejects_bad_arguments_on_the_host(lib):
+    counts = (ctypes.c_int64 * 2)()
+    pairs = (ctypes.c_int64 * 8)()
+    none2 = (ctypes.c_void_p * 2)(None, None)
+    assert lib.ising_observables_gather(None, 1, pairs, 4, counts) == -1
+    assert lib.ising_observables_gather(none2, 0, pairs, 4, counts) == -1
+    assert lib.ising_observables_gather(none2, 2, pairs, 4, counts) == -1  # NULL lattices
+    assert lib.ising_observables_gather(none2, 2, pairs, 4, None) == -1
