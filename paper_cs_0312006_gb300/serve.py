@@ -102,6 +102,8 @@ class Server:
         self.rounds = 0
         self.updates_done = 0
         self.t0 = None
+        self._pinned = None  # host buffer of the records' gather (grown on demand)
+        self._pinned_grow = False
 
     # -- requests ---------------------------------------------------------
     def submit(self, job: Job) -> None:
@@ -164,11 +166,11 @@ class Server:
         batch.sync()
         batch.close()
         self.rounds += 1
+        records = self._read_records(lats)
         still = []
-        for r, q in zip(self.resident, quanta):
+        for r, q, (E, M) in zip(self.resident, quanta, records):
             r.remaining -= q
             self.updates_done += q * r.job.spec.sites
-            E, M = r.lat.observables()
             r.E.append(E)
             r.M.append(M)
             if r.remaining == 0:
@@ -182,6 +184,32 @@ class Server:
             else:
                 still.append(r)
         self.resident = still
+
+    def _read_records(self, lats) -> list:
+        """Every resident lattice's pending (E, M) records: engine lattices (one
+        stream) through one ising_observables_gather into a pinned buffer and
+        one synchronisation; stand-ins one by one."""
+        if self.lattice_factory is not engine.Lattice or not lats:
+            return [lat.observables() for lat in lats]
+        import torch
+        while True:
+            if self._pinned is None or self._pinned_grow:
+                cap = max(1024, 2 * (0 if self._pinned is None else len(self._pinned)))
+                self._pinned = torch.zeros((cap, 2), dtype=torch.int64).pin_memory().numpy()
+                self._pinned_grow = False
+            try:
+                counts = engine.observables_gather(lats, self._pinned)
+                break
+            except engine.IsingError as e:
+                if e.code != engine.ERANGE:
+                    raise
+                self._pinned_grow = True  # nothing was queued: retry with more room
+        lats[0].synchronize()  # one wait (and the bounded-wait check) for all
+        out, off = [], 0
+        for c in counts:
+            out.append((self._pinned[off:off + c, 0].copy(), self._pinned[off:off + c, 1].copy()))
+            off += int(c)
+        return out
 
     def run(self, jobs=None) -> dict:
         """Serve ``jobs`` (arriving at their ``arrival_s`` after start) until all
