@@ -82,6 +82,70 @@ __device__ __forceinline__ void group_sync() {
         __syncthreads();
 }
 
+// Word w of the int8 colour array when a half row holds whole words
+// (W % 4 == 0): every word lies in one row, so its neighbour words are aligned
+// words of the other colour -- the same word of the rows (and planes) above
+// and below, and for the x-neighbours the word itself plus the previous or next
+// word of its own row taken cyclically (funnel-shifted by one byte).  Every
+// word, row ends and wrap rows included, takes this one path, with the rule
+// and draws of int8_word (word w's draw is Philox group w).
+template <int DIMS, bool MEASURE, int NC, int RULE>
+__device__ __forceinline__ void int8_word_rows(const PassArgs& a, const WordGeom& g, uint32_t w,
+                                               int& e_acc, int& m_neg, int& n_sites) {
+    uint32_t* own = static_cast<uint32_t*>(a.own);
+    const uint32_t* other = static_cast<const uint32_t*>(a.other);
+    const uint32_t nq = g.W >> 2;  // words per half row
+    const uint32_t r = w / nq, q = w - r * nq;
+    uint32_t y = r, z = 0u;
+    if (DIMS == 3) {
+        z = r / g.L;
+        y = r - z * g.L;
+    }
+    const int p = (a.c + (int)y + (int)z) & 1;
+    const uint32_t row0 = r * nq;
+    const uint32_t s = own[w];
+    const uint32_t nx = load_other<NC>(other + w);
+    uint32_t nxs;
+    if (p == 0) {  // byte j <- byte j - 1 of the row, cyclically
+        const uint32_t prev = load_other<NC>(other + row0 + (q == 0u ? nq - 1u : q - 1u));
+        nxs = __funnelshift_l(prev, nx, 8);
+    } else {       // byte j <- byte j + 1 of the row, cyclically
+        const uint32_t next = load_other<NC>(other + row0 + (q + 1u == nq ? 0u : q + 1u));
+        nxs = __funnelshift_r(nx, next, 8);
+    }
+    const uint32_t plane = z * g.L;
+    const uint32_t nym = load_other<NC>(other + (plane + (y == 0u ? g.L - 1u : y - 1u)) * nq + q);
+    const uint32_t nyp = load_other<NC>(other + (plane + (y + 1u == g.L ? 0u : y + 1u)) * nq + q);
+    uint32_t nzm = 0u, nzp = 0u;
+    if (DIMS == 3) {
+        nzm = load_other<NC>(other + ((z == 0u ? g.L - 1u : z - 1u) * g.L + y) * nq + q);
+        nzp = load_other<NC>(other + ((z + 1u == g.L ? 0u : z + 1u) * g.L + y) * nq + q);
+    }
+    const uint32_t D = disagreements<DIMS>(s, nx, nxs, nym, nyp, nzm, nzp);
+    uint32_t X;
+    if (RULE == kRuleHeatBath) {
+        const Philox4 u = philox4x32_10(w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
+        X = heatbath_count<DIMS>(D, u, a);
+    } else {
+        X = downhill_mask<DIMS>(D);
+        if (X != 0xFEFEFEFEu) {
+            const Philox4 u = philox4x32_10(w, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
+            X |= uphill_count<DIMS>(D, u, a);
+        }
+    }
+    const uint32_t snew = s ^ X;
+    own[w] = snew;
+    if (MEASURE) {
+        m_neg += __popc(snew & kByteBit7);
+        n_sites += 4;
+        if (a.c == 1) {
+            constexpr uint32_t q2 = 4u * DIMS * kByteOnes;
+            const uint32_t Dn = (D & ~X) | ((q2 - D) & X);
+            e_acc += __dp4a((int)Dn, (int)kByteOnes, 0) - 4 * 2 * DIMS;
+        }
+    }
+}
+
 template <int DIMS, int LAYOUT, bool MEASURE, int NC, int RULE>
 __device__ __forceinline__ void job_pass(const BatchJob& j, int c, uint32_t t, uint32_t rank,
                                          uint32_t nthr, int& e_acc, int& m_acc) {
@@ -109,6 +173,11 @@ __device__ __forceinline__ void job_pass(const BatchJob& j, int c, uint32_t t, u
         if (j.W >= 64 && vecs >= nthr) {
             for (uint32_t v = rank; v < vecs; v += nthr)
                 int8_vec<DIMS, MEASURE, NC, RULE>(a, g, v, e_acc, m_neg, n_sites);
+        } else if (j.W % 4 == 0 && RULE != kRuleMultiHit) {
+            // short rows of whole words: one uniform path for every word
+            const uint32_t words = j.half >> 2;
+            for (uint32_t w = rank; w < words; w += nthr)
+                int8_word_rows<DIMS, MEASURE, NC, RULE>(a, g, w, e_acc, m_neg, n_sites);
         } else {  // short rows or few vectors: four sites per item spread further
             const uint32_t words = (j.half + 3u) >> 2;
             for (uint32_t w = rank; w < words; w += nthr)
