@@ -132,7 +132,7 @@ def scan_betas():
 
 
 def workload_config(L: int, steps: int, lattices: int = N_BETA,
-                    rule: str = "metropolis", big: bool = False, time_every: int = 1) -> dict:
+                    rule: str = "metropolis", big: bool = False) -> dict:
     name = {"metropolis": "checkerboard Metropolis", "heatbath": "checkerboard heat-bath",
             "demon": f"deterministic demon dynamics, qmax={DEMON_QMAX}"}[rule]
     if big:
@@ -147,10 +147,7 @@ def workload_config(L: int, steps: int, lattices: int = N_BETA,
             "rule": rule,
             "lattices_per_gpu": lattices,
             "l2": f"inputs larger than L2: a step touches {lattices} x L^2 bytes of int8 spins",
-            "step": "one sweep (black pass, white pass, fused E/M) of each lattice",
-            "pass_timing": f"CUDA events around each lattice's sweep on every {time_every}th "
-                           f"step of the timed region (the events sit between the sweeps, "
-                           f"so fewer of them disturb the chained launches less)"}
+            "step": "one sweep (black pass, white pass, fused E/M) of each lattice"}
 
 
 def dist_setup():
@@ -590,7 +587,10 @@ def run_gpu(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
         "data": "synthetic",
         "config": workload_config(L, args.steps, len(betas), args.rule,
-                                  big=args.workload == "big", time_every=every),
+                                  big=args.workload == "big"),
+        "pass_timing": f"CUDA events around each lattice's sweep on every {every}th step of "
+                       f"the timed region (the events sit between sweeps, so fewer of them "
+                       f"disturb the chained launches less)",
         "layouts": layout_stats,
         "roofline": rooflines.get("int8") or rooflines.get("bitpack"),
         "roofline_bitpack": rooflines.get("bitpack"),
