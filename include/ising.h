@@ -176,7 +176,8 @@ int ising_observables_async(ising_lattice *lat, int64_t *pairs, int64_t cap, int
  * work goes there.  counts[i] (host, n entries) receives lattice i's number of
  * pending records at once, and its records go to pairs[2 * off_i ...] (int64
  * (E, M) pairs, oldest first) with off_i = counts[0] + ... + counts[i - 1];
- * they are cleared on the device.  `pairs` must be pinned host memory the
+ * they are cleared on the device (a handle listed twice gets them at its first
+ * entry and a count of 0 at the second).  `pairs` must be pinned host memory the
  * device can write (cudaHostAlloc, cudaMallocHost or cudaHostRegister, as
  * torch's pin_memory is); the kernel stores into it directly.  The values are
  * in place once the stream has passed this point.  ISING_EINVAL for n < 1, a

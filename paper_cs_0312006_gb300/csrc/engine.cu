@@ -481,13 +481,16 @@ int ising_observables_gather(ising_lattice* const* lats, int n, int64_t* pairs, 
         if (attr.type != cudaMemoryTypeHost || !attr.devicePointer) return ISING_EINVAL;
         out = static_cast<long long*>(attr.devicePointer);
     }
-    for (int i = 0; i < n; ++i) counts[i] = lats[i]->n_rec;
-    if (total == 0) return ISING_OK;
+    if (total == 0) {
+        for (int i = 0; i < n; ++i) counts[i] = 0;
+        return ISING_OK;
+    }
     GatherChunk chunk;
     chunk.count = 0;
     int64_t off = 0;
     for (int i = 0; i < n; ++i) {
         ising_lattice* h = lats[i];
+        counts[i] = h->n_rec;  // 0 for a handle listed twice, read at its first entry
         if (h->n_rec > 0) {
             chunk.src[chunk.count] = h->obs;
             chunk.n[chunk.count] = h->n_rec;

@@ -61,6 +61,14 @@ def test_gather_equals_per_lattice_reads(eng):
     # nothing pending now
     again = eng.observables_gather(lats, pairs)
     assert not again.any()
+    # a handle listed twice: its records at the first entry, none at the second
+    lats[0].sweep(2, 1)
+    counts = eng.observables_gather([lats[0], lats[1], lats[0]], pairs)
+    torch.cuda.synchronize()
+    assert list(counts) == [2, 0, 0]
+    twins[0].sweep(2, 1)
+    E, M = twins[0].observables()
+    assert np.array_equal(pairs[:2, 0], E) and np.array_equal(pairs[:2, 1], M)
     # the small 2D lattice against the oracle: 14 sweeps, E/M after each
     lat = eng.Lattice(2, 64, 0.44, 11, layout=INT8)
     lat.sweep(14, 1)
