@@ -120,3 +120,24 @@ def test_kaufman_large_torus_tends_to_onsager():
     for beta in (0.30, 0.60):
         assert abs(exact.kaufman_mean_energy(beta, 64) / 64 ** 2 -
                    exact.onsager_energy_per_site(beta)) < 1e-9
+
+
+@pytest.mark.parametrize("beta", [0.06, 0.08])
+def test_cubic_energy_high_temperature_series(orc, beta):
+    """3D has no closed form, but its high-temperature series fixes the
+    leading terms: with t = tanh(beta), ln Z / N = ln 2 + 3 ln cosh(beta)
+    + 3 t^4 + O(t^6) on the simple cubic lattice (three elementary squares per
+    site; no closed graph has fewer bonds), so the energy per site is
+    u = -3 t - 12 t^3 (1 - t^2) + O(t^5).  The t^3 term is 5x the acceptance
+    band here, so a dropped or misplaced z coupling fails; the band adds
+    200 t^5 for the next term (6 a_6 t^5 with a_6, the six-bond closed graphs
+    per site, well below 33)."""
+    L, nsweeps, burn = 16, 60_000, 500
+    t = math.tanh(beta)
+    want = -3.0 * t - 12.0 * t ** 3 * (1.0 - t * t)
+    _, E, _ = orc.run(3, L, beta, 555 + int(1000 * beta), nsweeps, measure_every=1)
+    u = E[burn:].astype(np.float64) / L ** 3
+    _check(u, want, f"u_3D({beta})", extra=200.0 * t ** 5)
+    # the t^3 term is resolved: the first-order value alone is rejected
+    err = exact.blocking_error(u)
+    assert abs(float(np.mean(u)) - (-3.0 * t)) > Z5 * err + 200.0 * t ** 5
