@@ -19,7 +19,7 @@
  *     accept iff R <= exp(-dE/kT)                                         (Sec. 2.2)
  *   - expected value E(F) = sum_i F(S_i) P(S_i) with Boltzmann P          (Eq. 1)
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent:
  *   - one "sweep" here is a black pass followed by a white pass, so every
  *     site is visited once per sweep; colour c(x,y[,z]) = (x+y[+z]) mod 2,
  *     black = colour 0;
