@@ -188,6 +188,17 @@ int ising_observables_async(ising_lattice *lat, int64_t *pairs, int64_t cap, int
 int ising_observables_gather(ising_lattice *const *lats, int n, int64_t *pairs, int64_t cap,
                              int64_t *counts);
 
+/*
+ * ising_observables_gather, and then the device stores `value` into *flag
+ * (pinned host memory, as for `pairs`) after the records are in place and
+ * visible to the host: a host that reads `value` there may read the records
+ * without an event or a synchronisation (the flag is written even when no
+ * record is pending).  ISING_EINVAL also for a flag that is not
+ * device-writable host memory.
+ */
+int ising_observables_gather_signal(ising_lattice *const *lats, int n, int64_t *pairs,
+                                    int64_t cap, int64_t *counts, int64_t *flag, int64_t value);
+
 /* Copy the spins to host memory in canonical order (L^dims int8).  Syncs. */
 int ising_get_spins(ising_lattice *lat, int8_t *host_out);
 

@@ -217,9 +217,12 @@ int check_timeout(ising_lattice* h) {
     return ISING_ETIMEOUT;
 }
 
-// Records of several lattices in one launch (ising_observables_gather): CTA i
-// copies lattice i's pending (E, M) pairs to `out` (mapped pinned host memory)
-// at its offset and zeroes them, restoring the zero invariant of the slots.
+// Records of several lattices in one launch (ising_observables_gather): one
+// CTA walks the chunk's lattices, copies each one's pending (E, M) pairs to
+// `out` (mapped pinned host memory) at its offset and zeroes them, restoring
+// the zero invariant of the slots; then, if `flag` is set, it stores `value`
+// there (mapped pinned host memory too) after a system-scope fence, so a host
+// that sees the value also sees the records.
 constexpr int kGatherChunk = 64;
 struct GatherChunk {
     unsigned long long* src[kGatherChunk];
@@ -228,15 +231,24 @@ struct GatherChunk {
     int count;
 };
 
-__global__ void gather_records_kernel(GatherChunk c, long long* out) {
+__global__ void gather_records_kernel(GatherChunk c, long long* out, long long* flag,
+                                      long long value) {
     grid_dependency_wait();  // the sweeps that wrote the records have completed
     launch_dependents();
-    const int i = blockIdx.x;
-    unsigned long long* src = c.src[i];
-    long long* dst = out + 2 * c.off[i];
-    for (int64_t j = threadIdx.x; j < 2 * c.n[i]; j += blockDim.x) {
-        dst[j] = (long long)src[j];
-        src[j] = 0ull;
+    for (int i = 0; i < c.count; ++i) {
+        unsigned long long* src = c.src[i];
+        long long* dst = out + 2 * c.off[i];
+        for (int64_t j = threadIdx.x; j < 2 * c.n[i]; j += blockDim.x) {
+            dst[j] = (long long)src[j];
+            src[j] = 0ull;
+        }
+    }
+    if (flag) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence_system();
+            *reinterpret_cast<volatile long long*>(flag) = value;
+        }
     }
 }
 
@@ -460,8 +472,21 @@ int ising_observables_async(ising_lattice* h, int64_t* pairs, int64_t cap, int64
     return ISING_OK;
 }
 
-int ising_observables_gather(ising_lattice* const* lats, int n, int64_t* pairs, int64_t cap,
-                             int64_t* counts) {
+// The device pointer of mapped pinned host memory, or nullptr if `p` is not
+// device-writable host memory.
+static long long* mapped_host(void* p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (attr.type != cudaMemoryTypeHost || !attr.devicePointer) return nullptr;
+    return static_cast<long long*>(attr.devicePointer);
+}
+
+int ising_observables_gather_signal(ising_lattice* const* lats, int n, int64_t* pairs,
+                                    int64_t cap, int64_t* counts, int64_t* flag,
+                                    int64_t value) {
     if (!lats || n < 1 || !counts) return ISING_EINVAL;
     int64_t total = 0;
     for (int i = 0; i < n; ++i) {
@@ -470,18 +495,12 @@ int ising_observables_gather(ising_lattice* const* lats, int n, int64_t* pairs, 
     }
     if (total > 0 && !pairs) return ISING_EINVAL;
     if (total > cap) return ISING_ERANGE;
+    // the kernel writes the host buffers directly: they must be pinned (mapped)
     long long* out = nullptr;
-    if (total > 0) {
-        // the kernel writes the host buffer directly: it must be pinned (mapped)
-        cudaPointerAttributes attr;
-        if (cudaPointerGetAttributes(&attr, pairs) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return ISING_EINVAL;
-        }
-        if (attr.type != cudaMemoryTypeHost || !attr.devicePointer) return ISING_EINVAL;
-        out = static_cast<long long*>(attr.devicePointer);
-    }
-    if (total == 0) {
+    if (total > 0 && !(out = mapped_host(pairs))) return ISING_EINVAL;
+    long long* dflag = nullptr;
+    if (flag && !(dflag = mapped_host(flag))) return ISING_EINVAL;
+    if (total == 0 && !dflag) {
         for (int i = 0; i < n; ++i) counts[i] = 0;
         return ISING_OK;
     }
@@ -499,13 +518,22 @@ int ising_observables_gather(ising_lattice* const* lats, int n, int64_t* pairs, 
             off += h->n_rec;
             h->n_rec = 0;
         }
-        if (chunk.count == kGatherChunk || (i == n - 1 && chunk.count > 0)) {
-            ISING_CHECK(launch_chained(gather_records_kernel, (unsigned)chunk.count, 64u, 0,
-                                       lats[0]->stream, chunk, out));
+        // the last launch (possibly with no records) carries the flag
+        const bool last = i == n - 1;
+        if (chunk.count == kGatherChunk || last) {
+            if (chunk.count > 0 || (last && dflag))
+                ISING_CHECK(launch_chained(gather_records_kernel, 1u, 256u, 0, lats[0]->stream,
+                                           chunk, out, last ? dflag : nullptr,
+                                           (long long)value));
             chunk.count = 0;
         }
     }
     return ISING_OK;
+}
+
+int ising_observables_gather(ising_lattice* const* lats, int n, int64_t* pairs, int64_t cap,
+                             int64_t* counts) {
+    return ising_observables_gather_signal(lats, n, pairs, cap, counts, nullptr, 0);
 }
 
 int ising_export_device(ising_lattice* h, int8_t* dev_out) {

@@ -77,6 +77,9 @@ def load_library():
             "ising_observables_async": ([P, P, ctypes.c_int64, i64p], ctypes.c_int),
             "ising_observables_gather": ([ctypes.POINTER(P), ctypes.c_int, P, ctypes.c_int64,
                                           i64p], ctypes.c_int),
+            "ising_observables_gather_signal": ([ctypes.POINTER(P), ctypes.c_int, P,
+                                                 ctypes.c_int64, i64p, P, ctypes.c_int64],
+                                                ctypes.c_int),
             "ising_get_spins": ([P, P], ctypes.c_int),
             "ising_set_spins": ([P, P, ctypes.c_uint64], ctypes.c_int),
             "ising_export_device": ([P, P], ctypes.c_int),
@@ -392,13 +395,16 @@ def batch_run_static(lattices, sweeps, measure_every, records_ptr: int, records_
            "ising_batch_run_static")
 
 
-def observables_gather(lattices, pairs: np.ndarray, counts: np.ndarray | None = None) -> np.ndarray:
+def observables_gather(lattices, pairs: np.ndarray, counts: np.ndarray | None = None,
+                       flag: np.ndarray | None = None, value: int = 0) -> np.ndarray:
     """``ising_observables_gather``: enqueue, with one kernel on the lattices'
     common stream, the copy of every lattice's pending (E, M) records into
     ``pairs`` (a pinned int64 array of shape (cap, 2), written by the device
     directly) and clear them.  Returns the per-lattice record counts at once;
     lattice i's records start at row counts[:i].sum().  The values are valid
-    once the stream passes this point (e.g. an event recorded next)."""
+    once the stream passes this point (e.g. an event recorded next), or, with
+    ``flag`` (a one-element view of a pinned int64 array), once the device has
+    stored ``value`` there (``ising_observables_gather_signal``)."""
     lib = load_library()
     assert pairs.dtype == np.int64 and pairs.flags.c_contiguous
     n = len(lattices)
@@ -406,8 +412,17 @@ def observables_gather(lattices, pairs: np.ndarray, counts: np.ndarray | None = 
         counts = np.zeros(n, dtype=np.int64)
     assert counts.dtype == np.int64 and counts.size >= n and counts.flags.c_contiguous
     handles = (ctypes.c_void_p * n)(*[lat.handle for lat in lattices])
-    _check(lib.ising_observables_gather(handles, n, ctypes.c_void_p(pairs.ctypes.data),
-                                        pairs.size // 2,
-                                        counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
-           "ising_observables_gather")
+    cnt = counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    if flag is None:
+        _check(lib.ising_observables_gather(handles, n, ctypes.c_void_p(pairs.ctypes.data),
+                                            pairs.size // 2, cnt),
+               "ising_observables_gather")
+    else:
+        assert flag.dtype == np.int64 and flag.size >= 1
+        _check(lib.ising_observables_gather_signal(handles, n,
+                                                   ctypes.c_void_p(pairs.ctypes.data),
+                                                   pairs.size // 2, cnt,
+                                                   ctypes.c_void_p(flag.ctypes.data),
+                                                   int(value)),
+               "ising_observables_gather_signal")
     return counts

@@ -130,3 +130,13 @@ def test_observables_gather_rejects_bad_arguments_on_the_host(lib):
     assert lib.ising_observables_gather(none2, 0, pairs, 4, counts) == -1
     assert lib.ising_observables_gather(none2, 2, pairs, 4, counts) == -1  # NULL lattices
     assert lib.ising_observables_gather(none2, 2, pairs, 4, None) == -1
+
+
+def test_observables_gather_signal_rejects_bad_arguments_on_the_host(lib):
+    counts = (ctypes.c_int64 * 2)()
+    pairs = (ctypes.c_int64 * 8)()
+    flag = (ctypes.c_int64 * 1)()
+    none2 = (ctypes.c_void_p * 2)(None, None)
+    assert lib.ising_observables_gather_signal(None, 1, pairs, 4, counts, flag, 1) == -1
+    assert lib.ising_observables_gather_signal(none2, 0, pairs, 4, counts, flag, 1) == -1
+    assert lib.ising_observables_gather_signal(none2, 2, pairs, 4, counts, flag, 1) == -1

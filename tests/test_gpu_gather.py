@@ -106,3 +106,41 @@ def test_gather_refusals(eng):
     assert list(counts) == [3, 3]
     for x in (a, b, c):
         x.close()
+
+
+def test_gather_signal_flag(eng):
+    """ising_observables_gather_signal: once the host sees the value in the
+    pinned flag word, the records are in place -- read here before any
+    synchronisation -- and equal the twins' per-lattice reads."""
+    import time
+    import torch
+    lats = [make(eng, c) for c in CASES[:4]]
+    twins = [make(eng, c) for c in CASES[:4]]
+    pairs = torch.zeros((64, 2), dtype=torch.int64).pin_memory().numpy()
+    flag = torch.zeros(2, dtype=torch.int64).pin_memory().numpy()
+    for k in (1, 2, 3):
+        for lat, twin, c in zip(lats, twins, CASES):
+            lat.sweep(c[5], c[6])
+            twin.sweep(c[5], c[6])
+        counts = eng.observables_gather(lats, pairs, flag=flag[1:], value=k)
+        t0 = time.monotonic()
+        while flag[1] != k:
+            assert time.monotonic() - t0 < 30.0, "the flag never arrived"
+        got = pairs[:int(counts.sum())].copy()  # before any synchronisation
+        off = 0
+        for c_k, twin in zip(counts, twins):
+            E, M = twin.observables()
+            assert c_k == len(E)
+            assert np.array_equal(got[off:off + c_k, 0], E)
+            assert np.array_equal(got[off:off + c_k, 1], M)
+            off += int(c_k)
+    # nothing pending: the flag still arrives
+    counts = eng.observables_gather(lats, pairs, flag=flag[1:], value=99)
+    torch.cuda.synchronize()
+    assert flag[1] == 99 and not counts.any()
+    assert flag[0] == 0  # the neighbouring word is untouched
+    with pytest.raises(eng.IsingError) as ei:
+        eng.observables_gather(lats, pairs, flag=np.zeros(1, dtype=np.int64), value=1)
+    assert ei.value.code == eng.EINVAL
+    for x in lats + twins:
+        x.close()
