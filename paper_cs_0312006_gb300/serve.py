@@ -80,7 +80,7 @@ class Server:
     def __init__(self, hbm_budget_bytes: int = 120 * 10 ** 9, max_resident: int = 4096,
                  round_s: float = 0.05, min_quantum: int = 1, keep_spins: bool = True,
                  batch_opts: dict | None = None, stream=None, clock=time.perf_counter,
-                 lattice_factory=None, batch_factory=None):
+                 lattice_factory=None, batch_factory=None, gather_records=None):
         self.budget = int(hbm_budget_bytes)
         self.max_resident = max_resident
         self.round_s = float(round_s)
@@ -94,6 +94,9 @@ class Server:
         # the engine by default; tests of the scheduling logic pass stand-ins
         self.lattice_factory = lattice_factory or engine.Lattice
         self.batch_factory = batch_factory or engine.Batch
+        # records through one gather per round (engine lattices on one stream)
+        self.gather_records = (self.lattice_factory is engine.Lattice
+                               if gather_records is None else bool(gather_records))
         self.pending: list[Job] = []
         self.resident: list[_Resident] = []
         self.results: dict[int, JobResult] = {}
@@ -185,17 +188,21 @@ class Server:
                 still.append(r)
         self.resident = still
 
+    def _alloc_pinned(self, cap: int) -> np.ndarray:
+        """A (cap, 2) int64 host buffer the device can write (pinned)."""
+        import torch
+        return torch.zeros((cap, 2), dtype=torch.int64).pin_memory().numpy()
+
     def _read_records(self, lats) -> list:
         """Every resident lattice's pending (E, M) records: engine lattices (one
         stream) through one ising_observables_gather into a pinned buffer and
         one synchronisation; stand-ins one by one."""
-        if self.lattice_factory is not engine.Lattice or not lats:
+        if not self.gather_records or not lats:
             return [lat.observables() for lat in lats]
-        import torch
         while True:
             if self._pinned is None or self._pinned_grow:
                 cap = max(1024, 2 * (0 if self._pinned is None else len(self._pinned)))
-                self._pinned = torch.zeros((cap, 2), dtype=torch.int64).pin_memory().numpy()
+                self._pinned = self._alloc_pinned(cap)
                 self._pinned_grow = False
             try:
                 counts = engine.observables_gather(lats, self._pinned)

@@ -142,3 +142,71 @@ def test_workload_generators():
     assert all(100 <= j.spec.sweeps <= 20000 for j in jobs)
     scan = workloads.beta_scan_2d()
     assert [round(s.beta, 2) for s in scan] == [round(0.30 + 0.02 * j, 2) for j in range(16)]
+
+
+class GatherLattice(FakeLattice):
+    """A stand-in that also answers the gather path's calls."""
+    syncs = 0
+
+    @property
+    def handle(self):
+        return id(self)
+
+    def synchronize(self):
+        GatherLattice.syncs += 1
+
+
+def fake_gather(lats, pairs, counts=None):
+    """ising_observables_gather's contract on the host: ERANGE (nothing
+    taken) when the buffer is too small, else every lattice's pending records
+    in order, cleared."""
+    from paper_cs_0312006_gb300 import engine
+    total = sum(len(lat.E) for lat in lats)
+    if total > len(pairs):
+        raise engine.IsingError(engine.ERANGE, "ising_observables_gather")
+    counts = np.zeros(len(lats), dtype=np.int64)
+    off = 0
+    for i, lat in enumerate(lats):
+        E, M = lat.observables()
+        counts[i] = len(E)
+        pairs[off:off + len(E), 0] = E
+        pairs[off:off + len(E), 1] = M
+        off += len(E)
+    return counts
+
+
+def test_records_gather_grows_its_buffer_and_matches_per_lattice_reads(monkeypatch):
+    """The gather path of a round: one read for all resident jobs into a host
+    buffer that doubles on ERANGE (nothing lost), one synchronisation, and
+    the same per-job records as the one-by-one path."""
+    monkeypatch.setattr(serve.engine, "observables_gather", fake_gather)
+
+    class HostServer(serve.Server):
+        allocs = []
+
+        def _alloc_pinned(self, cap):
+            HostServer.allocs.append(cap)
+            return np.zeros((cap, 2), dtype=np.int64)
+
+    def jobs():
+        out = []
+        for k in range(40):
+            spec = workloads.LatticeSpec(dims=2, L=64, beta=0.4, seed=k, sweeps=3000,
+                                         measure_every=1, layout=0, start=0)
+            out.append(workloads.Job(job_id=k, arrival_s=0.0, spec=spec))
+        return out
+
+    results = {}
+    for gather in (False, True):
+        GatherLattice.syncs = 0
+        srv = HostServer(lattice_factory=GatherLattice, batch_factory=FakeBatch, clock=Clock(),
+                         gather_records=gather, round_s=1.0, min_quantum=100)
+        srv.run(jobs())
+        results[gather] = srv.results
+        if gather:
+            assert HostServer.allocs[0] == 1024 and HostServer.allocs[-1] > 1024
+            assert GatherLattice.syncs == srv.rounds
+    for k, r in results[False].items():
+        g = results[True][k]
+        assert np.array_equal(r.E, g.E) and np.array_equal(r.M, g.M)
+        assert len(g.E) == 3000
