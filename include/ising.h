@@ -141,7 +141,11 @@ int ising_init(ising_lattice *lat, int start);
  * After sweep number u the fused kernels record (E, M) iff
  * (u + 1) % measure_every == 0 (measure_every >= 1).  Asynchronous on the
  * handle's stream; may grow the device record buffer.  ISING_ERANGE if the
- * counter would pass 2^32 - 1.
+ * counter would pass 2^32 - 1.  The colour passes are launched with
+ * programmatic stream serialisation: a pass may be scheduled while the kernel
+ * before it in the stream drains, and touches no memory until that kernel has
+ * completed, so stream order holds as for ordinary launches (an event or a
+ * copy between two passes only keeps them from overlapping their launch).
  */
 int ising_sweep(ising_lattice *lat, int64_t n, int measure_every);
 
