@@ -560,6 +560,27 @@ void ising_batch_destroy(ising_batch* b) {
     free_batch(b);
 }
 
+int ising_batch_run(ising_lattice* const* lats, int n, const int64_t* sweeps, int measure_every,
+                    void* stream) {
+    if (measure_every < 1 || n < 1) return ISING_EINVAL;
+    std::vector<int> every;
+    try {
+        every.assign((size_t)n, measure_every);
+    } catch (const std::bad_alloc&) {
+        return ISING_ENOMEM;
+    }
+    // one launch: a plain launch rather than a graph captured for one replay
+    ising_batch_opts o = {};
+    o.use_graph = -1;
+    ising_batch* b = nullptr;
+    int rc = ising_batch_create(&b, lats, n, sweeps, every.data(), &o, stream);
+    if (rc != ISING_OK) return rc;
+    rc = ising_batch_launch(b);
+    const int rs = ising_batch_sync(b);
+    ising_batch_destroy(b);
+    return rc != ISING_OK ? rc : rs;
+}
+
 int ising_batch_info(const ising_batch* b, int* grid, int* n_big, int* n_small, int* n_huge) {
     if (!b) return ISING_EINVAL;
     if (grid) *grid = b->q[0].grid > b->q[1].grid ? b->q[0].grid : b->q[1].grid;
@@ -656,6 +677,9 @@ int ising_batch_run_static(ising_lattice* const* lats, int n, const int64_t* swe
         if (!h || sweeps[i] < 0 || sweeps[i] > 0x7FFFFFFF) return ISING_EINVAL;
         if (h->rule == ISING_RULE_DEMON || h->rule == ISING_RULE_MULTIHIT)
             return ISING_EINVAL;  // not in the persistent kernel
+        // stream order is the only ordering against the handle's own work
+        // (earlier sweeps, later reads): the lattice must already be on `stream`
+        if (h->stream != static_cast<cudaStream_t>(stream)) return ISING_EINVAL;
         const int every = measure_every ? measure_every[i] : 1;
         if (every < 1) return ISING_EINVAL;
         if (sweeps[i] > 0 && h->t + (uint64_t)sweeps[i] - 1 > kMaxSweep) return ISING_ERANGE;

@@ -198,11 +198,6 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kStages];
     __shared__ uint32_t s_thb[8];  // heat bath: thr[d] by d, read per site
-    if (RULE == kRuleHeatBath && threadIdx.x == 0) {
-#pragma unroll
-        for (int i = 0; i < 7; ++i) s_thb[i] = a.thr[i];
-        s_thb[7] = 0u;
-    }
     const uint32_t W = (uint32_t)a.W, R = (uint32_t)tg.R;
     const uint32_t nv = W >> 4;
     // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -213,6 +208,11 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     grid_dependency_wait();  // the previous pass has completed (no global access before)
+    if (RULE == kRuleHeatBath && threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) s_thb[i] = a.thr[i];
+        s_thb[7] = 0u;
+    }
     __syncthreads();
     launch_dependents();
     if (threadIdx.x == 0)

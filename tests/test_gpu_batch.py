@@ -142,3 +142,32 @@ def test_batch_rejects_bad_arguments(eng):
     with pytest.raises(eng.IsingError):
         eng.Batch([lat], [1], measure_every=[0])
     lat.close()
+
+
+def test_batch_run_one_call_against_oracle(eng):
+    """ising_batch_run (create + launch + sync + destroy in one call): every
+    lattice's spins and E/M records equal the oracle's own run."""
+    specs = [(2, 64, 0.4406868, 20031109, INT8, 12, 1),
+             (2, 128, 0.35, 7, BITPACK, 9, 1),
+             (3, 16, 0.2216544, 5, INT8, 10, 1),
+             (2, 34, 0.55, 3, INT8, 11, 1),
+             (3, 8, 0.3, 9, BITPACK, 7, 1)]
+    lats = [eng.Lattice(d, L, b, sd, layout=lay) for (d, L, b, sd, lay, _, _) in specs]
+    eng.batch_run(lats, [sp[5] for sp in specs], 1)
+    for lat, (d, L, b, sd, lay, n, every) in zip(lats, specs):
+        E, M = lat.observables()
+        s = lat.get_spins()
+        lat.close()
+        s_o, E_o, M_o = oracle.run(d, L, b, sd, n, measure_every=every)
+        assert np.array_equal(E, E_o) and np.array_equal(M, M_o), (d, L)
+        assert np.array_equal(s, s_o), (d, L)
+
+
+def test_batch_run_refusals(eng):
+    lat = eng.Lattice(2, 32, 0.4, 1)
+    for args in (([lat], [1], 0), ([lat, lat], [1, 1], 1), ([lat], [-1], 1)):
+        with pytest.raises(eng.IsingError) as ei:
+            eng.batch_run(*args)
+        assert ei.value.code == eng.EINVAL
+    assert lat.info().sweeps_done == 0
+    lat.close()

@@ -108,3 +108,36 @@ def test_static_batch_rejects_too_many_or_too_little_room(eng):
     assert ei.value.code == eng.ERANGE
     assert lat.info().sweeps_done == 0  # nothing was issued
     lat.close()
+
+
+def test_static_batch_refuses_lattices_on_another_stream(eng):
+    """The call is ordered against a handle's own work by stream order alone,
+    so lattices must already be on the call's stream: a lattice on a side
+    stream is refused with nothing issued, and the same call on that stream
+    gives the allocating batch's result."""
+    import torch
+    side = torch.cuda.Stream()
+    spec = SPECS[0]
+    lat = eng.Lattice(*spec[:5])
+    lat.set_stream(side)
+    rec = torch.zeros((spec[5] + 1, 2), dtype=torch.int64, device="cuda")
+    with pytest.raises(eng.IsingError) as ei:
+        eng.batch_run_static([lat], spec[5], spec[6], rec.data_ptr(), spec[5] + 1,
+                             stream=torch.cuda.default_stream())
+    assert ei.value.code == eng.EINVAL
+    assert lat.info().sweeps_done == 0
+    with torch.cuda.stream(side):
+        rec.zero_()
+    eng.batch_run_static([lat], spec[5], spec[6], rec.data_ptr(), spec[5] + 1, stream=side)
+    side.synchronize()
+    got = rec.cpu().numpy()[:spec[5]]
+    ref = eng.Lattice(*spec[:5])
+    batch = eng.Batch([ref], [spec[5]], [spec[6]])
+    batch.launch()
+    batch.sync()
+    E, M = ref.observables()
+    batch.close()
+    assert np.array_equal(got[:, 0], E) and np.array_equal(got[:, 1], M)
+    assert np.array_equal(lat.get_spins(), ref.get_spins())
+    lat.close()
+    ref.close()
