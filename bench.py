@@ -348,13 +348,6 @@ def _reference_line(args, world, L, dt, what):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def philox_alu_peak_sites_per_s(sm_count: int, sm_mhz: float) -> float:
-    """Integer-pipe ceiling of a pass: one Philox4x32-10 call per 4 sites needs
-    18 non-uniform 32x32->64-bit multiplies, and an SM retires 32 of them per
-    clock (measured on this GPU with a Philox-only kernel)."""
-    return sm_count * (32.0 / 18.0) * 4.0 * sm_mhz * 1e6
-
-
 def run_gpu(args, world, rank, local):
     import torch
 
@@ -446,16 +439,21 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    ms = max_over_ranks(start.elapsed_time(stop), world, device="cuda")
+    ms_all = max_over_ranks(start.elapsed_time(stop), world, device="cuda")
     per_layout_updates = world * len(betas) * n_sites * args.steps
-    value = per_layout_updates * len(sets) / (ms / 1e3)
+    # the headline is the int8 layout's whole job (its own bracket of events),
+    # the other layout is reported beside it
+    head = "int8" if "int8" in sets else next(iter(sets))
+    ms = max_over_ranks(marks[head][0].elapsed_time(marks[head][1]), world, device="cuda")
+    value = per_layout_updates / (ms / 1e3)
     for lats in sets.values():  # every step recorded one (E, M) per lattice
         n_rec = [len(lat.observables()[0]) for lat in lats]
         assert all(n == args.steps for n in n_rec), n_rec
 
     peak_hbm, peak_kind = load_peaks()
-    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    # the integer ceiling: the device generator alone, measured here (outside
+    # the timed region) -- every site with dE > 0 needs one 32-bit draw
+    ceiling = measure_philox_ceiling(engine, torch)
     layout_stats = {}
     rooflines = {}
     for name in sets:
@@ -481,13 +479,16 @@ def run_gpu(args, world, rank, local):
             rtag = "" if args.rule == "metropolis" else ",heatbath"
             kname = (f"pass_int8_tma<2,measure{rtag}>" if int8_ran == engine.KERNEL_TMA else
                      f"pass_int8_strip<2,measure{rtag}>")
+            upd_s = updates_per_pass / (pass_ms / 1e3)
             rooflines[name] = {"kernel": kname, "bound": "hbm",
                                "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                                "frac": achieved / peak_hbm,
                                "traffic": measured_traffic(args.workload, "int8",
                                                            updates_per_pass, args.rule),
                                "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
-                               "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+                               "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                               "philox_ceiling_updates_per_s": ceiling["draws_per_s"],
+                               "frac_of_philox_ceiling": upd_s / ceiling["draws_per_s"]}
         elif args.rule == "demon":  # bit-packed demons: 7 bits per update, no draws
             bytes_per_pass = BYTES_PER_UPDATE_DEMON_PACKED * updates_per_pass
             achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
@@ -501,7 +502,7 @@ def run_gpu(args, world, rank, local):
                                "bytes_per_launch": bytes_per_pass, "launch_ms": pass_ms,
                                "peak_source": f"{peak_kind} hbm_gbs (copy)"}
         else:
-            peak = philox_alu_peak_sites_per_s(sm_count, sm_mhz)
+            peak = ceiling["draws_per_s"]
             achieved = updates_per_pass / (pass_ms / 1e3)
             rtag = "" if args.rule == "metropolis" else ",heatbath"
             rooflines[name] = {"kernel": f"pass_packed<2,measure{rtag}>", "bound": "alu",
@@ -510,58 +511,67 @@ def run_gpu(args, world, rank, local):
                                "traffic": measured_traffic(args.workload, "bitpack",
                                                            updates_per_pass, args.rule),
                                "launch_ms": pass_ms,
-                               "peak_source": "derived: SMs x 32 wide multiplies/clk / 18 per "
-                                              "Philox call x 4 sites x median SM clock"}
+                               "peak_source": "measured in this run: Philox4x32-10 calls/s of "
+                                              "the generator alone (ising_philox_probe) x 4 "
+                                              "draws per call (one draw per site update)"}
 
     # ---------------- end to end through the C ABI, host buffers ----------------
     e2e = None
     if not args.no_e2e:
-        host_init = torch.ones(n_sites, dtype=torch.int8).pin_memory().numpy()
-        host_out = torch.empty(n_sites, dtype=torch.int8).pin_memory().numpy()
+        e2e = {}
         e2e_steps = args.e2e_steps or args.steps
-        # step k's (E, M) pairs land in one half of a pinned double buffer and
-        # are read (summed) on the host while step k + 1 runs on the device
+        # every lattice's initial spins and final spins live in pinned host
+        # memory, which the import and export kernels read and write directly
+        # (ising_set_spins_async / ising_get_spins_async); step k's (E, M)
+        # pairs land in one half of a pinned double buffer (one gather kernel)
+        # and are summed on the host while step k + 1 runs on the device
+        host_init = torch.ones(n_sites, dtype=torch.int8).pin_memory()
+        host_out = [torch.empty(n_sites, dtype=torch.int8).pin_memory() for _ in betas]
         pairs = torch.zeros((2, len(betas), 2), dtype=torch.int64).pin_memory().numpy()
         ready = [torch.cuda.Event(), torch.cuda.Event()]
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        d2h = 0
-        host_sum = 0
-        for lats in sets.values():
+        for name, lats in sets.items():
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h2d = d2h = 0
+            host_sum = 0
             for lat in lats:
-                lat.set_spins(host_init, 0)  # H2D of the initial configuration
+                lat.set_spins_async(host_init.data_ptr(), 0)  # H2D: the initial configuration
+                h2d += n_sites
             last = None
             for k in range(e2e_steps):
                 for lat in lats:
                     lat.sweep(1, 1)
                 half = k % 2
-                # D2H of every lattice's (E, M): one gather kernel writes them
-                # into the pinned buffer
                 d2h += 16 * int(engine.observables_gather(lats, pairs[half]).sum())
                 ready[half].record(stream)
                 if last is not None:
                     ready[last].synchronize()
                     host_sum += int(pairs[last, :, 0].sum())
                 last = half
-            ready[last].synchronize()
-            host_sum += int(pairs[last, :, 0].sum())
-            for lat in lats:
-                lat.get_spins(host_out)  # D2H of the final configuration
+            for lat, buf in zip(lats, host_out):
+                lat.get_spins_async(buf.data_ptr())  # D2H: the final configuration
                 d2h += n_sites
-        torch.cuda.synchronize()
-        dt = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
-        for lats in sets.values():
+            torch.cuda.synchronize()
+            host_sum += int(pairs[last, :, 0].sum())
+            dt = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
             for lat in lats:
-                lat.synchronize()  # a bounded wait that gave up would be reported here
-        h2d_total = len(sets) * len(betas) * n_sites
-        e2e = {"value": world * len(sets) * len(betas) * n_sites * e2e_steps / dt,
-               "unit": "site updates/s", "h2d_bytes_per_step": h2d_total / e2e_steps,
-               "d2h_bytes_per_step": d2h / e2e_steps, "steps": e2e_steps,
-               "note": "per layout: ising_set_spins from pinned host memory, then per step one "
-                       "sweep of each lattice and one ising_observables_gather of every "
-                       "lattice's (E, M) into pinned host memory, read on the host while the "
-                       "next step runs, then ising_get_spins"}
+                lat.synchronize()  # a bounded wait or an invalid input would be reported here
+            e2e[name] = {"value": world * len(betas) * n_sites * e2e_steps / dt,
+                         "seconds": dt, "h2d_bytes": h2d, "d2h_bytes": d2h,
+                         "h2d_bytes_per_step": h2d / e2e_steps,
+                         "d2h_bytes_per_step": d2h / e2e_steps}
+        head_e2e = e2e[head]
+        e2e = {"value": head_e2e["value"], "unit": "site updates/s",
+               "h2d_bytes_per_step": head_e2e["h2d_bytes_per_step"],
+               "d2h_bytes_per_step": head_e2e["d2h_bytes_per_step"], "steps": e2e_steps,
+               "layout": head, "layouts": e2e,
+               "over_device_value": head_e2e["value"] / value,
+               "note": "per layout: ising_set_spins_async of every lattice from pinned host "
+                       "memory, then per step one sweep of each lattice and one "
+                       "ising_observables_gather of every lattice's (E, M) into pinned host "
+                       "memory (read on the host while the next step runs), then "
+                       "ising_get_spins_async of every lattice into pinned host memory"}
 
     for lats in sets.values():
         for lat in lats:
@@ -581,6 +591,11 @@ def run_gpu(args, world, rank, local):
         cpu = {"value": rate, "unit": "site updates/s", "cores": 1, "kind": "oracle",
                "sample": sample, "host": host_description()}
 
+    forms = {}
+    if world == 1 and not args.no_forms and args.rule == "metropolis":
+        forms["batched"] = batched_form(args)
+        forms["serving"] = serving_form(args)
+
     line = {
         "metric": "site updates/s", "value": value, "unit": "site updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -591,19 +606,80 @@ def run_gpu(args, world, rank, local):
         "pass_timing": f"CUDA events around each lattice's sweep on every {every}th step of "
                        f"the timed region (the events sit between sweeps, so fewer of them "
                        f"disturb the chained launches less)",
+        "headline_layout": head,
         "layouts": layout_stats,
+        "both_layouts": {"value": per_layout_updates * len(sets) / (ms_all / 1e3),
+                         "ms": ms_all},
         "roofline": rooflines.get("int8") or rooflines.get("bitpack"),
         "roofline_bitpack": rooflines.get("bitpack"),
-        "gpu_launches": len(sets) * len(betas) * (2 * args.steps + 1),
+        "philox_ceiling": ceiling,
+        "gpu_launches": len(sets) * len(betas) * 2 * args.steps,
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
+    line.update(forms)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def batched_form(args) -> dict:
+    """The batched form on its full workload (2048 lattices x 500 sweeps):
+    one persistent launch against one ising_sweep per lattice (one stream and
+    eight streams); every lattice bit-identical across the forms."""
+    import torch
+    from paper_cs_0312006_gb300 import autotune, batched, engine, workloads
+    specs = workloads.batched_mix(n=args.batch_lattices, sweeps=args.batch_sweeps)
+    tuned = autotune.tune(specs, use_cache=not args.retune)
+    opts, layout = tuned["opts"], tuned["layout"]
+    batched.run_batched(batched.scaled(specs[:64], 2), opts, 1, layout)  # warm-up
+    res = batched.compare_forms(specs, opts, layout)
+    if res["mismatches"]:
+        raise SystemExit(f"batched and plain forms differ on {res['mismatches']} lattices")
+    return {"config": {"workload": f"batched: {res['lattices']} lattices, {args.batch_sweeps} "
+                                   "sweeps each, 70% 2D L log-uniform [16,1024] beta U[0.2,0.6], "
+                                   "30% 3D L log-uniform [8,128] beta U[0.15,0.30], hot start, "
+                                   "E/M every 10 sweeps"},
+            "value": res["batched_updates_per_s"], "unit": "site updates/s",
+            "plain_value": res["plain_updates_per_s"],
+            "batched_over_plain": res["batched_over_plain"],
+            "batched_over_plain_8_streams": res["batched_over_plain_8_streams"],
+            "detail": res,
+            "autotune": {"opts": opts, "layout": layout, "candidates": len(tuned["results"]),
+                         "choice": tuned.get("choice")}}
+
+
+def serving_form(args) -> dict:
+    """The serving form on its full workload (Poisson job stream) against the
+    plain form (each job alone through ising_sweep, in arrival order)."""
+    from paper_cs_0312006_gb300 import serve, workloads
+    jobs = workloads.poisson_jobs(args.serve_jobs, rate_per_s=args.serve_rate)
+    warm = workloads.poisson_jobs(8, rate_per_s=1e6, seed=99, l2d=(32, 128), l3d=(16, 32),
+                                  sweeps=(10, 20))
+    serve.Server(round_s=args.round_s).run(warm)  # load and warm the kernels
+    srv = serve.Server(hbm_budget_bytes=int(args.hbm_budget_gb * 1e9), round_s=args.round_s,
+                       keep_spins=False)
+    summ = srv.run(jobs)
+    skip = max(0, len(jobs) // 10)
+    pct = serve.percentile_summary(srv.results, skip)
+    psum, pres = serve.run_plain_fifo(jobs)
+    plain = dict(psum, **serve.percentile_summary(pres, skip))
+    return {"config": {"workload": f"serving: {len(jobs)} Poisson jobs at {args.serve_rate}/s, "
+                                   "dims 2/3, L log-uniform (2D 32-4096, 3D 16-256), beta_c +- "
+                                   "0.05, sweeps log-uniform 100-20000, E/M every 10, HBM budget "
+                                   f"{args.hbm_budget_gb} GB; first {skip} jobs left out of the "
+                                   "percentiles"},
+            "value": summ["updates_per_s"], "unit": "site updates/s",
+            "p50_latency_s": pct["p50_latency_s"], "p99_latency_s": pct["p99_latency_s"],
+            "plain_value": plain["updates_per_s"],
+            "plain_p50_latency_s": plain["p50_latency_s"],
+            "plain_p99_latency_s": plain["p99_latency_s"],
+            "served_over_plain": summ["updates_per_s"] / plain["updates_per_s"],
+            "offered_load_updates_per_s": serve.offered_load(jobs, args.serve_rate),
+            "detail": dict(summ, **pct)}
 
 
 def run_batched_workload(args):
@@ -842,33 +918,53 @@ def run_percolation_workload(args):
     return 0
 
 
+def measure_philox_ceiling(engine, torch, reps: int = 5) -> dict:
+    """Calls/s of the device Philox4x32-10 alone (ising_philox_probe): every
+    resident thread folds 8192 calls into one register and stores one word,
+    so the launch measures the generator's integer arithmetic only.  Both
+    multiply forms, 4 and 8 independent calls in flight per thread."""
+    sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    threads, blocks = 256, sm * 8
+    out = torch.empty(blocks * threads, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for variant in (0, 1):
+        for chains in (4, 8):
+            iters = 8192 // chains
+            calls = blocks * threads * iters * chains
+            for _ in range(2):
+                engine.philox_probe(out.data_ptr(), blocks, threads, iters, variant, chains,
+                                    BASE_SEED, stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                engine.philox_probe(out.data_ptr(), blocks, threads, iters, variant, chains,
+                                    BASE_SEED, stream)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / reps
+            res[f"{'wide' if variant == 0 else 'split'}_x{chains}"] = {
+                "calls_per_s": calls / (ms / 1e3), "ms_per_launch": ms, "calls": calls}
+    best = max(res.values(), key=lambda r: r["calls_per_s"])
+    engine_form = max(res["wide_x4"]["calls_per_s"], res["wide_x8"]["calls_per_s"])
+    return {"forms": res, "best_calls_per_s": best["calls_per_s"],
+            "engine_form_calls_per_s": engine_form,
+            "draws_per_s": 4 * engine_form, "sm_count": sm,
+            "how": f"{blocks} CTAs x {threads} threads, 8192 calls folded per thread, "
+                   f"CUDA events over {reps} launches"}
+
+
 def run_philox_workload(args):
-    """Throughput of the device generator alone (ising_philox_fill): the
-    ceiling that the Metropolis draws put on any pass kernel."""
+    """Throughput of the device generator alone: the integer ceiling that the
+    Metropolis draws put on any pass kernel (one 32-bit draw per site with
+    dE > 0; a quarter of a call per site)."""
     import torch
     from paper_cs_0312006_gb300 import _build, engine
     _build.build()
     engine.load_library()
-    # 2^22 calls per launch: the 64 MiB of output stays in L2, so the launches
-    # measure the generator's arithmetic, not HBM stores
-    n = 1 << 22
-    out = torch.empty(4 * n, dtype=torch.int32, device="cuda")
-    for _ in range(3):
-        engine.philox_fill(out.data_ptr(), n, 5, 1, 0, BASE_SEED)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    reps = 200
-    for _ in range(reps):
-        engine.philox_fill(out.data_ptr(), n, 5, 1, 0, BASE_SEED)
-    b.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / reps
-    sm = torch.cuda.get_device_properties(0).multi_processor_count
-    line = {"metric": "Philox4x32-10 calls/s", "value": n / (ms / 1e3), "unit": "calls/s",
-            "draws_per_s": 4 * n / (ms / 1e3), "ms_per_launch": ms, "calls": n,
-            "store_GB_per_s": 16 * n / (ms / 1e3) / 1e9, "sm_count": sm,
-            "device": torch.cuda.get_device_name()}
+    res = measure_philox_ceiling(engine, torch, reps=args.probe_reps)
+    line = {"metric": "Philox4x32-10 calls/s", "value": res["engine_form_calls_per_s"],
+            "unit": "calls/s", "probe": res, "device": torch.cuda.get_device_name()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -919,9 +1015,13 @@ def main():
     ap.add_argument("--time-every", type=int, default=20,
                     help="time each lattice's sweep with events on every k-th step (an event "
                          "between two passes keeps the second from being scheduled early)")
+    ap.add_argument("--probe-reps", type=int, default=5,
+                    help="philox: timed launches of each probe form")
     ap.add_argument("--e2e-steps", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="leave the batched and serving forms out of the default line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "engine":

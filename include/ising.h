@@ -203,13 +203,43 @@ int ising_observables_gather(ising_lattice *const *lats, int n, int64_t *pairs, 
 int ising_observables_gather_signal(ising_lattice *const *lats, int n, int64_t *pairs,
                                     int64_t cap, int64_t *counts, int64_t *flag, int64_t value);
 
-/* Copy the spins to host memory in canonical order (L^dims int8).  Syncs. */
+/* Copy the spins to host memory in canonical order (L^dims int8).  Syncs.
+ * Pinned host memory is written by the export kernel directly; pageable
+ * memory goes through a device buffer taken for the call.  ISING_EINVAL if
+ * an ising_set_spins_async of this handle met an invalid value (see there). */
 int ising_get_spins(ising_lattice *lat, int8_t *host_out);
 
 /* Load spins (canonical int8 +-1, host memory) and set the sweep counter to
  * t; pending records are dropped.  Values other than +-1 give ISING_EINVAL
- * (checked on the host before anything changes).  Syncs. */
+ * (checked on the host before anything changes).  Syncs.  Pinned host memory
+ * is read by the import kernel directly, pageable memory through a device
+ * buffer taken for the call. */
 int ising_set_spins(ising_lattice *lat, const int8_t *host_in, uint64_t t);
+
+/*
+ * ising_set_spins without waiting (checkpoint resume, or the initial state
+ * of a job, overlapped with other work).  `in` holds L^dims canonical int8
+ * spins in memory the device can read directly: device memory, or pinned
+ * host memory (cudaHostAlloc, cudaMallocHost, cudaHostRegister, as torch's
+ * pin_memory is), which the import kernel reads over the host link with no
+ * staging copy.  Sets the sweep counter to t and drops pending records, then
+ * returns; the kernel runs in the handle's stream order, so `in` must stay
+ * unchanged until the stream has passed this point.  The values are checked
+ * on the device: if a byte is neither +1 nor -1, the next ising_synchronize,
+ * ising_observables or ising_get_spins of this handle returns ISING_EINVAL
+ * (once), and the spins are undefined until the next ising_init or
+ * ising_set_spins.  ISING_EINVAL at once for memory the device cannot read
+ * (pageable host memory: use ising_set_spins); ISING_ERANGE for
+ * t > 2^32.
+ */
+int ising_set_spins_async(ising_lattice *lat, const int8_t *in, uint64_t t);
+
+/* Write the spins in canonical order (L^dims int8) into memory the device can
+ * write directly -- device memory or pinned host memory -- without waiting:
+ * the export kernel runs in the handle's stream order and the values are in
+ * place once the stream has passed this point (an event, ising_synchronize).
+ * ISING_EINVAL for memory the device cannot write. */
+int ising_get_spins_async(ising_lattice *lat, int8_t *out);
 
 /* Write the spins in canonical order into caller-owned DEVICE memory
  * (L^dims bytes).  Asynchronous on the handle's stream. */
@@ -234,6 +264,20 @@ int ising_get_kernel(const ising_lattice *lat, int *kernel);
  * on `stream`.  For checking the generator and measuring its throughput. */
 int ising_philox_fill(uint32_t *dev_out, uint32_t n, uint32_t c1, uint32_t c2, uint32_t c3,
                       uint64_t seed, void *stream);
+
+/* Throughput probe of the same generator: blocks x threads threads (threads
+ * 128 or 256) each run iters x chains calls, counter word 0 = gid * iters *
+ * chains + k (distinct for every call), word 1 = 5, words 2 and 3 = 0 (the
+ * uniform words of a sweep's draws), and fold the four words of every call
+ * into one uint32 by xor, stored at dev_out[gid] (caller-owned device memory,
+ * blocks x threads words).  variant 0 is the form every kernel uses (one
+ * widening 32x32 -> 64-bit multiply per product), 1 the same function with
+ * separate low and high 32-bit multiplies; chains (4 or 8) independent calls
+ * per step.  Asynchronous on `stream`; calls/s = blocks x threads x iters x
+ * chains / time.  ISING_EINVAL for other shapes, ISING_ERANGE if the
+ * counters would pass 2^32.  For measuring the integer ceiling of a pass. */
+int ising_philox_probe(uint32_t *dev_out, int blocks, int threads, uint32_t iters, int variant,
+                       int chains, uint64_t seed, void *stream);
 
 /* Test hook for the bounded waits: while `on` is nonzero, every staged (TMA)
  * pass expects more bytes on its first tile than are ever copied, so its wait
@@ -356,6 +400,21 @@ int ising_batch_info(const ising_batch *b, int *grid, int *n_big, int *n_small, 
 void ising_batch_destroy(ising_batch *b);
 
 /*
+ * The batched form in one call: advance lattice i of lats[0..n-1] by
+ * sweeps[i] sweeps (Sec. 2.2's black and white passes, the same arithmetic and
+ * draws as ising_sweep) in one persistent launch on `stream`, recording E/M
+ * after sweep u iff (u + 1) % measure_every == 0 into each handle's own record
+ * buffer (read them with ising_observables or ising_observables_gather).
+ * Equivalent to ising_batch_create (default options, no graph) +
+ * ising_batch_launch + ising_batch_sync + ising_batch_destroy: it moves the
+ * lattices to `stream`, allocates the job table for the call, and returns
+ * once the sweeps are done.  Errors as at those calls (ISING_EINVAL for
+ * n < 1, measure_every < 1, a NULL or repeated lattice, a negative count).
+ */
+int ising_batch_run(ising_lattice *const *lats, int n, const int64_t *sweeps, int measure_every,
+                    void *stream);
+
+/*
  * ising_batch_run_static -- the batched launch for callers that cannot
  * allocate device memory while they run.  (An engine facility; the paper has
  * no counterpart.)  Some callers must not allocate once running: a real-time
@@ -368,7 +427,11 @@ void ising_batch_destroy(ising_batch *b);
  * call (more gives ISING_ERANGE before any work is issued); every GPU that
  * loads the library holds that array, about 200 KiB, until the process exits.
  *
- *   lats, n        n distinct lattices of the current device (1 <= n <= 2048).
+ *   lats, n        n distinct lattices of the current device (1 <= n <= 2048),
+ *                  each already on `stream` (ising_set_stream): the work is
+ *                  ordered against the handles' own calls by that stream
+ *                  alone, so a lattice on another stream gives ISING_EINVAL
+ *                  (nothing issued).
  *   sweeps         n sweep counts (>= 0).
  *   measure_every  NULL (every sweep) or n intervals (>= 1): E/M is recorded
  *                  after sweep u iff (u + 1) % measure_every[i] == 0.

@@ -176,6 +176,9 @@ void free_device(ising_lattice* h) {
     h->host_obs = nullptr;
     h->host_obs_cap = 0;
     h->obs_cap = 0;
+    if (h->bad_host) cudaFreeHost(const_cast<int*>(h->bad_host));
+    h->bad_host = nullptr;
+    h->bad_dev = nullptr;
 
 }
 
@@ -210,11 +213,59 @@ std::atomic<int> g_inject_timeout{0};
 
 bool injecting_timeout() { return g_inject_timeout.load() != 0; }
 
-// Read and clear the device's bounded-wait flag (after a synchronisation).
+// Read and clear the device's bounded-wait flag and the handle's invalid-input
+// flag (after a synchronisation).
+int check_bad_input(ising_lattice* h) {
+    if (!h->bad_host || *h->bad_host == 0) return ISING_OK;
+    *h->bad_host = 0;
+    return ISING_EINVAL;
+}
+
 int check_timeout(ising_lattice* h) {
+    const int rc = check_bad_input(h);
+    if (rc != ISING_OK) return rc;
     if (*h->dp->h_err == 0) return ISING_OK;
     *h->dp->h_err = 0;
     return ISING_ETIMEOUT;
+}
+
+// Bytes of one colour array that hold sites (without the spare tail).
+size_t col_data_bytes(const ising_lattice* h) {
+    return h->layout == ISING_BITPACK
+               ? (size_t)h->rows * (size_t)((h->L / 2 + 31) / 32) * sizeof(uint32_t)
+               : (size_t)h->half_sites;
+}
+
+// Canonical spins out of the layout into `dst` (device-writable; may be mapped
+// host memory), on the handle's stream.
+cudaError_t export_spins(ising_lattice* h, int8_t* dst) {
+    if (rows_ok(h->layout, h->L) && ((uintptr_t)dst & 15u) == 0)
+        return rows_export(h->col[0], h->col[1], dst, h->layout, h->L, h->rows, *h->dp,
+                           h->stream);
+    if (h->layout == ISING_BITPACK)
+        return packed_export(static_cast<const uint32_t*>(h->col[0]),
+                             static_cast<const uint32_t*>(h->col[1]), dst, h->L, h->dims,
+                             h->sites, *h->dp, h->stream);
+    return int8_export(static_cast<const int8_t*>(h->col[0]),
+                       static_cast<const int8_t*>(h->col[1]), dst, h->L, h->dims, h->sites,
+                       *h->dp, h->stream);
+}
+
+// Canonical spins from `src` (device-readable) into the layout; with `bad`
+// every byte is checked on the device and the flag raised if one is not +-1.
+cudaError_t import_spins(ising_lattice* h, const int8_t* src, int* bad) {
+    if (rows_ok(h->layout, h->L) && ((uintptr_t)src & 15u) == 0)
+        return rows_import(h->col[0], h->col[1], src, h->layout, h->L, h->rows, bad, *h->dp,
+                           h->stream);
+    if (bad) {
+        const cudaError_t e = check_spins(src, h->sites, bad, *h->dp, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (h->layout == ISING_BITPACK)
+        return packed_import(static_cast<uint32_t*>(h->col[0]), static_cast<uint32_t*>(h->col[1]),
+                             src, h->L, h->dims, h->rows, *h->dp, h->stream);
+    return int8_import(static_cast<int8_t*>(h->col[0]), static_cast<int8_t*>(h->col[1]), src,
+                       h->L, h->dims, h->sites, *h->dp, h->stream);
 }
 
 // Records of several lattices in one launch (ising_observables_gather): one
@@ -382,7 +433,10 @@ int ising_init(ising_lattice* h, int start) {
     if (start != ISING_HOT && start != ISING_COLD_UP && start != ISING_COLD_DOWN)
         return ISING_EINVAL;
     const uint32_t k0 = (uint32_t)(h->seed & 0xFFFFFFFFu), k1 = (uint32_t)(h->seed >> 32);
-    if (h->layout == ISING_BITPACK)
+    if (ising::rows_ok(h->layout, h->L))
+        ISING_CHECK(ising::rows_init(h->col[0], h->col[1], ising::col_data_bytes(h), h->layout,
+                                     h->L, h->rows, start, k0, k1, *h->dp, h->stream));
+    else if (h->layout == ISING_BITPACK)
         ISING_CHECK(ising::packed_init(static_cast<uint32_t*>(h->col[0]),
                                        static_cast<uint32_t*>(h->col[1]), h->L, h->dims, h->rows,
                                        start, k0, k1, *h->dp, h->stream));
@@ -504,19 +558,26 @@ int ising_observables_gather_signal(ising_lattice* const* lats, int n, int64_t* 
         for (int i = 0; i < n; ++i) counts[i] = 0;
         return ISING_OK;
     }
+    // every count is known before anything is queued (a handle listed twice
+    // reports its records at its first entry and 0 at the others)
+    for (int i = 0; i < n; ++i) {
+        counts[i] = lats[i]->n_rec;
+        lats[i]->n_rec = 0;  // a later entry of the same handle reads 0
+    }
+    for (int i = 0; i < n; ++i)
+        if (counts[i] > 0) lats[i]->n_rec = counts[i];  // restored until queued
     GatherChunk chunk;
     chunk.count = 0;
     int64_t off = 0;
+    int chunk_begin = 0;
     for (int i = 0; i < n; ++i) {
         ising_lattice* h = lats[i];
-        counts[i] = h->n_rec;  // 0 for a handle listed twice, read at its first entry
-        if (h->n_rec > 0) {
+        if (counts[i] > 0) {
             chunk.src[chunk.count] = h->obs;
-            chunk.n[chunk.count] = h->n_rec;
+            chunk.n[chunk.count] = counts[i];
             chunk.off[chunk.count] = off;
             ++chunk.count;
-            off += h->n_rec;
-            h->n_rec = 0;
+            off += counts[i];
         }
         // the last launch (possibly with no records) carries the flag
         const bool last = i == n - 1;
@@ -525,6 +586,10 @@ int ising_observables_gather_signal(ising_lattice* const* lats, int n, int64_t* 
                 ISING_CHECK(launch_chained(gather_records_kernel, 1u, 256u, 0, lats[0]->stream,
                                            chunk, out, last ? dflag : nullptr,
                                            (long long)value));
+            // queued: this chunk's records now belong to the caller's buffer
+            for (int k = chunk_begin; k <= i; ++k)
+                if (counts[k] > 0) lats[k]->n_rec = 0;
+            chunk_begin = i + 1;
             chunk.count = 0;
         }
     }
@@ -536,33 +601,81 @@ int ising_observables_gather(ising_lattice* const* lats, int n, int64_t* pairs, 
     return ising_observables_gather_signal(lats, n, pairs, cap, counts, nullptr, 0);
 }
 
+// The device address of `p` if kernels can read and write it directly (device
+// or managed memory, or pinned host memory mapped into the device's address
+// space), else nullptr.
+static void* device_reachable(const void* p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)
+        return const_cast<void*>(p);
+    if (attr.type == cudaMemoryTypeHost && attr.devicePointer) return attr.devicePointer;
+    return nullptr;
+}
+
+// The handle's invalid-input flag (mapped pinned host memory), made on first use.
+static int ensure_bad_flag(ising_lattice* h) {
+    if (h->bad_dev) return ISING_OK;
+    int* p = nullptr;
+    ISING_CHECK(cudaHostAlloc(reinterpret_cast<void**>(&p), sizeof(int), cudaHostAllocMapped));
+    *p = 0;
+    void* d = nullptr;
+    const cudaError_t e = cudaHostGetDevicePointer(&d, p, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(p);
+        return cuda_fail(e);
+    }
+    h->bad_host = p;
+    h->bad_dev = static_cast<int*>(d);
+    return ISING_OK;
+}
+
 int ising_export_device(ising_lattice* h, int8_t* dev_out) {
     if (!h || !dev_out) return ISING_EINVAL;
-    if (h->layout == ISING_BITPACK)
-        ISING_CHECK(ising::packed_export(static_cast<const uint32_t*>(h->col[0]),
-                                         static_cast<const uint32_t*>(h->col[1]), dev_out, h->L,
-                                         h->dims, h->sites, *h->dp, h->stream));
-    else
-        ISING_CHECK(ising::int8_export(static_cast<const int8_t*>(h->col[0]),
-                                       static_cast<const int8_t*>(h->col[1]), dev_out, h->L,
-                                       h->dims, h->sites, *h->dp, h->stream));
+    ISING_CHECK(ising::export_spins(h, dev_out));
+    return ISING_OK;
+}
+
+int ising_get_spins_async(ising_lattice* h, int8_t* out) {
+    if (!h || !out) return ISING_EINVAL;
+    void* d = device_reachable(out);
+    if (!d) return ISING_EINVAL;
+    ISING_CHECK(ising::export_spins(h, static_cast<int8_t*>(d)));
     return ISING_OK;
 }
 
 int ising_get_spins(ising_lattice* h, int8_t* host_out) {
     if (!h || !host_out) return ISING_EINVAL;
-    int8_t* tmp = nullptr;
-    ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
-    int rc = ising_export_device(h, tmp);
-    if (rc == ISING_OK) {
-        cudaError_t e = cudaMemcpyAsync(host_out, tmp, (size_t)h->sites, cudaMemcpyDeviceToHost,
-                                        h->stream);
-        if (e != cudaSuccess) rc = cuda_fail(e);
+    if (void* d = device_reachable(host_out)) {
+        // pinned host (or device) memory: the export kernel writes it directly
+        ISING_CHECK(ising::export_spins(h, static_cast<int8_t*>(d)));
+    } else {
+        int8_t* tmp = nullptr;
+        ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+        cudaError_t e = ising::export_spins(h, tmp);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_out, tmp, (size_t)h->sites, cudaMemcpyDeviceToHost,
+                                h->stream);
+        cudaFreeAsync(tmp, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e);
     }
-    cudaFreeAsync(tmp, h->stream);
-    if (rc != ISING_OK) return rc;
     ISING_CHECK(cudaStreamSynchronize(h->stream));
-    return ISING_OK;
+    return check_bad_input(h);
+}
+
+int ising_set_spins_async(ising_lattice* h, const int8_t* in, uint64_t t) {
+    if (!h || !in) return ISING_EINVAL;
+    if (t > kMaxSweep + 1) return ISING_ERANGE;
+    void* d = device_reachable(in);
+    if (!d) return ISING_EINVAL;
+    int rc = ensure_bad_flag(h);
+    if (rc != ISING_OK) return rc;
+    ISING_CHECK(ising::import_spins(h, static_cast<const int8_t*>(d), h->bad_dev));
+    h->t = t;
+    return clear_records(h);
 }
 
 int ising_set_spins(ising_lattice* h, const int8_t* host_in, uint64_t t) {
@@ -576,22 +689,18 @@ int ising_set_spins(ising_lattice* h, const int8_t* host_in, uint64_t t) {
         for (int64_t i = i0; i < i1; ++i) bad |= (host_in[i] != 1) & (host_in[i] != -1);
         if (bad) return ISING_EINVAL;
     }
-    int8_t* tmp = nullptr;
-    ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
-    cudaError_t e = cudaMemcpyAsync(tmp, host_in, (size_t)h->sites, cudaMemcpyHostToDevice,
-                                    h->stream);
-    if (e == cudaSuccess) {
-        if (h->layout == ISING_BITPACK)
-            e = ising::packed_import(static_cast<uint32_t*>(h->col[0]),
-                                     static_cast<uint32_t*>(h->col[1]), tmp, h->L, h->dims,
-                                     h->rows, *h->dp, h->stream);
-        else
-            e = ising::int8_import(static_cast<int8_t*>(h->col[0]),
-                                   static_cast<int8_t*>(h->col[1]), tmp, h->L, h->dims, h->sites,
-                                   *h->dp, h->stream);
+    if (void* d = device_reachable(host_in)) {
+        // pinned host (or device) memory: the import kernel reads it directly
+        ISING_CHECK(ising::import_spins(h, static_cast<const int8_t*>(d), nullptr));
+    } else {
+        int8_t* tmp = nullptr;
+        ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+        cudaError_t e = cudaMemcpyAsync(tmp, host_in, (size_t)h->sites, cudaMemcpyHostToDevice,
+                                        h->stream);
+        if (e == cudaSuccess) e = ising::import_spins(h, tmp, nullptr);
+        cudaFreeAsync(tmp, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e);
     }
-    cudaFreeAsync(tmp, h->stream);
-    if (e != cudaSuccess) return cuda_fail(e);
     h->t = t;
     int rc = clear_records(h);
     if (rc != ISING_OK) return rc;
@@ -759,6 +868,20 @@ int ising_philox_fill(uint32_t* dev_out, uint32_t n, uint32_t c1, uint32_t c2, u
     if (rc != ISING_OK) return rc;
     ISING_CHECK(ising::philox_fill(dev_out, n, c1, c2, c3, (uint32_t)(seed & 0xFFFFFFFFu),
                                    (uint32_t)(seed >> 32), *dp, static_cast<cudaStream_t>(stream)));
+    return ISING_OK;
+}
+
+int ising_philox_probe(uint32_t* dev_out, int blocks, int threads, uint32_t iters, int variant,
+                       int chains, uint64_t seed, void* stream) {
+    if (!dev_out || blocks < 1 || (threads != 128 && threads != 256) || iters < 1 ||
+        (variant != 0 && variant != 1) || (chains != 4 && chains != 8))
+        return ISING_EINVAL;
+    // every counter word 0 must be distinct: gid * iters * chains + k < 2^32
+    if ((uint64_t)blocks * (uint64_t)threads * iters * (uint64_t)chains > 0xFFFFFFFFull)
+        return ISING_ERANGE;
+    ISING_CHECK(ising::philox_probe(dev_out, blocks, threads, iters, variant, chains, 5u,
+                                    (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32),
+                                    static_cast<cudaStream_t>(stream)));
     return ISING_OK;
 }
 

@@ -39,6 +39,10 @@ struct ising_lattice {
     int hits = 2;                       // multi-hit Metropolis: trials per visit
     long long* host_obs = nullptr;      // pinned staging for ising_observables
     int64_t host_obs_cap = 0;           // in records
+    // raised by an import kernel of ising_set_spins_async that met a value
+    // other than +-1 (mapped pinned int: device view, host view)
+    int* bad_dev = nullptr;
+    volatile int* bad_host = nullptr;
 };
 
 namespace ising {
@@ -93,6 +97,8 @@ cudaError_t int8_query_occupancy(DeviceProps& dp);
 bool int8_vec_ok(int L);
 cudaError_t philox_fill(uint32_t* out, uint32_t n, uint32_t c1, uint32_t c2, uint32_t c3,
                         uint32_t key0, uint32_t key1, const DeviceProps& dp, cudaStream_t st);
+cudaError_t philox_probe(uint32_t* out, int blocks, int threads, uint32_t iters, int variant,
+                         int chains, uint32_t c1, uint32_t key0, uint32_t key1, cudaStream_t st);
 cudaError_t int8_pass(const PassArgs& a, int dims, int64_t half_sites, bool measure, int rule,
                       const DeviceProps& dp, cudaStream_t st);
 cudaError_t int8_init(int8_t* col0, int8_t* col1, int L, int dims, int64_t sites, int start,
@@ -108,6 +114,20 @@ bool int8_tma_ok(int dims, int L);
 bool int8_tma_preferred(int dims, int L);
 cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, int rule,
                           const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st);
+
+// canonical <-> layout conversion and initial states for half rows of whole
+// 16-byte vectors (int8, L % 32 == 0) or whole words (bit-packed, L % 64 == 0)
+// (convert.cu)
+bool rows_ok(int layout, int L);
+cudaError_t rows_init(void* col0, void* col1, size_t col_data_bytes, int layout, int L,
+                      int64_t rows, int start, uint32_t key0, uint32_t key1,
+                      const DeviceProps& dp, cudaStream_t st);
+cudaError_t rows_import(void* col0, void* col1, const int8_t* in, int layout, int L, int64_t rows,
+                        int* bad_flag, const DeviceProps& dp, cudaStream_t st);
+cudaError_t rows_export(const void* col0, const void* col1, int8_t* out, int layout, int L,
+                        int64_t rows, const DeviceProps& dp, cudaStream_t st);
+cudaError_t check_spins(const int8_t* in, int64_t n, int* bad_flag, const DeviceProps& dp,
+                        cudaStream_t st);
 
 // demon dynamics, int8 layout (sweep_demon.cu)
 cudaError_t demon_query_occupancy(DeviceProps& dp);

@@ -54,6 +54,26 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
     return Philox4{c0, c1, c2, c3};
 }
 
+// The same function with each 32x32 -> 64-bit product taken as a separate
+// low-half and high-half 32-bit multiply (mul.lo / mul.hi) instead of one
+// widening multiply; identical results.  Kept for measuring which form the
+// multiply pipe retires faster (ising_philox_probe).
+__device__ __forceinline__ Philox4 philox4x32_10_split(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                       uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t pa_hi = __umulhi(c0, kPhiloxMulA), pa_lo = c0 * kPhiloxMulA;
+        const uint32_t pb_hi = __umulhi(c2, kPhiloxMulB), pb_lo = c2 * kPhiloxMulB;
+        c0 = pb_hi ^ c1 ^ k0;
+        c1 = pb_lo;
+        c2 = pa_hi ^ c3 ^ k1;
+        c3 = pa_lo;
+        k0 += kPhiloxWeylA;
+        k1 += kPhiloxWeylB;
+    }
+    return Philox4{c0, c1, c2, c3};
+}
+
 // Programmatic dependent launch (griddepcontrol, sm_90 and later).  The
 // per-lattice pass kernels are launched with programmatic stream
 // serialisation (launch_chained), so the next kernel in the stream can be

@@ -252,6 +252,55 @@ __global__ void philox_fill_kernel(uint4* out, uint32_t n, uint32_t c1, uint32_t
     }
 }
 
+// Throughput probe of the generator: each thread runs `iters` rounds of CHAINS
+// independent calls (counters gid * iters * CHAINS + k, the sweep-like words
+// c1 = t, c2 = c = 0, c3 = 0), folds all four output words of every call into
+// a register and stores one word at the end, so stores and launch overhead
+// vanish against the arithmetic.  VARIANT 0 is the engine's form, 1 the
+// split-multiply form.
+template <int VARIANT, int CHAINS>
+__global__ void __launch_bounds__(256) philox_probe_kernel(uint32_t* out, uint32_t iters,
+                                                           uint32_t c1, uint32_t key0,
+                                                           uint32_t key1) {
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc[CHAINS];
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) acc[k] = 0u;
+    uint32_t ctr = gid * iters * (uint32_t)CHAINS;
+#pragma unroll 1
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < CHAINS; ++k) {
+            const Philox4 u =
+                VARIANT == 0 ? philox4x32_10(ctr + (uint32_t)k, c1, 0u, kTagSweep, key0, key1)
+                             : philox4x32_10_split(ctr + (uint32_t)k, c1, 0u, kTagSweep, key0,
+                                                   key1);
+            acc[k] ^= u.w0 ^ u.w1 ^ u.w2 ^ u.w3;
+        }
+        ctr += (uint32_t)CHAINS;
+    }
+    uint32_t r = 0u;
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) r ^= acc[k];
+    out[gid] = r;
+}
+
+cudaError_t philox_probe(uint32_t* out, int blocks, int threads, uint32_t iters, int variant,
+                         int chains, uint32_t c1, uint32_t key0, uint32_t key1, cudaStream_t st) {
+#define ISING_PROBE(V, C)                                                                  \
+    if (variant == V && chains == C) {                                                     \
+        philox_probe_kernel<V, C><<<(unsigned)blocks, (unsigned)threads, 0, st>>>(out, iters, \
+                                                                                  c1, key0, key1); \
+        return cudaGetLastError();                                                         \
+    }
+    ISING_PROBE(0, 4)
+    ISING_PROBE(0, 8)
+    ISING_PROBE(1, 4)
+    ISING_PROBE(1, 8)
+#undef ISING_PROBE
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t int8_query_occupancy(DeviceProps& dp) {
     cudaError_t e;
 #define ISING_OCC(R, D, M)                                                                   \

@@ -82,6 +82,8 @@ def load_library():
                                                 ctypes.c_int),
             "ising_get_spins": ([P, P], ctypes.c_int),
             "ising_set_spins": ([P, P, ctypes.c_uint64], ctypes.c_int),
+            "ising_set_spins_async": ([P, P, ctypes.c_uint64], ctypes.c_int),
+            "ising_get_spins_async": ([P, P], ctypes.c_int),
             "ising_export_device": ([P, P], ctypes.c_int),
             "ising_set_stream": ([P, P], ctypes.c_int),
             "ising_thresholds": ([P, u32p], ctypes.c_int),
@@ -99,6 +101,8 @@ def load_library():
             "ising_test_inject_timeout": ([ctypes.c_int], ctypes.c_int),
             "ising_philox_fill": ([P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint32, ctypes.c_uint64, P], ctypes.c_int),
+            "ising_philox_probe": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_uint64, P], ctypes.c_int),
             "ising_destroy": ([P], None),
             "ising_batch_create": ([ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int, i64p,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(BatchOpts), P],
@@ -109,6 +113,8 @@ def load_library():
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                                  ctypes.c_int),
             "ising_batch_destroy": ([P], None),
+            "ising_batch_run": ([ctypes.POINTER(P), ctypes.c_int, i64p, ctypes.c_int, P],
+                                ctypes.c_int),
             "ising_batch_run_static": ([ctypes.POINTER(P), ctypes.c_int, i64p,
                                         ctypes.POINTER(ctypes.c_int), P, ctypes.c_int64,
                                         ctypes.POINTER(BatchOpts), P], ctypes.c_int),
@@ -135,6 +141,18 @@ def philox_fill(dev_ptr: int, n: int, c1: int, c2: int, c3: int, seed: int, stre
                                             ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
                                             ctypes.c_void_p(int(raw) if raw else 0)),
            "ising_philox_fill")
+
+
+def philox_probe(dev_ptr: int, blocks: int, threads: int, iters: int, variant: int = 0,
+                 chains: int = 8, seed: int = 0, stream=None) -> None:
+    """``ising_philox_probe``: blocks x threads threads each fold iters x chains
+    Philox4x32-10 calls into one uint32 at ``dev_ptr``."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(load_library().ising_philox_probe(ctypes.c_void_p(dev_ptr), blocks, threads, iters,
+                                             variant, chains,
+                                             ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                                             ctypes.c_void_p(int(raw) if raw else 0)),
+           "ising_philox_probe")
 
 
 def test_inject_timeout(on: bool) -> None:
@@ -243,6 +261,20 @@ class Lattice:
     def set_spins(self, spins: np.ndarray, t: int = 0) -> None:
         s = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1)
         _check(self._lib.ising_set_spins(self._h, s.ctypes.data, int(t)), "ising_set_spins")
+
+    def set_spins_async(self, spins_ptr: int, t: int = 0) -> None:
+        """``ising_set_spins_async``: load L^dims canonical int8 spins from
+        device memory or pinned host memory at ``spins_ptr`` (e.g.
+        ``tensor.data_ptr()`` of a pinned CPU or a CUDA int8 tensor) in stream
+        order; invalid values are reported by the next synchronising call."""
+        _check(self._lib.ising_set_spins_async(self._h, ctypes.c_void_p(spins_ptr), int(t)),
+               "ising_set_spins_async")
+
+    def get_spins_async(self, out_ptr: int) -> None:
+        """``ising_get_spins_async``: write canonical int8 spins to device
+        memory or pinned host memory at ``out_ptr`` in stream order."""
+        _check(self._lib.ising_get_spins_async(self._h, ctypes.c_void_p(out_ptr)),
+               "ising_get_spins_async")
 
     def export_device(self, out_ptr: int) -> None:
         """Write canonical int8 spins to device memory at ``out_ptr``
@@ -369,6 +401,20 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def batch_run(lattices, sweeps, measure_every: int = 1, stream=None) -> None:
+    """``ising_batch_run``: advance every lattice by its sweeps in one
+    persistent launch on ``stream`` and wait; records go to the handles."""
+    lib = load_library()
+    n = len(lattices)
+    sw = np.asarray(np.broadcast_to(np.asarray(sweeps, dtype=np.int64), (n,)),
+                    dtype=np.int64).copy()
+    handles = (ctypes.c_void_p * n)(*[lat.handle for lat in lattices])
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib.ising_batch_run(handles, n, sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                               int(measure_every), ctypes.c_void_p(int(raw) if raw else 0)),
+           "ising_batch_run")
 
 
 def batch_run_static(lattices, sweeps, measure_every, records_ptr: int, records_cap: int,
