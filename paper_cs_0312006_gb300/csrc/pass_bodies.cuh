@@ -428,13 +428,16 @@ __device__ __forceinline__ uint4 update_vec(const uint4& s, const uint4& x, cons
 }
 
 
-// Two vectors at once (Metropolis): eight Philox calls in flight instead of
-// four, for the kernels whose threads own two vectors of a tile.
+// Two vectors at once (Metropolis), their eight Philox calls made by the
+// caller (u[w] is the draw of word w: vector w >> 2, word w & 3).  The
+// calls depend only on counters, so a kernel issues them before its loads
+// of the spins; every word then takes the counting test (the draw is used
+// only where dE > 0, so the result equals the lazy per-group form).
 template <int DIMS, bool MEASURE>
 __device__ __forceinline__ void update_vec_pair(uint4 (&S)[2], const uint4 (&x)[2],
                                                 const uint4 (&xs)[2], const uint4 (&ym)[2],
                                                 const uint4 (&yp)[2], const uint4 (&zm)[2],
-                                                const uint4 (&zp)[2], const uint32_t (&g0)[2],
+                                                const uint4 (&zp)[2], const Philox4 (&u)[8],
                                                 const PassArgs& a, int& e_acc, int& m_neg) {
     uint32_t sv[8], D[8], X[8];
 #pragma unroll
@@ -448,21 +451,8 @@ __device__ __forceinline__ void update_vec_pair(uint4 (&S)[2], const uint4 (&x)[
         D[4 * q + 2] = disagreements<DIMS>(S[q].z, x[q].z, xs[q].z, ym[q].z, yp[q].z, zm[q].z, zp[q].z);
         D[4 * q + 3] = disagreements<DIMS>(S[q].w, x[q].w, xs[q].w, ym[q].w, yp[q].w, zm[q].w, zp[q].w);
     }
-    bool need = false;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        X[w] = downhill_mask<DIMS>(D[w]);
-        need |= X[w] != 0xFEFEFEFEu;
-    }
-    if (need) {
-        Philox4 u[8];
-#pragma unroll
-        for (int w = 0; w < 8; ++w)
-            u[w] = philox4x32_10(g0[w >> 2] + (uint32_t)(w & 3), a.t, (uint32_t)a.c, kTagSweep,
-                                 a.key0, a.key1);
-#pragma unroll
-        for (int w = 0; w < 8; ++w) X[w] |= uphill_count<DIMS>(D[w], u[w], a);
-    }
+    for (int w = 0; w < 8; ++w) X[w] = downhill_mask<DIMS>(D[w]) | uphill_count<DIMS>(D[w], u[w], a);
     uint32_t out[8];
 #pragma unroll
     for (int w = 0; w < 8; ++w) {

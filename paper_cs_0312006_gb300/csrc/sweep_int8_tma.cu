@@ -138,14 +138,15 @@ __device__ __forceinline__ void issue_tile(const PassArgs& a, const TmaGeom& tg,
 }
 
 
-// Heat bath for two vectors at once: every site draws (eight Philox calls in
-// flight) and flips iff u < thr[d], the threshold read from a shared table
-// indexed by the site's disagreeing-neighbour count d (byte j of D is 2 d_j).
+// Heat bath for two vectors at once: every site draws (the eight Philox calls
+// made by the caller, u[w] for word w) and flips iff u < thr[d], the threshold
+// read from a shared table indexed by the site's disagreeing-neighbour count d
+// (byte j of D is 2 d_j).
 template <int DIMS, bool MEASURE>
 __device__ __forceinline__ void update_vec_pair_hb(uint4 (&S)[2], const uint4 (&x)[2],
                                                    const uint4 (&xs)[2], const uint4 (&ym)[2],
                                                    const uint4 (&yp)[2], const uint4 (&zm)[2],
-                                                   const uint4 (&zp)[2], const uint32_t (&g0)[2],
+                                                   const uint4 (&zp)[2], const Philox4 (&u)[8],
                                                    const uint32_t* s_thb, const PassArgs& a,
                                                    int& e_acc, int& m_neg) {
     uint32_t sv[8], D[8], X[8];
@@ -160,11 +161,6 @@ __device__ __forceinline__ void update_vec_pair_hb(uint4 (&S)[2], const uint4 (&
         D[4 * q + 2] = disagreements<DIMS>(S[q].z, x[q].z, xs[q].z, ym[q].z, yp[q].z, zm[q].z, zp[q].z);
         D[4 * q + 3] = disagreements<DIMS>(S[q].w, x[q].w, xs[q].w, ym[q].w, yp[q].w, zm[q].w, zp[q].w);
     }
-    Philox4 u[8];
-#pragma unroll
-    for (int w = 0; w < 8; ++w)
-        u[w] = philox4x32_10(g0[w >> 2] + (uint32_t)(w & 3), a.t, (uint32_t)a.c, kTagSweep,
-                             a.key0, a.key1);
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
         const uint32_t uw[4] = {u[w].w0, u[w].w1, u[w].w2, u[w].w3};
@@ -250,11 +246,21 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
             // two rows per step: eight Philox calls in flight per thread (the
             // heat bath reads each site's threshold from s_thb: 8.07e11 site
             // updates/s per pass at L = 8192 against 6.59e11 one row at a time
-            // with the counting test)
+            // with the counting test).  The calls need only counters, so they
+            // are issued before the loads of the spins (3 % faster at L = 8192
+            // than drawing after the neighbour counts).
             for (; i0 + 1u < R; i0 += 2u) {
                 for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
                     uint4 S[2], X[2], XS[2], YM[2], YP[2], ZM[2], ZP[2];
-                    uint32_t g0[2], rowg[2];
+                    uint32_t rowg[2];
+                    Philox4 u[8];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+                        rowg[q] = (z * (uint32_t)a.L + y0 + i0 + (uint32_t)q) * nv + v;
+#pragma unroll
+                    for (int w = 0; w < 8; ++w)
+                        u[w] = philox4x32_10(rowg[w >> 2] * 4u + (uint32_t)(w & 3), a.t,
+                                             (uint32_t)a.c, kTagSweep, a.key0, a.key1);
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
                         const uint32_t i = i0 + (uint32_t)q;
@@ -286,15 +292,13 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
                                                __funnelshift_r(oc.w, next, 8));
                         }
                         S[q] = own_s[i * nv + v];
-                        rowg[q] = (z * (uint32_t)a.L + y) * nv + v;
-                        g0[q] = rowg[q] * 4u;
                     }
                     int e_vec = 0;
                     if (RULE == kRuleHeatBath)
-                        update_vec_pair_hb<DIMS, MEASURE>(S, X, XS, YM, YP, ZM, ZP, g0, s_thb, a,
+                        update_vec_pair_hb<DIMS, MEASURE>(S, X, XS, YM, YP, ZM, ZP, u, s_thb, a,
                                                           e_vec, m_neg);
                     else
-                        update_vec_pair<DIMS, MEASURE>(S, X, XS, YM, YP, ZM, ZP, g0, a, e_vec,
+                        update_vec_pair<DIMS, MEASURE>(S, X, XS, YM, YP, ZM, ZP, u, a, e_vec,
                                                        m_neg);
                     own_g[rowg[0]] = S[0];
                     own_g[rowg[1]] = S[1];
