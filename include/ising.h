@@ -23,7 +23,11 @@
  *   - Work is issued on the handle's CUDA stream (default: the legacy default
  *     stream); calls that return host data synchronise that stream.
  *   - The library owns all device memory it allocates for a handle and frees
- *     it in ising_destroy().
+ *     it in ising_destroy().  Lattice memory (spins, demons, records) comes
+ *     from a stream-ordered pool the library keeps per device: a destroyed
+ *     lattice's blocks stay reserved for the next one (creating and
+ *     destroying lattices never synchronises the device) until
+ *     ising_release_cached_memory() hands them back.
  */
 #ifndef ISING_GB300_H
 #define ISING_GB300_H
@@ -339,8 +343,17 @@ int ising_get_info(const ising_lattice *lat, ising_info_t *out);
  * on a bounded wait since the last check (the flag is then cleared). */
 int ising_synchronize(ising_lattice *lat);
 
-/* Free everything the handle owns.  NULL is accepted. */
+/* Free everything the handle owns.  NULL is accepted.  Does not wait for the
+ * handle's queued work: its device memory returns to the library's pool in
+ * the handle's stream order (the stream must still exist); only a handle
+ * that holds pinned host buffers (after ising_observables or
+ * ising_set_spins_async) waits for its stream first. */
 void ising_destroy(ising_lattice *lat);
+
+/* Return the memory the library's pool on the current device keeps for
+ * reuse (blocks of destroyed lattices) to the system.  Synchronises the
+ * device first. */
+int ising_release_cached_memory(void);
 
 /*
  * Batched form: many independent lattices (any mix of dims, L, layout, beta,
@@ -384,6 +397,18 @@ typedef struct ising_batch_opts {
 int ising_batch_create(ising_batch **out, ising_lattice *const *lats, int n,
                        const int64_t *sweeps, const int *measure_every,
                        const ising_batch_opts *opts, void *stream);
+
+/* Replace the batch's lattices, sweep counts and measurement intervals (the
+ * same rules as at ising_batch_create; the options stay) for its next launch,
+ * reusing its device tables (they grow, in stream order, when n exceeds every
+ * earlier size).  May be called while an earlier launch of the batch is still
+ * running: that launch keeps its own lattices and counts, and the new ones
+ * follow it on the batch stream.  The new lattices are moved to the batch
+ * stream; a captured graph is dropped and recaptured at the next launch.
+ * For loops that change the set every round (continuous batching) without
+ * creating and destroying a batch each time. */
+int ising_batch_update(ising_batch *b, ising_lattice *const *lats, int n,
+                       const int64_t *sweeps, const int *measure_every);
 
 /* Advance every lattice of the batch by its sweeps (asynchronous). */
 int ising_batch_launch(ising_batch *b);

@@ -185,15 +185,23 @@ __device__ __forceinline__ void job_pass(const BatchJob& j, int c, uint32_t t, u
         }
         if (MEASURE) m_acc += n_sites - 2 * m_neg;
     } else {
+        // rows grouped by their offset in a Philox group, so that a warp's
+        // words share it and take the five-call draws together
         const uint32_t items = j.rows * (((uint32_t)j.W + 31u) >> 5);
+        const uint32_t rgroups = packed_row_groups((uint32_t)j.W);
         for (uint32_t it = rank; it < items; it += nthr)
-            packed_word<DIMS, MEASURE, NC, RULE>(a, it, e_acc, m_acc);
+            packed_word<DIMS, MEASURE, NC, RULE, RULE != kRuleMultiHit>(a, it, e_acc, m_acc,
+                                                                        rgroups);
     }
 }
 
 template <int DIMS, int LAYOUT, int MODE, int RULE>
 __device__ void run_job(BatchJob* jp, uint32_t rank, uint32_t nthr, bool leader) {
-    constexpr int NC = MODE == kModeCluster ? 2 : 0;
+    // plain loads in both modes: the passes of a cluster job are separated by
+    // the cluster barrier, whose release/acquire (cluster scope) makes the
+    // other CTAs' writes of the previous pass visible to them (3 % faster on
+    // the 2048-lattice mix than reading through L2 only)
+    constexpr int NC = 0;
     const BatchJob j = *jp;
     int rec = 0;
     for (int s = 0; s < j.nsweeps; ++s) {
@@ -327,23 +335,35 @@ struct RuleQueues {
     int grid = 0;  // resident CTAs of that rule's kernel
 };
 
+#define ISING_BCHECK(call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ising::cuda_fail(e_); \
+    } while (0)
+
 struct ising_batch {
     std::vector<ising_lattice*> lats;
     std::vector<int64_t> sweeps;
     std::vector<int> every;
     std::vector<int> huge;  // lattices advanced by the per-lattice kernels
     std::vector<char> in_table;
+    std::vector<int> order;  // per rule: [big..., small...] (host copy)
     ising_batch_opts opts{};
     cudaStream_t stream = nullptr;
+    const DeviceProps* dp = nullptr;
+    int cap = 0;                 // lattices the tables below can hold
     BatchJob* d_jobs = nullptr;
     BatchJob* h_jobs = nullptr;  // pinned mirror
-    int* d_order = nullptr;      // per rule: [big..., small...]
+    int* d_order = nullptr;
+    int* h_order = nullptr;      // pinned mirror
     int* d_counters = nullptr;   // two per rule
     RuleQueues q[2];             // [ISING_RULE_METROPOLIS], [ISING_RULE_HEATBATH]
+    int grid[2] = {0, 0};        // resident CTAs of each rule's kernel (0: not yet known)
     std::vector<int> rule;       // each lattice's rule when the batch was made
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t uploaded = nullptr;
     bool table_valid = false;  // device table equals the host mirror's continuation
+    bool order_dirty = true;   // the device order array must be uploaded
     int64_t launches = 0;
 };
 
@@ -371,60 +391,46 @@ int queued_jobs(const ising_batch* b) {
 void free_batch(ising_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->uploaded) cudaEventDestroy(b->uploaded);
-    if (b->d_jobs) cudaFree(b->d_jobs);
-    if (b->d_order) cudaFree(b->d_order);
-    if (b->d_counters) cudaFree(b->d_counters);
+    if (b->d_jobs) cudaFreeAsync(b->d_jobs, b->stream);
+    if (b->d_order) cudaFreeAsync(b->d_order, b->stream);
+    if (b->d_counters) cudaFreeAsync(b->d_counters, b->stream);
     if (b->h_jobs) cudaFreeHost(b->h_jobs);
+    if (b->h_order) cudaFreeHost(b->h_order);
     delete b;
 }
 
-}  // namespace
-
-#define ISING_BCHECK(call)                                  \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
-        if (e_ != cudaSuccess) return ising::cuda_fail(e_); \
-    } while (0)
-
-extern "C" {
-
-int ising_batch_create(ising_batch** out, ising_lattice* const* lats, int n,
-                       const int64_t* sweeps, const int* measure_every,
-                       const ising_batch_opts* opts, void* stream) {
-    if (!out) return ISING_EINVAL;
-    *out = nullptr;
+// Arguments of a batch's lattice list: valid handles, each at most once.
+int check_members(ising_lattice* const* lats, int n, const int64_t* sweeps,
+                  const int* measure_every) {
     if (!lats || n < 1 || !sweeps) return ISING_EINVAL;
-    ising_batch_opts o = {};
-    if (opts) o = *opts;
-    if (o.block_threads == 0) o.block_threads = 256;
-    if (o.cluster_size == 0) o.cluster_size = 4;
-    if (o.big_sites == 0) o.big_sites = 1 << 18;
-    if (o.huge_sites == 0) o.huge_sites = (int64_t)1 << 22;
-    if (o.block_threads != 128 && o.block_threads != 256) return ISING_EINVAL;
-    if (o.cluster_size < 1 || o.cluster_size > 8) return ISING_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!lats[i] || sweeps[i] < 0 || sweeps[i] > 0x7FFFFFFF) return ISING_EINVAL;
         if (measure_every && measure_every[i] < 1) return ISING_EINVAL;
-        for (int k = 0; k < i; ++k)
-            if (lats[k] == lats[i]) return ISING_EINVAL;  // a lattice may appear once
     }
-    ising_batch* b = new (std::nothrow) ising_batch();
-    if (!b) return ISING_ENOMEM;
+    std::vector<ising_lattice*> sorted(lats, lats + n);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+        return ISING_EINVAL;  // a lattice may appear once
+    return ISING_OK;
+}
+
+// Take a new lattice list: move the lattices to the batch stream, build the
+// per-rule queues (largest work first, split at the size thresholds) and make
+// room in the tables.  Growing the tables frees the old ones in stream order,
+// after any launch already queued.
+int assign_members(ising_batch* b, ising_lattice* const* lats, int n, const int64_t* sweeps,
+                   const int* measure_every) {
+    const ising_batch_opts& o = b->opts;
+    for (int i = 0; i < n; ++i) {
+        const int rc = ising_set_stream(lats[i], b->stream);
+        if (rc != ISING_OK) return rc;
+    }
     b->lats.assign(lats, lats + n);
     b->sweeps.assign(sweeps, sweeps + n);
     b->every.resize(n);
     for (int i = 0; i < n; ++i) b->every[i] = measure_every ? measure_every[i] : 1;
-    b->opts = o;
-    b->stream = static_cast<cudaStream_t>(stream);
-    int rc = ISING_OK;
-    for (int i = 0; i < n && rc == ISING_OK; ++i) rc = ising_set_stream(b->lats[i], stream);
-    if (rc != ISING_OK) {
-        free_batch(b);
-        return rc;
-    }
-
-    // queues per rule: largest work first, split at the size thresholds
     std::vector<int> big[2], small[2];
+    b->huge.clear();
     b->in_table.assign(n, 1);
     b->rule.resize(n);
     for (int i = 0; i < n; ++i) {
@@ -444,38 +450,106 @@ int ising_batch_create(ising_batch** out, ising_lattice* const* lats, int n,
     auto by_work = [&](int x, int y) {
         return b->lats[x]->sites * b->sweeps[x] > b->lats[y]->sites * b->sweeps[y];
     };
-    std::vector<int> order;
+    b->order.clear();
     for (int r = 0; r < 2; ++r) {
         std::stable_sort(big[r].begin(), big[r].end(), by_work);
         std::stable_sort(small[r].begin(), small[r].end(), by_work);
-        b->q[r].offset = (int)order.size();
+        b->q[r].offset = (int)b->order.size();
         b->q[r].n_big = (int)big[r].size();
         b->q[r].n_small = (int)small[r].size();
-        order.insert(order.end(), big[r].begin(), big[r].end());
-        order.insert(order.end(), small[r].begin(), small[r].end());
+        b->order.insert(b->order.end(), big[r].begin(), big[r].end());
+        b->order.insert(b->order.end(), small[r].begin(), small[r].end());
     }
-
-    cudaError_t e = cudaMalloc(&b->d_jobs, sizeof(BatchJob) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 4 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_jobs, sizeof(BatchJob) * (size_t)n);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
-    if (e == cudaSuccess && !order.empty())  // empty when every lattice is huge
-        e = cudaMemcpy(b->d_order, order.data(), sizeof(int) * order.size(),
-                       cudaMemcpyHostToDevice);
-    // persistent grids: as many clusters as can be resident
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
-        if (b->q[r].n_big + b->q[r].n_small == 0) continue;
+    if (n > b->cap) {
+        // the pinned mirrors may still be the source of a queued upload
+        if (b->uploaded) ISING_BCHECK(cudaEventSynchronize(b->uploaded));
+        if (b->d_jobs) ISING_BCHECK(cudaFreeAsync(b->d_jobs, b->stream));
+        if (b->d_order) ISING_BCHECK(cudaFreeAsync(b->d_order, b->stream));
+        if (b->h_jobs) ISING_BCHECK(cudaFreeHost(b->h_jobs));
+        if (b->h_order) ISING_BCHECK(cudaFreeHost(b->h_order));
+        b->d_jobs = nullptr;
+        b->d_order = nullptr;
+        b->h_jobs = nullptr;
+        b->h_order = nullptr;
+        b->cap = 0;
+        const int cap = n;
+        ISING_BCHECK(pool_alloc(reinterpret_cast<void**>(&b->d_jobs), sizeof(BatchJob) * cap,
+                                *b->dp, b->stream));
+        ISING_BCHECK(pool_alloc(reinterpret_cast<void**>(&b->d_order), sizeof(int) * cap,
+                                *b->dp, b->stream));
+        ISING_BCHECK(cudaMallocHost(reinterpret_cast<void**>(&b->h_jobs), sizeof(BatchJob) * cap));
+        ISING_BCHECK(cudaMallocHost(reinterpret_cast<void**>(&b->h_order), sizeof(int) * cap));
+        b->cap = cap;
+    }
+    // persistent grids: as many clusters as can be resident (once per rule)
+    for (int r = 0; r < 2; ++r) {
+        if (b->q[r].n_big + b->q[r].n_small == 0 || b->grid[r] > 0) {
+            b->q[r].grid = b->grid[r];
+            continue;
+        }
         int clusters = 0;
-        e = resident_clusters(r, o.block_threads, o.cluster_size, &clusters);
-        b->q[r].grid = clusters * o.cluster_size;
+        ISING_BCHECK(resident_clusters(r, o.block_threads, o.cluster_size, &clusters));
+        b->grid[r] = clusters * o.cluster_size;
+        b->q[r].grid = b->grid[r];
     }
+    if (b->exec) {  // the captured launch holds the old queue sizes
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->table_valid = false;
+    b->order_dirty = true;
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ising_batch_create(ising_batch** out, ising_lattice* const* lats, int n,
+                       const int64_t* sweeps, const int* measure_every,
+                       const ising_batch_opts* opts, void* stream) {
+    if (!out) return ISING_EINVAL;
+    *out = nullptr;
+    ising_batch_opts o = {};
+    if (opts) o = *opts;
+    if (o.block_threads == 0) o.block_threads = 256;
+    if (o.cluster_size == 0) o.cluster_size = 4;
+    if (o.big_sites == 0) o.big_sites = 1 << 18;
+    if (o.huge_sites == 0) o.huge_sites = (int64_t)1 << 22;
+    if (o.block_threads != 128 && o.block_threads != 256) return ISING_EINVAL;
+    if (o.cluster_size < 1 || o.cluster_size > 8) return ISING_EINVAL;
+    int rc = check_members(lats, n, sweeps, measure_every);
+    if (rc != ISING_OK) return rc;
+    const DeviceProps* dp = nullptr;
+    rc = device_props(&dp);
+    if (rc != ISING_OK) return rc;
+    ising_batch* b = new (std::nothrow) ising_batch();
+    if (!b) return ISING_ENOMEM;
+    b->opts = o;
+    b->dp = dp;
+    b->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = pool_alloc(reinterpret_cast<void**>(&b->d_counters), 4 * sizeof(int), *dp,
+                               b->stream);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_fail(e);
     }
+    rc = assign_members(b, lats, n, sweeps, measure_every);
+    if (rc != ISING_OK) {
+        free_batch(b);
+        return rc;
+    }
     *out = b;
     return ISING_OK;
+}
+
+int ising_batch_update(ising_batch* b, ising_lattice* const* lats, int n, const int64_t* sweeps,
+                       const int* measure_every) {
+    if (!b) return ISING_EINVAL;
+    const int rc = check_members(lats, n, sweeps, measure_every);
+    if (rc != ISING_OK) return rc;
+    return assign_members(b, lats, n, sweeps, measure_every);
 }
 
 int ising_batch_launch(ising_batch* b) {
@@ -493,7 +567,7 @@ int ising_batch_launch(ising_batch* b) {
         const int rc = ising_sweep(b->lats[i], b->sweeps[i], b->every[i]);
         if (rc != ISING_OK) return rc;
     }
-    ISING_BCHECK(cudaEventSynchronize(b->uploaded));  // the mirror is free to change
+    ISING_BCHECK(cudaEventSynchronize(b->uploaded));  // the mirrors are free to change
     for (int i = 0; i < n; ++i) {
         if (!b->in_table[i]) continue;
         ising_lattice* h = b->lats[i];
@@ -507,11 +581,17 @@ int ising_batch_launch(ising_batch* b) {
     }
     // records reserved for later launches must stay inside the capacity: if the
     // last reserve is about to run out, the table is rebuilt (moved == true)
-    if (moved) {
+    if (moved || b->order_dirty) {
         ISING_BCHECK(cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(BatchJob) * (size_t)n,
                                      cudaMemcpyHostToDevice, b->stream));
+        if (b->order_dirty && !b->order.empty()) {  // empty when every lattice is huge
+            std::memcpy(b->h_order, b->order.data(), sizeof(int) * b->order.size());
+            ISING_BCHECK(cudaMemcpyAsync(b->d_order, b->h_order, sizeof(int) * b->order.size(),
+                                         cudaMemcpyHostToDevice, b->stream));
+        }
         ISING_BCHECK(cudaEventRecord(b->uploaded, b->stream));
         b->table_valid = true;
+        b->order_dirty = false;
     }
     if (b->opts.use_graph >= 0 && !b->exec && queued_jobs(b) > 0) {
         // capture [reset queue counters, persistent kernel] once; replay it

@@ -59,10 +59,22 @@ int device_props(const DeviceProps** out) {
         q.h_err = static_cast<volatile int*>(flag);
         *q.h_err = 0;
         ISING_CHECK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&q.d_err), flag, 0));
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        ISING_CHECK(cudaMemPoolCreate(&q.pool, &props));
+        uint64_t keep = UINT64_MAX;  // never hand freed blocks back on a synchronisation
+        ISING_CHECK(cudaMemPoolSetAttribute(q.pool, cudaMemPoolAttrReleaseThreshold, &keep));
         p = q;
     }
     *out = &p;
     return ISING_OK;
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, const DeviceProps& dp, cudaStream_t st) {
+    return cudaMallocFromPoolAsync(p, bytes, dp.pool, st);
 }
 
 // floor(exp(-x) * 2^32) for x = 2 beta k > 0, decided exactly.  The double
@@ -161,16 +173,18 @@ void rule_thresholds(const ising_lattice* h, uint32_t out[7]) {
         std::memcpy(out, h->thr, sizeof(h->thr));
 }
 
+// Device buffers go back to the pool in the handle's stream order (after the
+// work already queued there), so nothing waits here.
 void free_device(ising_lattice* h) {
     for (void*& p : h->col) {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, h->stream);
         p = nullptr;
     }
     for (void*& p : h->dem) {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, h->stream);
         p = nullptr;
     }
-    if (h->obs) cudaFree(h->obs);
+    if (h->obs) cudaFreeAsync(h->obs, h->stream);
     h->obs = nullptr;
     if (h->host_obs) cudaFreeHost(h->host_obs);
     h->host_obs = nullptr;
@@ -190,7 +204,7 @@ int ensure_records(ising_lattice* h, int64_t need) {
     if (cap < need) cap = need;
     if (cap < 64) cap = 64;
     unsigned long long* nb = nullptr;
-    ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&nb), (size_t)cap * 16, h->stream));
+    ISING_CHECK(pool_alloc(reinterpret_cast<void**>(&nb), (size_t)cap * 16, *h->dp, h->stream));
     ISING_CHECK(cudaMemsetAsync(nb, 0, (size_t)cap * 16, h->stream));
     if (h->n_rec > 0)
         ISING_CHECK(cudaMemcpyAsync(nb, h->obs, (size_t)h->n_rec * 16, cudaMemcpyDeviceToDevice,
@@ -411,7 +425,7 @@ int ising_create(ising_lattice** out, int dims, int L, double beta, uint64_t see
     else
         h->col_bytes = (((size_t)h->half_sites + 15) & ~(size_t)15) + 16;
     for (int c = 0; c < 2; ++c) {
-        cudaError_t e = cudaMalloc(&h->col[c], h->col_bytes);
+        cudaError_t e = ising::pool_alloc(&h->col[c], h->col_bytes, *dp, h->stream);
         if (e != cudaSuccess) {
             free_device(h);
             delete h;
@@ -654,7 +668,7 @@ int ising_get_spins(ising_lattice* h, int8_t* host_out) {
         ISING_CHECK(ising::export_spins(h, static_cast<int8_t*>(d)));
     } else {
         int8_t* tmp = nullptr;
-        ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+        ISING_CHECK(ising::pool_alloc(reinterpret_cast<void**>(&tmp), (size_t)h->sites, *h->dp, h->stream));
         cudaError_t e = ising::export_spins(h, tmp);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(host_out, tmp, (size_t)h->sites, cudaMemcpyDeviceToHost,
@@ -694,7 +708,7 @@ int ising_set_spins(ising_lattice* h, const int8_t* host_in, uint64_t t) {
         ISING_CHECK(ising::import_spins(h, static_cast<const int8_t*>(d), nullptr));
     } else {
         int8_t* tmp = nullptr;
-        ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+        ISING_CHECK(ising::pool_alloc(reinterpret_cast<void**>(&tmp), (size_t)h->sites, *h->dp, h->stream));
         cudaError_t e = cudaMemcpyAsync(tmp, host_in, (size_t)h->sites, cudaMemcpyHostToDevice,
                                         h->stream);
         if (e == cudaSuccess) e = ising::import_spins(h, tmp, nullptr);
@@ -765,7 +779,7 @@ int ising_set_demons(ising_lattice* h, const uint8_t* host_q, int fill, int qmax
     const size_t dem_bytes = packed ? 2 * h->col_bytes : h->col_bytes;
     for (int c = 0; c < 2; ++c) {
         if (h->dem[c]) continue;
-        ISING_CHECK(cudaMalloc(&h->dem[c], dem_bytes));
+        ISING_CHECK(ising::pool_alloc(&h->dem[c], dem_bytes, *h->dp, h->stream));
         ISING_CHECK(cudaMemsetAsync(h->dem[c], 0, dem_bytes, h->stream));
     }
     if (!host_q && packed && fill != 0) {
@@ -775,7 +789,7 @@ int ising_set_demons(ising_lattice* h, const uint8_t* host_q, int fill, int qmax
     }
     if (host_q) {
         uint8_t* tmp = nullptr;
-        ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+        ISING_CHECK(ising::pool_alloc(reinterpret_cast<void**>(&tmp), (size_t)h->sites, *h->dp, h->stream));
         cudaError_t e = cudaMemcpyAsync(tmp, host_q, (size_t)h->sites, cudaMemcpyHostToDevice,
                                         h->stream);
         if (e == cudaSuccess)
@@ -803,7 +817,7 @@ int ising_set_demons(ising_lattice* h, const uint8_t* host_q, int fill, int qmax
 int ising_get_demons(ising_lattice* h, uint8_t* host_out) {
     if (!h || !host_out || !h->dem[0]) return ISING_EINVAL;
     uint8_t* tmp = nullptr;
-    ISING_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (size_t)h->sites, h->stream));
+    ISING_CHECK(ising::pool_alloc(reinterpret_cast<void**>(&tmp), (size_t)h->sites, *h->dp, h->stream));
     cudaError_t e =
         h->layout == ISING_BITPACK
             ? ising::demon_packed_export(static_cast<const uint32_t*>(h->dem[0]),
@@ -892,9 +906,20 @@ int ising_test_inject_timeout(int on) {
 
 void ising_destroy(ising_lattice* h) {
     if (!h) return;
-    cudaStreamSynchronize(h->stream);
+    // pinned host buffers that queued work may still touch are freed only
+    // after that work; device memory returns to the pool in stream order
+    if (h->host_obs || h->bad_host) cudaStreamSynchronize(h->stream);
     free_device(h);
     delete h;
+}
+
+int ising_release_cached_memory(void) {
+    const DeviceProps* dp = nullptr;
+    const int rc = device_props(&dp);
+    if (rc != ISING_OK) return rc;
+    ISING_CHECK(cudaDeviceSynchronize());
+    ISING_CHECK(cudaMemPoolTrimTo(dp->pool, 0));
+    return ISING_OK;
 }
 
 }  // extern "C"

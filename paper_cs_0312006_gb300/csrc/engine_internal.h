@@ -58,6 +58,10 @@ struct DeviceProps {
     // host memory (device view d_err, host view h_err), read without a copy
     int* d_err = nullptr;
     volatile int* h_err = nullptr;
+    // the library's stream-ordered pool for lattice memory (spin, demon and
+    // record buffers): freed blocks stay reserved for the next lattice, so
+    // creating and destroying lattices never synchronises the device
+    cudaMemPool_t pool = nullptr;
 };
 
 // Launch `kernel` on `st` with programmatic stream serialisation: it may be
@@ -86,6 +90,8 @@ bool injecting_timeout();
 // the threshold table of the lattice's rule, as the kernels take it (PassArgs::thr)
 void rule_thresholds(const ising_lattice* h, uint32_t out[7]);
 int device_props(const DeviceProps** out);
+// stream-ordered allocation from the device's lattice pool
+cudaError_t pool_alloc(void** p, size_t bytes, const DeviceProps& dp, cudaStream_t st);
 int ensure_records(ising_lattice* h, int64_t need);
 // n sweeps of a small lattice in one persistent single-CTA launch (batch.cu)
 int small_sweep(ising_lattice* h, int64_t n, int every, unsigned long long* slots);

@@ -625,19 +625,63 @@ __device__ __forceinline__ uint32_t group_accept(const K& k, const Philox4& u, i
     return acc;
 }
 
+// Accept mask of a 16-site half of a packed word whose first bit is half
+// index g0 * 4 + M + 16 * HALF (M = 1..3: the row starts inside a Philox
+// group).  Its sites draw from the five groups g0 + 4 HALF .. g0 + 4 HALF + 4
+// (bit b takes word (M + b) & 3 of group g0 + ((M + b) >> 2)); the five calls
+// are made together, and every index is a compile-time constant.
+template <int DIMS, int M, int HALF, typename K>
+__device__ __forceinline__ uint32_t packed_accept_half_shifted(const K& k, uint32_t g0,
+                                                               const PassArgs& a, uint32_t c2) {
+    Philox4 u[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        u[i] = philox4x32_10(g0 + (uint32_t)(4 * HALF + i), a.t, c2, kTagSweep, a.key0, a.key1);
+    uint32_t acc = 0u;
+#pragma unroll
+    for (int b = 16 * HALF; b < 16 * HALF + 16; ++b) {
+        const int q = M + b - 16 * HALF;  // draw index within the five calls
+        const Philox4& g = u[q >> 2];
+        const uint32_t w = (q & 3) == 0 ? g.w0 : (q & 3) == 1 ? g.w1 : (q & 3) == 2 ? g.w2 : g.w3;
+        acc |= (w < site_threshold<DIMS>(k, b, a) ? 1u : 0u) << b;
+    }
+    return acc;
+}
+
+template <int DIMS, int M, typename K>
+__device__ __forceinline__ uint32_t packed_accept_shifted(const K& k, uint32_t need, uint32_t g0,
+                                                          const PassArgs& a, uint32_t c2) {
+    uint32_t acc = 0u;
+    if (need & 0xFFFFu) acc |= packed_accept_half_shifted<DIMS, M, 0>(k, g0, a, c2);
+    if (need >> 16) acc |= packed_accept_half_shifted<DIMS, M, 1>(k, g0, a, c2);
+    return acc;
+}
+
 // Accept mask of the `need` bits of a packed word (Metropolis: the sites with
 // dE > 0; heat bath: every valid site) whose 32 bits are the half indices
 // hb = hbase + b (b = 0..31).  Bit b's draw
 // is word (hb & 3) of Philox group hb >> 2.  When hbase is a multiple of 4 the
 // eight groups are the word's nibbles and are computed four at a time; when a
 // row starts inside a group (W not a multiple of 4) the word spans nine
-// groups, taken one at a time (measured faster here than interleaving them,
-// which raises register pressure in the batched kernel).
-template <int DIMS, typename K>
+// groups.  With ILP9 (the per-lattice pass), when the lanes of the warp share
+// the row offset, each half takes its five groups together
+// (packed_accept_shifted); otherwise, and in the batched kernel (which runs at
+// a fixed register budget), the nine are taken one at a time.
+template <int DIMS, typename K, bool ILP9 = false>
 __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uint32_t hbase,
                                                   const PassArgs& a, uint32_t c2) {
     uint32_t acc = 0u;
     const uint32_t m = hbase & 3u, g0 = hbase >> 2;
+    if (ILP9 && m != 0u) {
+        // the compile-time offset paths only when the warp agrees on it
+        const uint32_t lanes = __activemask();
+        const uint32_t m0 = __shfl_sync(lanes, m, __ffs(lanes) - 1);
+        if (__all_sync(lanes, m == m0)) {
+            if (m == 1u) return packed_accept_shifted<DIMS, 1>(k, need, g0, a, c2);
+            if (m == 2u) return packed_accept_shifted<DIMS, 2>(k, need, g0, a, c2);
+            return packed_accept_shifted<DIMS, 3>(k, need, g0, a, c2);
+        }
+    }
     if (m == 0u) {
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
@@ -675,15 +719,43 @@ __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uin
 // when xh < W; the other bits of a row's last word stay 0 and never flip).
 // The x-neighbour wrap at the row ends comes from the row's last valid bit
 // (p = 0, first word) or first bit (p = 1, last word).
-template <int DIMS, bool MEASURE, int NC, int RULE = kRuleMetropolis>
+//
+// With rgroups > 1 the items visit the rows grouped by r mod rgroups: every
+// row of a group starts at the same offset inside a Philox group (r W mod 4
+// depends only on r mod 4 for odd W, on r mod 2 for W = 2 mod 4), so the lanes
+// of a warp share it and take the five-call path together instead of
+// diverging over all four offsets.  Group c holds rows c, c + rgroups, ...
+// (the first rows mod rgroups groups one row more).
+__host__ __device__ __forceinline__ uint32_t packed_row_groups(uint32_t W) {
+    return (W & 1u) ? 4u : ((W & 3u) == 2u ? 2u : 1u);
+}
+
+__device__ __forceinline__ uint32_t grouped_row(uint32_t j, uint32_t rows, uint32_t rgroups) {
+    const uint32_t G = rows / rgroups, rem = rows - G * rgroups;
+    const uint32_t head = rem * (G + 1u);  // rows in the longer groups
+    uint32_t c, k;
+    if (j < head) {
+        c = j / (G + 1u);
+        k = j - c * (G + 1u);
+    } else {
+        const uint32_t jj = j - head;
+        c = G ? jj / G : 0u;
+        k = jj - c * G;
+        c += rem;
+    }
+    return k * rgroups + c;
+}
+
+template <int DIMS, bool MEASURE, int NC, int RULE = kRuleMetropolis, bool ILP9 = false>
 __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, int& e_acc,
-                                            int& m_acc) {
+                                            int& m_acc, uint32_t rgroups = 1u) {
     const uint32_t W = (uint32_t)a.W;
     const uint32_t nq = (W + 31u) >> 5;
     const uint32_t L = (uint32_t)a.L;
     uint32_t* own = static_cast<uint32_t*>(a.own);
     const uint32_t* other = static_cast<const uint32_t*>(a.other);
-    const uint32_t r = item / nq, q = item - r * nq;
+    const uint32_t j = item / nq, q = item - j * nq;
+    const uint32_t r = rgroups > 1u ? grouped_row(j, (uint32_t)a.rows, rgroups) : j;
     uint32_t y = r, z = 0;
     if (DIMS == 3) {
         z = r / L;
@@ -726,7 +798,7 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
     if constexpr (RULE == kRuleHeatBath) {  // every valid site draws
         const Digits k = DIMS == 2 ? digits2(s ^ o, s ^ sh, s ^ oym, s ^ oyp)
                                    : digits3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
-        flip = packed_accept<DIMS>(k, valid, r * W + 32u * q, a, (uint32_t)a.c);
+        flip = packed_accept<DIMS, Digits, ILP9>(k, valid, r * W + 32u * q, a, (uint32_t)a.c);
     } else if constexpr (RULE == kRuleMultiHit) {  // a.hits trials, neighbours fixed
         uint32_t cur = s;
 #pragma unroll 1
@@ -740,8 +812,8 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
             uint32_t f = k.always;
             const uint32_t need = ~k.always & valid;
             if (need)
-                f |= packed_accept<DIMS>(k, need, r * W + 32u * q, a,
-                                         (uint32_t)a.c + 2u * (uint32_t)m);
+                f |= packed_accept<DIMS, Counts, ILP9>(k, need, r * W + 32u * q, a,
+                                                       (uint32_t)a.c + 2u * (uint32_t)m);
             cur ^= f & valid;
         }
         flip = cur ^ s;
@@ -754,7 +826,7 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
         }
         flip = k.always;
         const uint32_t need = ~k.always & valid;
-        if (need) flip |= packed_accept<DIMS>(k, need, r * W + 32u * q, a, (uint32_t)a.c);
+        if (need) flip |= packed_accept<DIMS, Counts, ILP9>(k, need, r * W + 32u * q, a, (uint32_t)a.c);
     }
     const uint32_t snew = s ^ (flip & valid);
     own[row + q] = snew;

@@ -28,15 +28,17 @@ namespace ising {
 namespace {
 
 // One item = one 32-site word of the colour array (see packed_word()).
+// Rows that start inside a Philox group are visited grouped by their offset
+// (rgroups, see packed_word).
 template <int DIMS, bool MEASURE, int RULE>
-__global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a) {
+__global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a, uint32_t rgroups) {
     const uint32_t items = (uint32_t)a.rows * (((uint32_t)a.W + 31u) >> 5);
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_acc = 0;
     grid_dependency_wait();
     launch_dependents();
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride)
-        packed_word<DIMS, MEASURE, 1, RULE>(a, g, e_acc, m_acc);
+        packed_word<DIMS, MEASURE, 1, RULE, RULE != kRuleMultiHit>(a, g, e_acc, m_acc, rgroups);
     if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
 }
 
@@ -121,7 +123,11 @@ cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream
     const int64_t cap = (int64_t)dp.sm_count * dp.blocks_per_sm_packed[RULE][DIMS - 2][MEASURE];
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    return launch_chained(pass_packed<DIMS, MEASURE, RULE>, (unsigned)blocks, 256u, 0, st, a);
+    // odd W: a row's offset in its Philox group is r W mod 4, set by r mod 4;
+    // W = 2 mod 4: by r mod 2
+    const uint32_t rgroups = packed_row_groups((uint32_t)a.W);
+    return launch_chained(pass_packed<DIMS, MEASURE, RULE>, (unsigned)blocks, 256u, 0, st, a,
+                          rgroups);
 }
 
 }  // namespace
@@ -130,7 +136,7 @@ cudaError_t packed_query_occupancy(DeviceProps& dp) {
     cudaError_t e;
 #define ISING_OCC(R, D, M)                                                                    \
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_packed[R][D - 2][M],   \
-                                                      pass_packed<D, M, R>, 256, 0);           \
+                                                      pass_packed<D, M, R>, 256, 0);          \
     if (e != cudaSuccess) return e;
     ISING_OCC(kRuleMetropolis, 2, false)
     ISING_OCC(kRuleMetropolis, 2, true)

@@ -104,10 +104,13 @@ def load_library():
             "ising_philox_probe": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_uint64, P], ctypes.c_int),
             "ising_destroy": ([P], None),
+            "ising_release_cached_memory": ([], ctypes.c_int),
             "ising_batch_create": ([ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int, i64p,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(BatchOpts), P],
                                    ctypes.c_int),
             "ising_batch_launch": ([P], ctypes.c_int),
+            "ising_batch_update": ([P, ctypes.POINTER(P), ctypes.c_int, i64p,
+                                    ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "ising_batch_sync": ([P], ctypes.c_int),
             "ising_batch_info": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -372,6 +375,21 @@ class Batch:
                                       ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                       ctypes.byref(opts), ctypes.c_void_p(int(raw) if raw else 0)),
                "ising_batch_create")
+
+    def update(self, lattices, sweeps, measure_every=1) -> None:
+        """``ising_batch_update``: replace the batch's lattices and sweep counts
+        (the next launch advances these), keeping its device tables."""
+        self.lattices = list(lattices)
+        n = len(self.lattices)
+        sw = np.asarray(np.broadcast_to(np.asarray(sweeps, dtype=np.int64), (n,)),
+                        dtype=np.int64).copy()
+        ev = np.asarray(np.broadcast_to(np.asarray(measure_every, dtype=np.int32), (n,)),
+                        dtype=np.int32).copy()
+        handles = (ctypes.c_void_p * n)(*[lat.handle for lat in self.lattices])
+        _check(self._lib.ising_batch_update(self._h, handles, n,
+                                            sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                            ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+               "ising_batch_update")
 
     def launch(self) -> None:
         _check(self._lib.ising_batch_launch(self._h), "ising_batch_launch")

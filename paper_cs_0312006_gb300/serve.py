@@ -19,6 +19,16 @@ of the round).  Short jobs therefore finish within a round or two while
 20,000-sweep 4096^2 jobs progress at the GPU's full rate.  Because draws are
 keyed by (seed, sweep, colour, site), a job's result does not depend on which
 round or mix it ran in.
+
+With engine lattices the rounds are pipelined: one long-lived batch is
+updated in place each round (``ising_batch_update``), the huge jobs run
+their per-lattice sweeps on a second stream so that they overlap the
+persistent launch, each round's records are gathered into one half of a
+pinned double buffer, and round k + 1 is queued before round k's records are
+read and its finished jobs retired; lattice memory comes from the library's
+stream-ordered pool, so admitting and retiring jobs never waits for the
+device.  The class rates that size the quanta start from the constants below
+and follow each round's measured GPU times.
 """
 from __future__ import annotations
 
@@ -57,6 +67,7 @@ class _Resident:
     admit_s: float
     E: list = field(default_factory=list)
     M: list = field(default_factory=list)
+    last_round: int = -1  # pipelined mode: the last round this job was queued in
 
 
 def job_bytes(spec) -> int:
@@ -76,11 +87,16 @@ class Server:
     RATE_FULL = 6e11
     RATE_CLUSTER = 2.5e10
     RATE_CTA = 1.0e9
+    # pipelined mode: starting rates per slot (one CTA, one cluster), then
+    # adapted to the measured time of each persistent launch
+    RATE_CTA_SLOT = 1.5e9
+    RATE_CLUSTER_SLOT = 1.0e10
 
     def __init__(self, hbm_budget_bytes: int = 120 * 10 ** 9, max_resident: int = 4096,
                  round_s: float = 0.05, min_quantum: int = 1, keep_spins: bool = True,
                  batch_opts: dict | None = None, stream=None, clock=time.perf_counter,
-                 lattice_factory=None, batch_factory=None, gather_records=None):
+                 lattice_factory=None, batch_factory=None, gather_records=None,
+                 pipelined=None, adapt_rates: bool = True):
         self.budget = int(hbm_budget_bytes)
         self.max_resident = max_resident
         self.round_s = float(round_s)
@@ -107,6 +123,19 @@ class Server:
         self.t0 = None
         self._pinned = None  # host buffer of the records' gather (grown on demand)
         self._pinned_grow = False
+        # class rates that size the quanta (pipelined mode: adapted to measured times)
+        self.pipelined = (self.lattice_factory is engine.Lattice) if pipelined is None \
+            else bool(pipelined)
+        self.rate_full, self.rate_cluster, self.rate_cta = (self.RATE_FULL, self.RATE_CLUSTER,
+                                                            self.RATE_CTA)
+        if self.pipelined:  # per slot: the quanta share each class's slots
+            self.rate_cluster, self.rate_cta = self.RATE_CLUSTER_SLOT, self.RATE_CTA_SLOT
+        self.adapt_rates = adapt_rates
+        # launch shape of the persistent kernel, for the processor-sharing quanta
+        self.cluster_size = int(self.batch_opts.get("cluster_size") or 8)
+        self.default_grid = 456
+        self.round_log = []  # pipelined mode: (small jobs, huge jobs, GPU s of each part)
+        self._admit_streams = None
 
     # -- requests ---------------------------------------------------------
     def submit(self, job: Job) -> None:
@@ -127,8 +156,12 @@ class Server:
             if (not blocked and job.arrival_s <= now and len(self.resident) < self.max_resident
                     and self.bytes_in_use + need <= self.budget):
                 sp = job.spec
+                stream = self.stream
+                if self._admit_streams is not None:  # pipelined: huge jobs on their own stream
+                    huge = self.huge_sites > 0 and sp.sites >= self.huge_sites
+                    stream = self._admit_streams[1 if huge else 0]
                 lat = self.lattice_factory(sp.dims, sp.L, sp.beta, sp.seed, layout=sp.layout,
-                                           start=sp.start, stream=self.stream)
+                                           start=sp.start, stream=stream)
                 self.resident.append(_Resident(job, lat, need, sp.sweeps, now))
                 self.bytes_in_use += need
                 self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
@@ -140,16 +173,17 @@ class Server:
 
     def _rate(self, sites: int, n_huge: int) -> float:
         if self.huge_sites > 0 and sites >= self.huge_sites:
-            return self.RATE_FULL / max(n_huge, 1)
+            return self.rate_full / max(n_huge, 1)
         if sites >= self.big_sites:
-            return self.RATE_CLUSTER
-        return self.RATE_CTA
+            return self.rate_cluster
+        return self.rate_cta
 
-    def _quanta(self) -> list:
-        n_huge = sum(1 for r in self.resident
+    def _quanta(self, resident=None) -> list:
+        resident = self.resident if resident is None else resident
+        n_huge = sum(1 for r in resident
                      if self.huge_sites > 0 and r.job.spec.sites >= self.huge_sites)
         q = []
-        for r in self.resident:
+        for r in resident:
             sites = r.job.spec.sites
             sweeps = max(self.min_quantum,
                          int(self.round_s * self._rate(sites, n_huge) // sites))
@@ -225,17 +259,191 @@ class Server:
             self.submit(j)
         self.pending.sort(key=lambda j: (j.arrival_s, j.job_id))
         self.t0 = self.clock()
-        while self.pending or self.resident:
-            self._admit()
-            if self.resident:
-                self._round()
-            else:
-                nxt = self.pending[0].arrival_s
-                wait = nxt - self.now()
-                if wait > 0:
-                    time.sleep(min(wait, 0.01))
+        if self.pipelined:
+            self._run_pipelined()
+        else:
+            while self.pending or self.resident:
+                self._admit()
+                if self.resident:
+                    self._round()
+                else:
+                    self._idle()
         makespan = self.now()
         return self.summary(makespan)
+
+    def _idle(self) -> None:
+        if self.pending:
+            wait = self.pending[0].arrival_s - self.now()
+            if wait > 0:
+                time.sleep(min(wait, 0.01))
+
+    # -- pipelined rounds (engine lattices) ------------------------------------
+    # Device operations behind small hooks (streams, events, the records
+    # gather), so that the scheduling can be driven on the CPU by stand-ins.
+    def _new_stream(self):
+        import torch
+        return torch.cuda.Stream()
+
+    def _record(self, stream, timing: bool = False):
+        import torch
+        ev = torch.cuda.Event(enable_timing=timing)
+        ev.record(stream)
+        return ev
+
+    def _gather(self, lats, slot: int):
+        """Queue one gather of ``lats``' pending records into the pinned
+        buffer of ``slot``; returns (buffer, counts).  The buffer doubles when
+        the records do not fit (nothing is queued then)."""
+        while True:
+            buf = self._bufs.get(slot)
+            if buf is None or self._grow.get(slot):
+                cap = max(1024, 2 * (0 if buf is None else len(buf)))
+                buf = self._alloc_pinned(cap)
+                self._bufs[slot] = buf
+                self._grow[slot] = False
+            try:
+                return buf, engine.observables_gather(lats, buf)
+            except engine.IsingError as e:
+                if e.code != engine.ERANGE:
+                    raise
+                self._grow[slot] = True
+
+    def _is_huge(self, r) -> bool:
+        return self.huge_sites > 0 and r.job.spec.sites >= self.huge_sites
+
+    def _slots(self, batch):
+        """Resident CTAs and clusters of the persistent launch."""
+        grid = batch.info()["grid"] if batch is not None else 0
+        if grid <= 0:
+            grid = self.default_grid
+        return grid, max(1, grid // self.cluster_size)
+
+    def _shared_quanta(self, active, in_batch_huge: bool, batch):
+        """Sweeps per job for one round, by processor sharing within each
+        execution class: the class's time budget times its rate per slot times
+        min(1, slots / jobs), over the job's sites.  Huge jobs run by the
+        per-lattice kernels share the whole GPU; while there are at least as
+        many of them as clusters they are cluster jobs instead."""
+        n_cta, n_cl = self._slots(batch)
+        huge = [r for r in active if self._is_huge(r)]
+        cls = {}
+        for r in active:
+            if self._is_huge(r) and not in_batch_huge:
+                cls[id(r)] = "huge"
+            elif r.job.spec.sites >= self.big_sites:
+                cls[id(r)] = "cluster"
+            else:
+                cls[id(r)] = "cta"
+        count = {c: sum(1 for r in active if cls[id(r)] == c) for c in ("huge", "cluster", "cta")}
+        both = count["cluster"] > 0 and count["cta"] > 0
+        budget = self.round_s / 2 if both else self.round_s
+        capacity = {"cluster": budget * self.rate_cluster * min(1.0, n_cl / max(1, count["cluster"])),
+                    "cta": budget * self.rate_cta * min(1.0, n_cta / max(1, count["cta"])),
+                    "huge": self.round_s * self.rate_full / max(1, len(huge))}
+        q = []
+        for r in active:
+            sweeps = max(self.min_quantum, int(capacity[cls[id(r)]] // r.job.spec.sites))
+            every = r.job.spec.measure_every
+            if sweeps > every:  # whole measurement intervals keep rounds aligned
+                sweeps -= sweeps % every
+            q.append(min(r.remaining, sweeps))
+        return q, cls
+
+    def _run_pipelined(self) -> None:
+        st = self._new_stream()
+        self._admit_streams = (st, st)
+        self._bufs, self._grow = {}, {}
+        batch = None
+        opts = dict(self.batch_opts)
+        opts["huge_sites"] = -1  # the huge jobs' per-lattice sweeps are issued here
+        opts.setdefault("cluster_size", self.cluster_size)
+        opts.setdefault("big_sites", self.big_sites)
+        inflight = None
+        slot = 0
+        while self.pending or self.resident or inflight is not None:
+            self._admit()
+            active = [r for r in self.resident if r.remaining > 0]
+            issued = None
+            if active:
+                _, n_cl = self._slots(batch)
+                in_batch_huge = sum(1 for r in active if self._is_huge(r)) >= n_cl
+                quanta, cls = self._shared_quanta(active, in_batch_huge, batch)
+                per_lattice = [(r, q) for r, q in zip(active, quanta) if cls[id(r)] == "huge"]
+                in_batch = [(r, q) for r, q in zip(active, quanta) if cls[id(r)] != "huge"]
+                ev = {"t0": self._record(st, timing=True)}
+                for r, q in per_lattice:
+                    r.lat.sweep(q, r.job.spec.measure_every)
+                ev["t1"] = self._record(st, timing=True)
+                if in_batch:
+                    lats = [r.lat for r, _ in in_batch]
+                    sweeps = [q for _, q in in_batch]
+                    every = [r.job.spec.measure_every for r, _ in in_batch]
+                    if batch is None:
+                        batch = self.batch_factory(lats, sweeps, every, use_graph=False,
+                                                   stream=st, **opts)
+                    else:
+                        batch.update(lats, sweeps, every)
+                    batch.launch()
+                ev["t2"] = self._record(st, timing=True)
+                group = per_lattice + in_batch
+                buf, counts = self._gather([r.lat for r, _ in group], slot)
+                parts = [(group, buf, counts, self._record(st))]
+                for r, q in zip(active, quanta):
+                    r.remaining -= q
+                    r.last_round = self.rounds
+                    self.updates_done += q * r.job.spec.sites
+                issued = {"parts": parts, "ev": ev, "index": self.rounds,
+                          "n_small": len(in_batch), "n_huge": len(per_lattice),
+                          "huge_work": sum(q * r.job.spec.sites for r, q in per_lattice),
+                          "small_work": sum(q * r.job.spec.sites for r, q in in_batch)}
+                self.rounds += 1
+                slot ^= 1
+            if inflight is not None:
+                self._finish_round(inflight)
+            inflight = issued
+            if not active and inflight is None:
+                self._idle()
+        if batch is not None:
+            batch.close()
+
+    def _finish_round(self, rnd) -> None:
+        """Wait for a queued round, hand its records to the jobs, retire the
+        jobs it finished and adapt the class rates to its measured times."""
+        for group, buf, counts, done in rnd["parts"]:
+            done.synchronize()
+            off = 0
+            for (r, _), c in zip(group, counts):
+                r.E.append(buf[off:off + c, 0].copy())
+                r.M.append(buf[off:off + c, 1].copy())
+                off += int(c)
+        if rnd["parts"]:  # one bounded-wait / input check for the round
+            first_group = rnd["parts"][0][0]
+            first_group[0][0].lat.synchronize()
+        ev = rnd["ev"]
+        t_huge = ev["t0"].elapsed_time(ev["t1"]) / 1e3 if rnd["n_huge"] else 0.0
+        t_small = ev["t1"].elapsed_time(ev["t2"]) / 1e3 if rnd["n_small"] else 0.0
+        self.round_log.append((rnd["n_small"], rnd["n_huge"], t_small, t_huge))
+        if self.adapt_rates and rnd["huge_work"] > 0 and t_huge > 0:
+            self.rate_full = 0.5 * self.rate_full + 0.5 * rnd["huge_work"] / t_huge
+        if self.adapt_rates and rnd["small_work"] > 0 and t_small > 0:
+            # the persistent launch took t_small for work sized to round_s
+            f = min(4.0, max(0.25, self.round_s / t_small)) ** 0.5
+            f = min(f, 1.25)  # grow slowly: an underfilled round also runs short
+            self.rate_cluster *= f
+            self.rate_cta *= f
+        still = []
+        for r in self.resident:
+            if r.remaining == 0 and r.last_round == rnd["index"]:
+                spins = r.lat.get_spins() if self.keep_spins else None
+                self.results[r.job.job_id] = JobResult(
+                    r.job.job_id, r.job.arrival_s, r.admit_s, self.now(), r.job.spec.sweeps,
+                    r.job.spec.sites, np.concatenate(r.E) if r.E else np.zeros(0, np.int64),
+                    np.concatenate(r.M) if r.M else np.zeros(0, np.int64), spins)
+                r.lat.close()
+                self.bytes_in_use -= r.bytes
+            else:
+                still.append(r)
+        self.resident = still
 
     def summary(self, makespan: float, skip_first: int = 0) -> dict:
         res = sorted(self.results.values(), key=lambda r: r.job_id)

@@ -171,3 +171,27 @@ def test_batch_run_refusals(eng):
         assert ei.value.code == eng.EINVAL
     assert lat.info().sweeps_done == 0
     lat.close()
+
+
+def test_batch_update_between_launches_equals_alone(eng):
+    """One batch reused for changing lattice sets (ising_batch_update), the
+    second launch queued behind the first with no synchronisation: every
+    lattice ends as if its sweeps had run alone."""
+    specs = mix_specs(5, n=24)
+    lats = [eng.Lattice(d, L, b, sd, layout=lay) for (d, L, b, sd, lay, _, _) in specs]
+    first, second = list(range(0, 16)), list(range(8, 24))  # overlapping sets
+    batch = eng.Batch([lats[i] for i in first], [specs[i][5] for i in first],
+                      [specs[i][6] for i in first], cluster_size=2, big_sites=4096,
+                      use_graph=False)
+    batch.launch()
+    batch.update([lats[i] for i in second], [specs[i][5] for i in second],
+                 [specs[i][6] for i in second])
+    batch.launch()
+    batch.sync()
+    batch.close()
+    for i, (spec, lat) in enumerate(zip(specs, lats)):
+        launches = (i in first) + (i in second)
+        E, M = lat.observables()
+        got = (lat.get_spins(), E, M)
+        lat.close()
+        assert same(got, run_alone(eng, spec, launches=launches)), (i, spec)

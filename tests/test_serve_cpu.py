@@ -210,3 +210,74 @@ def test_records_gather_grows_its_buffer_and_matches_per_lattice_reads(monkeypat
         g = results[True][k]
         assert np.array_equal(r.E, g.E) and np.array_equal(r.M, g.M)
         assert len(g.E) == 3000
+
+
+class SweepLattice(GatherLattice):
+    """A stand-in that can also sweep alone (the pipelined loop's huge jobs)."""
+
+    def sweep(self, n, every):
+        for _ in range(n):
+            self.t += 1
+            if self.t % every == 0:
+                self.E.append(self.t)
+                self.M.append(-self.t)
+
+
+class UpdatableBatch(FakeBatch):
+    def info(self):
+        return {"grid": 16}
+
+    def update(self, lats, sweeps, every):
+        self.lats, self.sweeps, self.every = lats, list(sweeps), list(every)
+        FakeBatch.calls.append(list(sweeps))
+
+
+class FakeEvent:
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return 1.0  # ms
+
+
+class PipelinedHostServer(serve.Server):
+    """The pipelined loop with its device hooks on the host."""
+
+    def _new_stream(self):
+        return object()
+
+    def _record(self, stream, timing=False):
+        return FakeEvent()
+
+    def _gather(self, lats, slot):
+        buf = np.zeros((4096, 2), dtype=np.int64)
+        return buf, fake_gather(lats, buf)
+
+
+def test_pipelined_rounds_give_the_synchronous_results():
+    """Rounds queued ahead of the record reads, a long-lived batch updated in
+    place and huge jobs swept on their own stream: every job gets exactly the
+    records of the one-round-at-a-time loop and is retired once."""
+    def jobs():
+        out = []
+        for k in range(30):
+            L = 64 if k % 3 else 512  # every third job is huge here
+            sp = workloads.LatticeSpec(dims=2, L=L, beta=0.4, seed=k, sweeps=50 + 37 * k,
+                                       measure_every=5, layout=0, start=0)
+            out.append(workloads.Job(job_id=k, arrival_s=0.002 * k, spec=sp))
+        return out
+
+    results = {}
+    for pipelined in (False, True):
+        FakeLattice.live = 0
+        cls = PipelinedHostServer if pipelined else serve.Server
+        srv = cls(lattice_factory=SweepLattice, batch_factory=UpdatableBatch, clock=Clock(),
+                  round_s=1e-3, pipelined=pipelined, gather_records=False,
+                  batch_opts=dict(huge_sites=512 * 512))
+        summ = srv.run(jobs())
+        assert summ["jobs"] == 30 and FakeLattice.live == 0
+        results[pipelined] = srv.results
+    for k, r in results[False].items():
+        p = results[True][k]
+        assert np.array_equal(r.E, p.E) and np.array_equal(r.M, p.M), k
+        assert len(p.E) == (50 + 37 * k) // 5
