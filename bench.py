@@ -372,6 +372,12 @@ def run_gpu(args, world, rank, local):
     stream = torch.cuda.current_stream()
     int8_kernel = {"auto": engine.KERNEL_AUTO, "strip": engine.KERNEL_STRIP,
                    "tma": engine.KERNEL_TMA}[args.int8_kernel]
+    int8_tuned = None
+    if int8_kernel == engine.KERNEL_AUTO and args.layout in ("both", "int8"):
+        # the int8 pass configuration for this lattice shape, measured (or read
+        # from the cache) and registered so that ISING_KERNEL_AUTO runs it
+        from paper_cs_0312006_gb300 import autotune
+        int8_tuned = autotune.tune_int8(2, L, use_cache=not args.retune)
     rule = {"metropolis": engine.RULE_METROPOLIS, "heatbath": engine.RULE_HEATBATH,
             "demon": engine.RULE_METROPOLIS}[args.rule]
     sets = {name: [engine.Lattice(2, L, b, BASE_SEED + 16 * rank + j, layout=lay,
@@ -389,6 +395,7 @@ def run_gpu(args, world, rank, local):
                 lat.set_rule(engine.RULE_DEMON)
         del fields
     int8_ran = sets["int8"][0].kernel() if "int8" in sets else -1
+    int8_cfg = sets["int8"][0].int8_config() if "int8" in sets else None
 
     def barrier():
         if world > 1:
@@ -520,28 +527,50 @@ def run_gpu(args, world, rank, local):
     if not args.no_e2e:
         e2e = {}
         e2e_steps = args.e2e_steps or args.steps
-        # every lattice's initial spins and final spins live in pinned host
-        # memory, which the import and export kernels read and write directly
-        # (ising_set_spins_async / ising_get_spins_async); step k's (E, M)
-        # pairs land in one half of a pinned double buffer (one gather kernel)
-        # and are summed on the host while step k + 1 runs on the device
+        # every lattice's initial and final spins live in pinned host memory.
+        # The host<->device copies run on the copy engines of a second stream
+        # and overlap the other lattices' sweeps: lattice j's upload lands in a
+        # device buffer that ising_set_spins_async reads once its copy event
+        # has passed, and its final spins (ising_get_spins_async into a device
+        # buffer) go down while the later lattices finish their last sweep.
+        # Step k's (E, M) pairs land in one half of a pinned double buffer
+        # (one gather kernel) and are summed on the host while step k + 1 runs.
         host_init = torch.ones(n_sites, dtype=torch.int8).pin_memory()
         host_out = [torch.empty(n_sites, dtype=torch.int8).pin_memory() for _ in betas]
+        dev_in = [torch.empty(n_sites, dtype=torch.int8, device="cuda") for _ in betas]
+        dev_out = [torch.empty(n_sites, dtype=torch.int8, device="cuda") for _ in betas]
         pairs = torch.zeros((2, len(betas), 2), dtype=torch.int64).pin_memory().numpy()
         ready = [torch.cuda.Event(), torch.cuda.Event()]
+        copy_stream = torch.cuda.Stream()
         for name, lats in sets.items():
             barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h2d = d2h = 0
             host_sum = 0
-            for lat in lats:
-                lat.set_spins_async(host_init.data_ptr(), 0)  # H2D: the initial configuration
-                h2d += n_sites
+            uploaded = []
+            with torch.cuda.stream(copy_stream):
+                for j in range(len(lats)):  # H2D: every lattice's initial configuration
+                    dev_in[j].copy_(host_init, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(copy_stream)
+                    uploaded.append(ev)
+                    h2d += n_sites
             last = None
             for k in range(e2e_steps):
-                for lat in lats:
+                for j, lat in enumerate(lats):
+                    if k == 0:
+                        stream.wait_event(uploaded[j])
+                        lat.set_spins_async(dev_in[j].data_ptr(), 0)
                     lat.sweep(1, 1)
+                    if k == e2e_steps - 1:  # D2H of the final configuration
+                        lat.get_spins_async(dev_out[j].data_ptr())
+                        done = torch.cuda.Event()
+                        done.record(stream)
+                        copy_stream.wait_event(done)
+                        with torch.cuda.stream(copy_stream):
+                            host_out[j].copy_(dev_out[j], non_blocking=True)
+                        d2h += n_sites
                 half = k % 2
                 d2h += 16 * int(engine.observables_gather(lats, pairs[half]).sum())
                 ready[half].record(stream)
@@ -549,9 +578,6 @@ def run_gpu(args, world, rank, local):
                     ready[last].synchronize()
                     host_sum += int(pairs[last, :, 0].sum())
                 last = half
-            for lat, buf in zip(lats, host_out):
-                lat.get_spins_async(buf.data_ptr())  # D2H: the final configuration
-                d2h += n_sites
             torch.cuda.synchronize()
             host_sum += int(pairs[last, :, 0].sum())
             dt = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
@@ -561,17 +587,20 @@ def run_gpu(args, world, rank, local):
                          "seconds": dt, "h2d_bytes": h2d, "d2h_bytes": d2h,
                          "h2d_bytes_per_step": h2d / e2e_steps,
                          "d2h_bytes_per_step": d2h / e2e_steps}
+        del dev_in, dev_out
         head_e2e = e2e[head]
         e2e = {"value": head_e2e["value"], "unit": "site updates/s",
                "h2d_bytes_per_step": head_e2e["h2d_bytes_per_step"],
                "d2h_bytes_per_step": head_e2e["d2h_bytes_per_step"], "steps": e2e_steps,
                "layout": head, "layouts": e2e,
                "over_device_value": head_e2e["value"] / value,
-               "note": "per layout: ising_set_spins_async of every lattice from pinned host "
-                       "memory, then per step one sweep of each lattice and one "
-                       "ising_observables_gather of every lattice's (E, M) into pinned host "
-                       "memory (read on the host while the next step runs), then "
-                       "ising_get_spins_async of every lattice into pinned host memory"}
+               "note": "per layout: every lattice's initial spins copied from pinned host "
+                       "memory on a copy stream and loaded with ising_set_spins_async, then per "
+                       "step one sweep of each lattice and one ising_observables_gather of "
+                       "every lattice's (E, M) into pinned host memory (read on the host while "
+                       "the next step runs); each lattice's final spins written by "
+                       "ising_get_spins_async and copied to pinned host memory on the copy "
+                       "stream while the later lattices finish"}
 
     for lats in sets.values():
         for lat in lats:
@@ -593,6 +622,8 @@ def run_gpu(args, world, rank, local):
 
     forms = {}
     if world == 1 and not args.no_forms and args.rule == "metropolis":
+        forms["small"] = small_form(args)
+        forms["cubic"] = cubic_form(args, peak_hbm, ceiling)
         forms["batched"] = batched_form(args)
         forms["serving"] = serving_form(args)
 
@@ -613,6 +644,12 @@ def run_gpu(args, world, rank, local):
         "roofline": rooflines.get("int8") or rooflines.get("bitpack"),
         "roofline_bitpack": rooflines.get("bitpack"),
         "philox_ceiling": ceiling,
+        "int8_config": {"ran": int8_cfg,
+                        "tuned": None if int8_tuned is None else
+                        {"config": int8_tuned["config"],
+                         "candidates": [{"config": r["config"],
+                                         "site_updates_per_s": r["site_updates_per_s"]}
+                                        for r in int8_tuned["results"]]}},
         "gpu_launches": len(sets) * len(betas) * 2 * args.steps,
         "clocks": clocks,
         "e2e": e2e,
@@ -680,6 +717,84 @@ def serving_form(args) -> dict:
             "served_over_plain": summ["updates_per_s"] / plain["updates_per_s"],
             "offered_load_updates_per_s": serve.offered_load(jobs, args.serve_rate),
             "detail": dict(summ, **pct)}
+
+
+def cubic_form(args, peak_hbm: float, ceiling: dict) -> dict:
+    """3D cubic L=256 (16.8 M sites) at beta 0.2216544, hot start, seed
+    20031109, 1000 sweeps with E/M every 10 sweeps, in both layouts; the int8
+    pass configuration tuned for this shape; the int8 pass against the HBM
+    roofline (3 B per update) and the Philox ceiling."""
+    import torch
+    from paper_cs_0312006_gb300 import autotune, engine
+    L, beta, n = args.cubic_L, 0.2216544, args.cubic_sweeps
+    sites = L ** 3
+    tuned = autotune.tune_int8(3, L, use_cache=not args.retune)
+    out = {}
+    for name, lay in (("int8", engine.INT8), ("bitpack", engine.BITPACK)):
+        lat = engine.Lattice(3, L, beta, BASE_SEED, layout=lay)
+        lat.sweep(3, 10)  # warm-up
+        lat.observables()
+        lat.init(engine.HOT)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lat.sweep(n, 10)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        E, M = lat.observables()
+        cfg = lat.int8_config()
+        lat.close()
+        rate = sites * n / (ms / 1e3)
+        out[name] = {"value": rate, "ms": ms, "records": len(E), "us_per_sweep": ms * 1e3 / n,
+                     "int8_config": cfg if name == "int8" else None}
+    int8_rate = out["int8"]["value"]
+    achieved = BYTES_PER_UPDATE_INT8 * int8_rate / 1e9
+    return {"config": {"workload": f"3D cubic L={L}, beta 0.2216544, hot start, seed "
+                                   f"{BASE_SEED}, {n} sweeps, E/M every 10 sweeps, int8 and "
+                                   "bit-packed layouts"},
+            "value": int8_rate, "unit": "site updates/s", "layouts": out,
+            "int8_tuned": tuned["config"],
+            "roofline": {"kernel": "int8 pass (tuned configuration), 3D", "bound": "hbm",
+                         "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                         "frac": achieved / peak_hbm, "traffic": None,
+                         "frac_of_philox_ceiling": int8_rate / ceiling["draws_per_s"],
+                         "note": "whole sweeps timed (both passes, fused E/M every 10 sweeps)"}}
+
+
+def small_form(args) -> dict:
+    """The critical 2D L=64 run: beta 0.4406868, hot start, seed 20031109,
+    1000 sweeps with E/M every sweep, one single-CTA launch; median of five
+    runs, checked bit for bit against the oracle."""
+    import numpy as np
+    import torch
+    from paper_cs_0312006_gb300 import engine
+    import oracle
+    L, beta, n = 64, 0.4406868, 1000
+    lat = engine.Lattice(2, L, beta, BASE_SEED)
+    lat.sweep(n, 1)  # warm-up run
+    lat.observables()
+    times = []
+    for _ in range(5):
+        lat.init(engine.HOT)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lat.sweep(n, 1)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    E, M = lat.observables()
+    s = lat.get_spins()
+    lat.close()
+    s_o, E_o, M_o = oracle.run(2, L, beta, BASE_SEED, n, measure_every=1)
+    exact = bool(np.array_equal(s, s_o) and np.array_equal(E[-n:], E_o)
+                 and np.array_equal(M[-n:], M_o))
+    ms = sorted(times)[len(times) // 2]
+    return {"config": {"workload": "2D L=64, beta 0.4406868, hot start, seed 20031109, 1000 "
+                                   "sweeps, E/M every sweep"},
+            "value": L * L * n / (ms / 1e3), "unit": "site updates/s",
+            "us_per_sweep": ms * 1e3 / n, "bit_exact_vs_oracle": exact}
 
 
 def run_batched_workload(args):

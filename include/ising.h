@@ -52,7 +52,8 @@ enum {
 
 /* Kernels for the int8 colour pass (same results; see ising_set_kernel). */
 enum {
-    ISING_KERNEL_AUTO = 0,  /* staged for 2D with 4096 <= L <= 16384, strip otherwise (measured) */
+    ISING_KERNEL_AUTO = 0,  /* a registered configuration (ising_set_int8_config), else staged
+                               for 2D with 4096 <= L <= 16384 and strip otherwise (measured) */
     ISING_KERNEL_STRIP = 1, /* per-thread row strips, neighbour rows in registers */
     ISING_KERNEL_TMA = 2    /* tiles staged in shared memory by bulk (TMA) copies */
 };
@@ -260,6 +261,42 @@ int ising_set_kernel(ising_lattice *lat, int kernel);
  * stands for the general kernel used when L/2 is not a multiple of 16).  For
  * the bit-packed layout *kernel is set to -1. */
 int ising_get_kernel(const ising_lattice *lat, int *kernel);
+
+/*
+ * Tuned int8 pass configurations (for the autotuner).  A configuration names
+ * the kernel of the int8 colour pass and, for the staged kernel, its shape:
+ *   kernel       ISING_KERNEL_STRIP or ISING_KERNEL_TMA;
+ *   tile_rows    half rows per staged tile (of one plane in 3D): 1 (each
+ *                thread one row at a time) or 2, 4, ..., 64 (each thread two
+ *                rows at a time); 0: the engine's default for L (about 8 KiB
+ *                of own-colour rows);
+ *   ctas_per_sm  resident CTAs per SM of the staged kernel, 1..8 (fewer if
+ *                they do not fit); 0: as many as fit.
+ * Results never depend on the configuration.
+ */
+typedef struct ising_int8_config {
+    int kernel;
+    int tile_rows;
+    int ctas_per_sm;
+} ising_int8_config;
+
+/* Register `cfg` for int8 lattices of `dims` with L_min <= L <= L_max: their
+ * ISING_KERNEL_AUTO passes (and, for tile_rows and ctas_per_sm, their
+ * ISING_KERNEL_TMA passes) run it from the next sweep on; a later
+ * registration overrides an earlier one where they overlap; a configuration
+ * the staged kernel cannot take for some L (tile rows not dividing L, stages
+ * too large for shared memory) runs the general kernels there.  Process-wide
+ * (all devices); thread-safe.  ISING_EINVAL for dims not in {2, 3}, an empty
+ * range or a value out of range. */
+int ising_set_int8_config(int dims, int L_min, int L_max, const ising_int8_config *cfg);
+
+/* Drop every registered configuration (ISING_KERNEL_AUTO returns to the
+ * built-in choice: the staged kernel for 2D 4096 <= L <= 16384). */
+int ising_clear_int8_configs(void);
+
+/* The configuration the lattice's int8 passes run now (registered or
+ * built-in, size limits resolved); kernel = -1 for the bit-packed layout. */
+int ising_get_int8_config(const ising_lattice *lat, ising_int8_config *out);
 
 /* The engine's counter-based generator on the device: for c0 = 0..n-1,
  * dev_out[4*c0 + j] = word j of Philox4x32-10(key = seed; counter =

@@ -1,9 +1,12 @@
-"""Autotuner for the batched launch.
+"""Autotuner for the batched launch and the int8 per-lattice pass.
 
 Searches the launch shape of the persistent batched kernel -- threads per CTA,
 CTAs per cluster for large lattices, the size threshold of the cluster queue,
 and the spin layout policy -- on a scaled-down sample of the workload, and
-keeps the fastest.  Every candidate must produce bit-identical spins and E/M
+keeps the fastest; and, per lattice shape, the int8 colour pass (register
+strips, or tiles staged by bulk copies with their rows per tile -- one or two
+rows per thread at a time -- and resident CTAs per SM), registered with the
+engine so that ISING_KERNEL_AUTO runs the winner.  Every candidate must produce bit-identical spins and E/M
 for every lattice (the draws are keyed by site, sweep and colour, so the
 launch shape never changes a result); a candidate that does not is an error,
 not a slower choice.  The winner is cached as JSON per device name and
@@ -98,4 +101,97 @@ def tune(specs, sample_sweeps: int = 40, sample_lattices: int = 512, seed: int =
                 json.dump(cache, f, indent=1)
         except (OSError, ValueError):
             pass
+    return entry
+
+
+# ---------------------------------------------------------------------------
+# The int8 per-lattice pass: which kernel (register strips or tiles staged by
+# bulk copies), and for the staged kernel its rows per tile (1: each thread
+# one row at a time; 2 and 4: two rows at a time, eight Philox calls in
+# flight) and its resident CTAs per SM.
+# ---------------------------------------------------------------------------
+def int8_candidates(dims: int, L: int) -> list:
+    """The strip kernel, and the staged kernel over rows per tile (short rows
+    need tall tiles to give every thread work) and resident CTAs per SM."""
+    W = L // 2
+    rows = [r for r in (1, 2, 4, 8, 16, 32, 64) if r * W <= 32768 and L % r == 0]
+    if dims == 3:
+        rows = [r for r in rows if r * W >= 1024] or rows[-1:]
+    else:
+        rows = rows[:3]
+    return [dict(kernel=1, tile_rows=0, ctas_per_sm=0)] + [
+        dict(kernel=2, tile_rows=r, ctas_per_sm=c) for r in rows for c in (0, 3, 2)]
+
+
+def _int8_run(engine, dims, L, sweeps, seed=20031109):
+    """Time `sweeps` sweeps of one cold lattice with the registered
+    configuration; returns (seconds, fingerprint, resolved config)."""
+    import torch
+    lat = engine.Lattice(dims, L, 0.4 if dims == 2 else 0.22, seed, layout=engine.INT8,
+                         start=engine.COLD_UP)
+    resolved = lat.int8_config()
+    lat.sweep(2, 1)  # warm-up
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    lat.sweep(sweeps, 1)
+    b.record()
+    b.synchronize()
+    E, M = lat.observables()
+    s = lat.get_spins()
+    lat.close()
+    fp = (hashlib.sha1(s.tobytes()).hexdigest(), E.tobytes(), M.tobytes())
+    return a.elapsed_time(b) / 1e3, fp, resolved
+
+
+def tune_int8(dims: int, L: int, L_range=None, sweeps: int = 10, use_cache: bool = True,
+              register: bool = True) -> dict:
+    """Measure every int8 pass configuration on a (dims, L) lattice, check
+    that all give bit-identical spins and E/M, and register the fastest for
+    lattices with L in ``L_range`` (default: L alone) so that
+    ISING_KERNEL_AUTO runs it.  Returns {"config": ..., "results": [...]}."""
+    from . import engine
+    lo, hi = L_range or (L, L)
+    key = f"int8|{_device_name()}|{dims}|{L}"
+    entry = None
+    if use_cache and os.path.exists(CACHE):
+        try:
+            with open(CACHE) as f:
+                entry = json.load(f).get(key)
+        except (OSError, ValueError):
+            entry = None
+    if entry is None:
+        results, reference, seen = [], None, set()
+        for cand in int8_candidates(dims, L):
+            engine.clear_int8_configs()
+            engine.set_int8_config(dims, L, L, **cand)
+            dt, fp, resolved = _int8_run(engine, dims, L, sweeps)
+            shape = tuple(sorted(resolved.items()))
+            if resolved["kernel"] != cand["kernel"] or shape in seen:
+                continue  # the staged kernel cannot take this shape, or a duplicate
+            seen.add(shape)
+            if reference is None:
+                reference = fp
+            elif fp != reference:
+                raise RuntimeError(f"autotune: int8 configuration {cand} changed a result")
+            results.append({"config": resolved, "seconds": dt,
+                            "site_updates_per_s": L ** dims * sweeps / dt})
+        engine.clear_int8_configs()
+        best = min(results, key=lambda r: r["seconds"])
+        entry = {"config": best["config"], "results": results,
+                 "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+        if use_cache:
+            try:
+                os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+                cache = {}
+                if os.path.exists(CACHE):
+                    with open(CACHE) as f:
+                        cache = json.load(f)
+                cache[key] = entry
+                with open(CACHE, "w") as f:
+                    json.dump(cache, f, indent=1)
+            except (OSError, ValueError):
+                pass
+    if register:
+        engine.set_int8_config(dims, lo, hi, **entry["config"])
     return entry

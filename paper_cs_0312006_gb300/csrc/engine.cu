@@ -317,11 +317,55 @@ __global__ void gather_records_kernel(GatherChunk c, long long* out, long long* 
     }
 }
 
-bool uses_tma(const ising_lattice* h) {
-    return h->layout != ISING_BITPACK && ising::int8_tma_ok(h->dims, h->L) &&
-           (h->kernel == ISING_KERNEL_TMA ||
-            (h->kernel == ISING_KERNEL_AUTO && ising::int8_tma_preferred(h->dims, h->L)));
+// Tuned int8 pass configurations (ising_set_int8_config): for lattices of
+// dims and L_min <= L <= L_max, ISING_KERNEL_AUTO runs `cfg`; the latest
+// matching entry wins.
+struct Int8Policy {
+    int dims, L_min, L_max;
+    ising_int8_config cfg;
+};
+std::mutex g_policy_mu;
+std::vector<Int8Policy> g_policy;
+
+bool find_policy(int dims, int L, ising_int8_config* out) {
+    std::lock_guard<std::mutex> lk(g_policy_mu);
+    for (auto it = g_policy.rbegin(); it != g_policy.rend(); ++it)
+        if (it->dims == dims && it->L_min <= L && L <= it->L_max) {
+            *out = it->cfg;
+            return true;
+        }
+    return false;
 }
+
+// The int8 pass a lattice runs: the kernel, and for the staged kernel its
+// rows per tile and CTAs per SM (0: defaults).
+ising_int8_config resolve_int8(const ising_lattice* h) {
+    ising_int8_config c = {ISING_KERNEL_STRIP, 0, 0};
+    if (h->layout == ISING_BITPACK) return c;
+    ising_int8_config tuned;
+    const bool have = find_policy(h->dims, h->L, &tuned);
+    if (h->kernel == ISING_KERNEL_TMA) {
+        c.kernel = ISING_KERNEL_TMA;
+        if (have && tuned.kernel == ISING_KERNEL_TMA) {
+            c.tile_rows = tuned.tile_rows;
+            c.ctas_per_sm = tuned.ctas_per_sm;
+        }
+    } else if (h->kernel == ISING_KERNEL_AUTO) {
+        if (have)
+            c = tuned;
+        else if (ising::int8_tma_preferred(h->dims, h->L))
+            c.kernel = ISING_KERNEL_TMA;
+    }
+    if (c.kernel == ISING_KERNEL_TMA && !ising::int8_tma_ok(h->dims, h->L, c.tile_rows)) {
+        // the staged kernel cannot take this shape: the general kernels run
+        c.kernel = ISING_KERNEL_STRIP;
+        c.tile_rows = c.ctas_per_sm = 0;
+    }
+    if (c.kernel != ISING_KERNEL_TMA) c.tile_rows = c.ctas_per_sm = 0;
+    return c;
+}
+
+bool uses_tma(const ising_lattice* h) { return resolve_int8(h).kernel == ISING_KERNEL_TMA; }
 
 int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     PassArgs a;
@@ -354,10 +398,10 @@ int run_pass(ising_lattice* h, int c, uint32_t t, unsigned long long* slot) {
     }
     if (h->layout == ISING_BITPACK)
         ISING_CHECK(ising::packed_pass(a, h->dims, slot != nullptr, h->rule, *h->dp, h->stream));
-    else if (uses_tma(h))
+    else if (const ising_int8_config c = resolve_int8(h); c.kernel == ISING_KERNEL_TMA)
         ISING_CHECK(ising::int8_pass_tma(a, h->dims, slot != nullptr, h->rule, *h->dp,
                                          h->dp->d_err, g_inject_timeout.load() ? 16u : 0u,
-                                         h->stream));
+                                         h->stream, c.tile_rows, c.ctas_per_sm));
     else
         ISING_CHECK(ising::int8_pass(a, h->dims, h->half_sites, slot != nullptr, h->rule,
                                      *h->dp, h->stream));
@@ -870,6 +914,33 @@ int ising_get_kernel(const ising_lattice* h, int* kernel) {
     if (!h || !kernel) return ISING_EINVAL;
     *kernel = h->layout == ISING_BITPACK ? -1
                                          : (uses_tma(h) ? ISING_KERNEL_TMA : ISING_KERNEL_STRIP);
+    return ISING_OK;
+}
+
+int ising_set_int8_config(int dims, int L_min, int L_max, const ising_int8_config* cfg) {
+    if (!cfg || (dims != 2 && dims != 3) || L_min < 2 || L_max < L_min) return ISING_EINVAL;
+    if (cfg->kernel != ISING_KERNEL_STRIP && cfg->kernel != ISING_KERNEL_TMA) return ISING_EINVAL;
+    const int R = cfg->tile_rows;
+    if (R < 0 || R > 64 || (R & (R - 1)) != 0) return ISING_EINVAL;  // 0 or a power of two <= 64
+    if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8) return ISING_EINVAL;
+    std::lock_guard<std::mutex> lk(g_policy_mu);
+    g_policy.push_back(Int8Policy{dims, L_min, L_max, *cfg});
+    return ISING_OK;
+}
+
+int ising_clear_int8_configs(void) {
+    std::lock_guard<std::mutex> lk(g_policy_mu);
+    g_policy.clear();
+    return ISING_OK;
+}
+
+int ising_get_int8_config(const ising_lattice* h, ising_int8_config* out) {
+    if (!h || !out) return ISING_EINVAL;
+    if (h->layout == ISING_BITPACK) {
+        *out = ising_int8_config{-1, 0, 0};
+        return ISING_OK;
+    }
+    *out = resolve_int8(h);
     return ISING_OK;
 }
 

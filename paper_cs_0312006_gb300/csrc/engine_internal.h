@@ -115,11 +115,13 @@ cudaError_t int8_import(int8_t* col0, int8_t* col1, const int8_t* in, int L, int
                         int64_t sites, const DeviceProps& dp, cudaStream_t st);
 
 // int8 layout, inputs staged by bulk copies (sweep_int8_tma.cu)
-bool int8_tma_ok(int dims, int L);
-// ISING_KERNEL_AUTO's choice of the staged kernel (measured; see the definition)
+bool int8_tma_ok(int dims, int L, int rows_per_tile);
+// ISING_KERNEL_AUTO's choice of the staged kernel without a tuned
+// configuration (measured; see the definition)
 bool int8_tma_preferred(int dims, int L);
 cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, int rule,
-                          const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st);
+                          const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st,
+                          int rows_per_tile, int ctas_per_sm);
 
 // canonical <-> layout conversion and initial states for half rows of whole
 // 16-byte vectors (int8, L % 32 == 0) or whole words (bit-packed, L % 64 == 0)

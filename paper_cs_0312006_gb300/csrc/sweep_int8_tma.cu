@@ -35,11 +35,11 @@ constexpr int kStages = 2;
 
 // Rows per tile: about 8 KiB of own-colour rows (two rows of a 2D L = 8192
 // lattice, which measured best there against 1, 4 and 8), at least 2 and at
-// most 32 rows, a power of two that divides L.
+// most 64 rows, a power of two that divides L.
 __host__ __device__ inline int tile_rows(int L) {
     const int W = L / 2;
     int R = 2;
-    while (R < 32 && 2 * R * W <= 8192 && L % (2 * R) == 0) R *= 2;
+    while (R < 64 && 2 * R * W <= 8192 && L % (2 * R) == 0) R *= 2;
     while (R > 1 && L % R != 0) R >>= 1;
     return R;
 }
@@ -190,7 +190,7 @@ __device__ __forceinline__ void update_vec_pair_hb(uint4 (&S)[2], const uint4 (&
 }
 
 template <int DIMS, bool MEASURE, int RULE>
-__global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
+__global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 3) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kStages];
     __shared__ uint32_t s_thb[8];  // heat bath: thr[d] by d, read per site
@@ -249,21 +249,26 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
             // with the counting test).  The calls need only counters, so they
             // are issued before the loads of the spins (3 % faster at L = 8192
             // than drawing after the neighbour counts).
-            for (; i0 + 1u < R; i0 += 2u) {
-                for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
+            // items are (row pair, column) of the tile, columns fastest, so that
+            // short rows (3D) still give every thread work
+            const uint32_t pairs = R >> 1;
+            for (uint32_t item = threadIdx.x; item < pairs * nv; item += blockDim.x) {
+                {
+                    const uint32_t pr = item / nv, v = item - pr * nv;
+                    const uint32_t ip = 2u * pr;  // the pair's first row in the tile
                     uint4 S[2], X[2], XS[2], YM[2], YP[2], ZM[2], ZP[2];
                     uint32_t rowg[2];
                     Philox4 u[8];
 #pragma unroll
                     for (int q = 0; q < 2; ++q)
-                        rowg[q] = (z * (uint32_t)a.L + y0 + i0 + (uint32_t)q) * nv + v;
+                        rowg[q] = (z * (uint32_t)a.L + y0 + ip + (uint32_t)q) * nv + v;
 #pragma unroll
                     for (int w = 0; w < 8; ++w)
                         u[w] = philox4x32_10(rowg[w >> 2] * 4u + (uint32_t)(w & 3), a.t,
                                              (uint32_t)a.c, kTagSweep, a.key0, a.key1);
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const uint32_t i = i0 + (uint32_t)q;
+                        const uint32_t i = ip + (uint32_t)q;
                         const uint32_t y = y0 + i;
                         const int p = (a.c + (int)y + (int)z) & 1;
                         const uint32_t* row32 =
@@ -306,6 +311,7 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
                     n_vec += 2;
                 }
             }
+            i0 = 2u * pairs;
         }
         for (uint32_t i = i0; i < R; ++i) {
             const uint32_t y = y0 + i;
@@ -354,13 +360,14 @@ __global__ void __launch_bounds__(512) pass_int8_tma(PassArgs a, TmaGeom tg, int
 
 template <int DIMS, bool MEASURE, int RULE>
 cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uint32_t extra_tx,
-                         cudaStream_t st) {
+                         cudaStream_t st, int rows_per_tile, int ctas_per_sm) {
     TmaGeom tg;
     tg.extra_tx = extra_tx;
     const int planes = DIMS == 3 ? a.L : 1;
-    // tile_rows() and 256 threads measured best on GB300 (2D L=8192: 44.7 us
-    // per pass with two rows, against 49 us with four and 55 us with eight)
-    const int R = tile_rows(a.L);
+    // default: tile_rows() and 256 threads, measured best on GB300 (2D L=8192:
+    // 44.7 us per pass with two rows, against 49 us with four and 55 us with
+    // eight); a tuned configuration may ask for other rows per tile
+    const int R = rows_per_tile > 0 ? rows_per_tile : tile_rows(a.L);
     const int threads = 256;
     tg.R = R;
     tg.bands = a.L / R;
@@ -382,6 +389,7 @@ cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uin
                                                       threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     int grid = dp.sm_count * per_sm;
     if (grid > tg.tiles) grid = tg.tiles;
     return launch_chained(pass_int8_tma<DIMS, MEASURE, RULE>, (unsigned)grid, (unsigned)threads,
@@ -390,12 +398,14 @@ cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uin
 
 }  // namespace
 
-// The staged kernel needs W % 16 == 0 and its stages (2 x (2R+2) half rows,
-// plus 2 x 2R for 3D) to fit in shared memory.
-bool int8_tma_ok(int dims, int L) {
+// The staged kernel needs W % 16 == 0, R rows per tile dividing L (R = 0:
+// the default tile_rows) and its stages (2 x (2R+2) half rows, plus 2 x 2R
+// for 3D) to fit in shared memory.
+bool int8_tma_ok(int dims, int L, int rows_per_tile) {
     const int W = L / 2;
     if (W % 16 != 0) return false;
-    const int R = tile_rows(L);
+    const int R = rows_per_tile > 0 ? rows_per_tile : tile_rows(L);
+    if (R < 1 || L % R != 0) return false;
     const size_t stage = (size_t)(2 * R + 2) * W + (dims == 3 ? 2u * R * W : 0u);
     return (size_t)kStages * stage <= 200 * 1024;
 }
@@ -403,12 +413,12 @@ bool int8_tma_ok(int dims, int L) {
 template <int RULE>
 static cudaError_t int8_pass_tma_rule(const PassArgs& a, int dims, bool measure,
                                       const DeviceProps& dp, int* err, uint32_t extra_tx,
-                                      cudaStream_t st) {
+                                      cudaStream_t st, int R, int ctas) {
     if (dims == 2)
-        return measure ? launch_tma_t<2, true, RULE>(a, dp, err, extra_tx, st)
-                       : launch_tma_t<2, false, RULE>(a, dp, err, extra_tx, st);
-    return measure ? launch_tma_t<3, true, RULE>(a, dp, err, extra_tx, st)
-                   : launch_tma_t<3, false, RULE>(a, dp, err, extra_tx, st);
+        return measure ? launch_tma_t<2, true, RULE>(a, dp, err, extra_tx, st, R, ctas)
+                       : launch_tma_t<2, false, RULE>(a, dp, err, extra_tx, st, R, ctas);
+    return measure ? launch_tma_t<3, true, RULE>(a, dp, err, extra_tx, st, R, ctas)
+                   : launch_tma_t<3, false, RULE>(a, dp, err, extra_tx, st, R, ctas);
 }
 
 // Where the staged kernel measured faster than the strip kernel on GB300: 2D
@@ -418,18 +428,22 @@ static cudaError_t int8_pass_tma_rule(const PassArgs& a, int dims, bool measure,
 // kernel's 8.02e11).  With short rows (3D, small 2D) a tile holds about one
 // vector per thread and its barriers dominate.
 bool int8_tma_preferred(int dims, int L) {
-    if (dims != 2 || L < 4096 || !int8_tma_ok(dims, L)) return false;
+    if (dims != 2 || L < 4096 || !int8_tma_ok(dims, L, 0)) return false;
     const int W = L / 2, R = tile_rows(L);
     return 2 * (size_t)kStages * (size_t)(2 * R + 2) * W <= 200 * 1024;
 }
 
 cudaError_t int8_pass_tma(const PassArgs& a, int dims, bool measure, int rule,
-                          const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st) {
+                          const DeviceProps& dp, int* err, uint32_t extra_tx, cudaStream_t st,
+                          int rows_per_tile, int ctas_per_sm) {
     if (rule == kRuleHeatBath)
-        return int8_pass_tma_rule<kRuleHeatBath>(a, dims, measure, dp, err, extra_tx, st);
+        return int8_pass_tma_rule<kRuleHeatBath>(a, dims, measure, dp, err, extra_tx, st,
+                                                 rows_per_tile, ctas_per_sm);
     if (rule == kRuleMultiHit)
-        return int8_pass_tma_rule<kRuleMultiHit>(a, dims, measure, dp, err, extra_tx, st);
-    return int8_pass_tma_rule<kRuleMetropolis>(a, dims, measure, dp, err, extra_tx, st);
+        return int8_pass_tma_rule<kRuleMultiHit>(a, dims, measure, dp, err, extra_tx, st,
+                                                 rows_per_tile, ctas_per_sm);
+    return int8_pass_tma_rule<kRuleMetropolis>(a, dims, measure, dp, err, extra_tx, st,
+                                               rows_per_tile, ctas_per_sm);
 }
 
 }  // namespace ising

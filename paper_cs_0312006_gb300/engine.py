@@ -41,6 +41,11 @@ class BatchOpts(ctypes.Structure):
                 ("huge_sites", ctypes.c_int64)]
 
 
+class Int8Config(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("tile_rows", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int)]
+
+
 class IsingInfo(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int), ("L", ctypes.c_int), ("layout", ctypes.c_int),
                 ("rule", ctypes.c_int), ("beta", ctypes.c_double),
@@ -98,6 +103,10 @@ def load_library():
             "ising_synchronize": ([P], ctypes.c_int),
             "ising_set_kernel": ([P, ctypes.c_int], ctypes.c_int),
             "ising_get_kernel": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "ising_set_int8_config": ([ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(Int8Config)], ctypes.c_int),
+            "ising_clear_int8_configs": ([], ctypes.c_int),
+            "ising_get_int8_config": ([P, ctypes.POINTER(Int8Config)], ctypes.c_int),
             "ising_test_inject_timeout": ([ctypes.c_int], ctypes.c_int),
             "ising_philox_fill": ([P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint32, ctypes.c_uint64, P], ctypes.c_int),
@@ -156,6 +165,19 @@ def philox_probe(dev_ptr: int, blocks: int, threads: int, iters: int, variant: i
                                              ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
                                              ctypes.c_void_p(int(raw) if raw else 0)),
            "ising_philox_probe")
+
+
+def set_int8_config(dims: int, L_min: int, L_max: int, kernel: int, tile_rows: int = 0,
+                    ctas_per_sm: int = 0) -> None:
+    """``ising_set_int8_config``: the int8 pass configuration that
+    ISING_KERNEL_AUTO runs for lattices of ``dims`` with L_min <= L <= L_max."""
+    cfg = Int8Config(kernel, tile_rows, ctas_per_sm)
+    _check(load_library().ising_set_int8_config(dims, L_min, L_max, ctypes.byref(cfg)),
+           "ising_set_int8_config")
+
+
+def clear_int8_configs() -> None:
+    _check(load_library().ising_clear_int8_configs(), "ising_clear_int8_configs")
 
 
 def test_inject_timeout(on: bool) -> None:
@@ -309,6 +331,12 @@ class Lattice:
     def set_kernel(self, kernel: int) -> None:
         """int8 pass kernel: KERNEL_AUTO, KERNEL_STRIP or KERNEL_TMA."""
         _check(self._lib.ising_set_kernel(self._h, int(kernel)), "ising_set_kernel")
+
+    def int8_config(self) -> dict:
+        """``ising_get_int8_config``: the int8 pass this lattice runs now."""
+        c = Int8Config()
+        _check(self._lib.ising_get_int8_config(self._h, ctypes.byref(c)), "ising_get_int8_config")
+        return {"kernel": c.kernel, "tile_rows": c.tile_rows, "ctas_per_sm": c.ctas_per_sm}
 
     def kernel(self) -> int:
         """The int8 pass kernel the sweeps run (KERNEL_STRIP / KERNEL_TMA; -1 if packed)."""

@@ -140,3 +140,17 @@ def test_observables_gather_signal_rejects_bad_arguments_on_the_host(lib):
     assert lib.ising_observables_gather_signal(None, 1, pairs, 4, counts, flag, 1) == -1
     assert lib.ising_observables_gather_signal(none2, 0, pairs, 4, counts, flag, 1) == -1
     assert lib.ising_observables_gather_signal(none2, 2, pairs, 4, counts, flag, 1) == -1
+
+
+def test_int8_configuration_arguments_checked_on_host():
+    from paper_cs_0312006_gb300 import engine
+    engine.load_library()
+    bad = [(4, 64, 64, dict(kernel=2)), (2, 64, 32, dict(kernel=2)), (2, 64, 64, dict(kernel=5)),
+           (2, 64, 64, dict(kernel=2, tile_rows=3)), (2, 64, 64, dict(kernel=2, ctas_per_sm=9)),
+           (2, 1, 64, dict(kernel=1))]
+    for dims, lo, hi, cfg in bad:
+        with pytest.raises(engine.IsingError) as ei:
+            engine.set_int8_config(dims, lo, hi, **cfg)
+        assert ei.value.code == engine.EINVAL
+    engine.set_int8_config(3, 16, 256, kernel=2, tile_rows=4, ctas_per_sm=2)
+    engine.clear_int8_configs()
