@@ -120,31 +120,44 @@ def int8_candidates(dims: int, L: int) -> list:
     else:
         rows = rows[:3]
     return [dict(kernel=1, tile_rows=0, ctas_per_sm=0)] + [
-        dict(kernel=2, tile_rows=r, ctas_per_sm=c) for r in rows for c in (0, 3, 2)]
+        dict(kernel=2, tile_rows=r, ctas_per_sm=c) for r in rows for c in (0, 3)]
 
 
-def _int8_run(engine, dims, L, sweeps, seed=20031109):
-    """Time `sweeps` sweeps of one cold lattice with the registered
-    configuration; returns (seconds, fingerprint, resolved config)."""
+L2_BYTES = 129 * 2 ** 20
+
+
+def _int8_run(engine, dims, L, sweeps, seed=20031109, repeats=2):
+    """Time `sweeps` sweeps of each of n cold lattices in turn (n chosen so
+    that their spins exceed L2, as in a real run) with the registered
+    configuration, best of `repeats`; returns (seconds per lattice-sweep,
+    fingerprint, resolved config)."""
     import torch
-    lat = engine.Lattice(dims, L, 0.4 if dims == 2 else 0.22, seed, layout=engine.INT8,
-                         start=engine.COLD_UP)
-    resolved = lat.int8_config()
-    lat.sweep(2, 1)  # warm-up
+    n = max(1, min(8, -(-3 * L2_BYTES // (L ** dims))))
+    lats = [engine.Lattice(dims, L, 0.4 if dims == 2 else 0.22, seed + j, layout=engine.INT8,
+                           start=engine.COLD_UP) for j in range(n)]
+    resolved = lats[0].int8_config()
+    for lat in lats:
+        lat.sweep(1, 1)  # warm-up
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    lat.sweep(sweeps, 1)
-    b.record()
-    b.synchronize()
-    E, M = lat.observables()
-    s = lat.get_spins()
-    lat.close()
+    best = float("inf")
+    for _ in range(repeats):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(sweeps):
+            for lat in lats:
+                lat.sweep(1, 1)
+        b.record()
+        b.synchronize()
+        best = min(best, a.elapsed_time(b) / 1e3 / (sweeps * n))
+    E, M = lats[0].observables()
+    s = lats[0].get_spins()
+    for lat in lats:
+        lat.close()
     fp = (hashlib.sha1(s.tobytes()).hexdigest(), E.tobytes(), M.tobytes())
-    return a.elapsed_time(b) / 1e3, fp, resolved
+    return best, fp, resolved
 
 
-def tune_int8(dims: int, L: int, L_range=None, sweeps: int = 10, use_cache: bool = True,
+def tune_int8(dims: int, L: int, L_range=None, sweeps: int = 5, use_cache: bool = True,
               register: bool = True) -> dict:
     """Measure every int8 pass configuration on a (dims, L) lattice, check
     that all give bit-identical spins and E/M, and register the fastest for
@@ -175,7 +188,15 @@ def tune_int8(dims: int, L: int, L_range=None, sweeps: int = 10, use_cache: bool
             elif fp != reference:
                 raise RuntimeError(f"autotune: int8 configuration {cand} changed a result")
             results.append({"config": resolved, "seconds": dt,
-                            "site_updates_per_s": L ** dims * sweeps / dt})
+                            "site_updates_per_s": L ** dims / dt})
+        # the two leaders timed again, longer, before choosing
+        results.sort(key=lambda r: r["seconds"])
+        for r in results[:2]:
+            engine.clear_int8_configs()
+            engine.set_int8_config(dims, L, L, **r["config"])
+            dt, _, _ = _int8_run(engine, dims, L, 3 * sweeps)  # results checked above
+            r["seconds"] = min(r["seconds"], dt)
+            r["site_updates_per_s"] = L ** dims / r["seconds"]
         engine.clear_int8_configs()
         best = min(results, key=lambda r: r["seconds"])
         entry = {"config": best["config"], "results": results,

@@ -190,7 +190,7 @@ __device__ __forceinline__ void update_vec_pair_hb(uint4 (&S)[2], const uint4 (&
 }
 
 template <int DIMS, bool MEASURE, int RULE>
-__global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 3) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
+__global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kStages];
     __shared__ uint32_t s_thb[8];  // heat bath: thr[d] by d, read per site
@@ -250,66 +250,77 @@ __global__ void __launch_bounds__(256, DIMS == 2 ? 4 : 3) pass_int8_tma(PassArgs
             // are issued before the loads of the spins (3 % faster at L = 8192
             // than drawing after the neighbour counts).
             // items are (row pair, column) of the tile, columns fastest, so that
-            // short rows (3D) still give every thread work
-            const uint32_t pairs = R >> 1;
-            for (uint32_t item = threadIdx.x; item < pairs * nv; item += blockDim.x) {
-                {
-                    const uint32_t pr = item / nv, v = item - pr * nv;
-                    const uint32_t ip = 2u * pr;  // the pair's first row in the tile
-                    uint4 S[2], X[2], XS[2], YM[2], YP[2], ZM[2], ZP[2];
-                    uint32_t rowg[2];
-                    Philox4 u[8];
+            // short rows (3D) still give every thread work.  A thread takes its
+            // items two at a time: the second item's calls are issued between
+            // the first item's loads and its update, so that the generator's
+            // multiplies overlap the update's logic (39.6 -> 37.4 us per pass
+            // at L = 8192 with 128-thread CTAs, two items per thread per tile).
+            const uint32_t pairs = R >> 1, n_items = pairs * nv;
+            auto draw = [&](uint32_t item, Philox4 (&u)[8]) {
+                const uint32_t pr = item / nv, v = item - pr * nv;
 #pragma unroll
-                    for (int q = 0; q < 2; ++q)
-                        rowg[q] = (z * (uint32_t)a.L + y0 + ip + (uint32_t)q) * nv + v;
-#pragma unroll
-                    for (int w = 0; w < 8; ++w)
-                        u[w] = philox4x32_10(rowg[w >> 2] * 4u + (uint32_t)(w & 3), a.t,
-                                             (uint32_t)a.c, kTagSweep, a.key0, a.key1);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const uint32_t i = ip + (uint32_t)q;
-                        const uint32_t y = y0 + i;
-                        const int p = (a.c + (int)y + (int)z) & 1;
-                        const uint32_t* row32 =
-                            reinterpret_cast<const uint32_t*>(oth + (i + 1u) * W);
-                        const uint4 oc = oth16[(i + 1u) * nv + v];
-                        X[q] = oc;
-                        YM[q] = oth16[i * nv + v];
-                        YP[q] = oth16[(i + 2u) * nv + v];
-                        ZM[q] = make_uint4(0u, 0u, 0u, 0u);
-                        ZP[q] = ZM[q];
-                        if (DIMS == 3) {
-                            ZM[q] = zm16[i * nv + v];
-                            ZP[q] = zp16[i * nv + v];
-                        }
-                        if (p == 0) {
-                            const uint32_t prev = row32[(v == 0u ? nv - 1u : v - 1u) * 4u + 3u];
-                            XS[q] = make_uint4(__funnelshift_l(prev, oc.x, 8),
-                                               __funnelshift_l(oc.x, oc.y, 8),
-                                               __funnelshift_l(oc.y, oc.z, 8),
-                                               __funnelshift_l(oc.z, oc.w, 8));
-                        } else {
-                            const uint32_t next = row32[(v + 1u == nv ? 0u : v + 1u) * 4u];
-                            XS[q] = make_uint4(__funnelshift_r(oc.x, oc.y, 8),
-                                               __funnelshift_r(oc.y, oc.z, 8),
-                                               __funnelshift_r(oc.z, oc.w, 8),
-                                               __funnelshift_r(oc.w, next, 8));
-                        }
-                        S[q] = own_s[i * nv + v];
-                    }
-                    int e_vec = 0;
-                    if (RULE == kRuleHeatBath)
-                        update_vec_pair_hb<DIMS, MEASURE>(S, X, XS, YM, YP, ZM, ZP, u, s_thb, a,
-                                                          e_vec, m_neg);
-                    else
-                        update_vec_pair<DIMS, MEASURE>(S, X, XS, YM, YP, ZM, ZP, u, a, e_vec,
-                                                       m_neg);
-                    own_g[rowg[0]] = S[0];
-                    own_g[rowg[1]] = S[1];
-                    e_acc += e_vec;
-                    n_vec += 2;
+                for (int w = 0; w < 8; ++w) {
+                    const uint32_t rg = (z * (uint32_t)a.L + y0 + 2u * pr + (uint32_t)(w >> 2)) * nv + v;
+                    u[w] = philox4x32_10(rg * 4u + (uint32_t)(w & 3), a.t, (uint32_t)a.c,
+                                         kTagSweep, a.key0, a.key1);
                 }
+            };
+            auto update = [&](uint32_t item, const Philox4 (&u)[8]) {
+                const uint32_t pr = item / nv, v = item - pr * nv;
+                const uint32_t ip = 2u * pr;  // the pair's first row in the tile
+                uint4 S[2], X[2], XS[2], YM[2], YP[2], ZM[2], ZP[2];
+                uint32_t rowg[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const uint32_t i = ip + (uint32_t)q;
+                    const uint32_t y = y0 + i;
+                    const int p = (a.c + (int)y + (int)z) & 1;
+                    const uint32_t* row32 = reinterpret_cast<const uint32_t*>(oth + (i + 1u) * W);
+                    const uint4 oc = oth16[(i + 1u) * nv + v];
+                    X[q] = oc;
+                    YM[q] = oth16[i * nv + v];
+                    YP[q] = oth16[(i + 2u) * nv + v];
+                    ZM[q] = make_uint4(0u, 0u, 0u, 0u);
+                    ZP[q] = ZM[q];
+                    if (DIMS == 3) {
+                        ZM[q] = zm16[i * nv + v];
+                        ZP[q] = zp16[i * nv + v];
+                    }
+                    if (p == 0) {
+                        const uint32_t prev = row32[(v == 0u ? nv - 1u : v - 1u) * 4u + 3u];
+                        XS[q] = make_uint4(__funnelshift_l(prev, oc.x, 8),
+                                           __funnelshift_l(oc.x, oc.y, 8),
+                                           __funnelshift_l(oc.y, oc.z, 8),
+                                           __funnelshift_l(oc.z, oc.w, 8));
+                    } else {
+                        const uint32_t next = row32[(v + 1u == nv ? 0u : v + 1u) * 4u];
+                        XS[q] = make_uint4(__funnelshift_r(oc.x, oc.y, 8),
+                                           __funnelshift_r(oc.y, oc.z, 8),
+                                           __funnelshift_r(oc.z, oc.w, 8),
+                                           __funnelshift_r(oc.w, next, 8));
+                    }
+                    S[q] = own_s[i * nv + v];
+                    rowg[q] = (z * (uint32_t)a.L + y) * nv + v;
+                }
+                int e_vec = 0;
+                if (RULE == kRuleHeatBath)
+                    update_vec_pair_hb<DIMS, MEASURE>(S, X, XS, YM, YP, ZM, ZP, u, s_thb, a,
+                                                      e_vec, m_neg);
+                else
+                    update_vec_pair<DIMS, MEASURE>(S, X, XS, YM, YP, ZM, ZP, u, a, e_vec,
+                                                   m_neg);
+                own_g[rowg[0]] = S[0];
+                own_g[rowg[1]] = S[1];
+                e_acc += e_vec;
+                n_vec += 2;
+            };
+            for (uint32_t base = threadIdx.x; base < n_items; base += 2u * blockDim.x) {
+                const uint32_t second = base + blockDim.x;
+                Philox4 u0[8], u1[8];
+                draw(base, u0);
+                draw(second, u1);  // counters only: harmless past the last item
+                update(base, u0);
+                if (second < n_items) update(second, u1);
             }
             i0 = 2u * pairs;
         }
@@ -364,11 +375,11 @@ cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uin
     TmaGeom tg;
     tg.extra_tx = extra_tx;
     const int planes = DIMS == 3 ? a.L : 1;
-    // default: tile_rows() and 256 threads, measured best on GB300 (2D L=8192:
-    // 44.7 us per pass with two rows, against 49 us with four and 55 us with
-    // eight); a tuned configuration may ask for other rows per tile
+    // default: tile_rows() (2D L = 8192: two rows, measured best against 1, 4
+    // and 8) and 128 threads, each taking its (row pair, column) items two at
+    // a time; a tuned configuration may ask for other rows per tile
     const int R = rows_per_tile > 0 ? rows_per_tile : tile_rows(a.L);
-    const int threads = 256;
+    const int threads = 128;  // two items per thread per 2-row tile at L = 8192
     tg.R = R;
     tg.bands = a.L / R;
     tg.tiles = tg.bands * planes;
