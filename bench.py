@@ -177,23 +177,35 @@ class ClockSampler:
         self.gpu_index = gpu_index
         self.proc = None
         self.lines = []
+        self.times = []
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
+        """Start sampling every 50 ms and wait (at most wait_s) for the first
+        sample, so that a short timed region that follows is covered."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + wait_s
+        while not self.lines and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.times.append(time.time())
 
-    def stop(self):
+    def count_since(self, t0: float) -> int:
+        return sum(1 for t in list(self.times) if t >= t0)
+
+    def stop(self, since: float = 0.0):
+        """Summarise the samples taken at or after `since` (time.time())."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -204,7 +216,9 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln, t in zip(list(self.lines), list(self.times)):
+            if t < since:
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -403,19 +417,31 @@ def run_gpu(args, world, rank, local):
             dist.barrier()
 
     # ---------------- warm-up ----------------
+    sampler = ClockSampler(local)
+    sampler.start()
     for lats in sets.values():
         for _ in range(args.warmup):
             for lat in lats:
                 lat.sweep(1, 1)
+    # the same sweeps for a moment more (at least 0.3 s and 5 clock samples,
+    # at most 3 s), so that the clock record covers the GPU under this load:
+    # the timed region of a short run is shorter than the sampling interval
+    soak_from = time.time()
+    while time.time() - soak_from < 3.0:
+        for lats in sets.values():
+            for lat in lats:
+                lat.sweep(1, 1)
+        torch.cuda.synchronize()
+        if time.time() - soak_from >= 0.3 and sampler.count_since(soak_from) >= 5:
+            break
+    for lats in sets.values():
         for lat in lats:
             lat.observables()
     torch.cuda.synchronize()
 
     # ---------------- device-timed value ----------------
-    sampler = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
-    sampler.start()
     marks = {}
     pairs = {name: [] for name in sets}
     start = torch.cuda.Event(enable_timing=True)
@@ -428,24 +454,27 @@ def run_gpu(args, world, rank, local):
         for lat in lats:
             lat.init(engine.COLD_UP)
         for k in range(args.steps):
+            # a timed step is bracketed as a whole: its 2 x 16 passes run back
+            # to back, so the events break no chained launch inside it
             time_this = k % every == 0
+            if time_this:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
             for lat in lats:
-                if time_this:
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    lat.sweep(1, 1)
-                    e1.record(stream)
-                    pairs[name].append((e0, e1))
-                else:
-                    lat.sweep(1, 1)
+                lat.sweep(1, 1)
+            if time_this:
+                e1.record(stream)
+                pairs[name].append((e0, e1))
         b1.record(stream)
         marks[name] = (b0, b1)
     stop = torch.cuda.Event(enable_timing=True)
     stop.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop(since=soak_from)
+    if clocks is not None:
+        clocks["window"] = "the same sweeps just before the timed region, and the timed region"
     ms_all = max_over_ranks(start.elapsed_time(stop), world, device="cuda")
     per_layout_updates = world * len(betas) * n_sites * args.steps
     # the headline is the int8 layout's whole job (its own bracket of events),
@@ -465,7 +494,9 @@ def run_gpu(args, world, rank, local):
     rooflines = {}
     for name in sets:
         part_ms = marks[name][0].elapsed_time(marks[name][1])
-        pass_ms = sum(a.elapsed_time(b) for a, b in pairs[name]) / (2 * len(pairs[name]))
+        # average launch: the timed steps' time over their passes (2 per lattice)
+        pass_ms = (sum(a.elapsed_time(b) for a, b in pairs[name]) /
+                   (2 * len(sets[name]) * len(pairs[name])))
         updates_per_pass = n_sites // 2
         layout_stats[name] = {"value": world * len(betas) * n_sites * args.steps / (part_ms / 1e3),
                               "ms": part_ms, "pass_ms": pass_ms,
@@ -1128,8 +1159,9 @@ def main():
     ap.add_argument("--lattices", type=int, default=N_BETA,
                     help="how many of the 16 betas to run (profiling uses fewer)")
     ap.add_argument("--time-every", type=int, default=20,
-                    help="time each lattice's sweep with events on every k-th step (an event "
-                         "between two passes keeps the second from being scheduled early)")
+                    help="bracket every k-th step with events (an event between two passes "
+                         "keeps the second from being scheduled early, so only step "
+                         "boundaries carry them)")
     ap.add_argument("--probe-reps", type=int, default=5,
                     help="philox: timed launches of each probe form")
     ap.add_argument("--e2e-steps", type=int, default=0)
