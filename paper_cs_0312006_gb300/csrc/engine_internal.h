@@ -52,7 +52,7 @@ struct DeviceProps {
     int sm_count = 0;
     // resident CTAs per SM of the int8 strip pass and the bit-packed pass
     int blocks_per_sm_vec[4][2][2] = {};     // [rule][dims - 2][measure]; rule 2 unused
-    int blocks_per_sm_packed[4][2][2] = {};
+    int blocks_per_sm_packed[4][2][2][2] = {};  // ... [full words, power-of-two counts]
     int blocks_per_sm_demon[2][2] = {{1, 1}, {1, 1}};  // demon strip pass [dims-2][measure]
     // raised by a kernel whose bounded wait ran out: one int of mapped pinned
     // host memory (device view d_err, host view h_err), read without a copy

@@ -667,12 +667,14 @@ __device__ __forceinline__ uint32_t packed_accept_shifted(const K& k, uint32_t n
 // the row offset, each half takes its five groups together
 // (packed_accept_shifted); otherwise, and in the batched kernel (which runs at
 // a fixed register budget), the nine are taken one at a time.
-template <int DIMS, typename K, bool ILP9 = false>
+// ALIGNED: the caller knows hbase % 4 == 0 (rows of a multiple of 32 sites),
+// so only the eight-group path is compiled.
+template <int DIMS, typename K, bool ILP9 = false, bool ALIGNED = false>
 __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uint32_t hbase,
                                                   const PassArgs& a, uint32_t c2) {
     uint32_t acc = 0u;
-    const uint32_t m = hbase & 3u, g0 = hbase >> 2;
-    if (ILP9 && m != 0u) {
+    const uint32_t m = ALIGNED ? 0u : hbase & 3u, g0 = hbase >> 2;
+    if (!ALIGNED && ILP9 && m != 0u) {
         // the compile-time offset paths only when the warp agrees on it
         const uint32_t lanes = __activemask();
         const uint32_t m0 = __shfl_sync(lanes, m, __ffs(lanes) - 1);
@@ -696,6 +698,7 @@ __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uin
         }
         return acc;
     }
+    if constexpr (ALIGNED) return acc;
 #pragma unroll 1
     for (int g = 0; g < 9; ++g) {
         const int lo = 4 * g - (int)m;  // bit of the group's word 0 (may be < 0)
@@ -746,22 +749,27 @@ __device__ __forceinline__ uint32_t grouped_row(uint32_t j, uint32_t rows, uint3
     return k * rgroups + c;
 }
 
-template <int DIMS, bool MEASURE, int NC, int RULE = kRuleMetropolis, bool ILP9 = false>
+// FULL: W is a multiple of 32 and nq = W / 32 (and L in 3D) a power of two,
+// 2^nq_shift (2^l_shift): every word is full, rows start on a Philox group,
+// and the item's row and word come from shifts instead of divisions.
+template <int DIMS, bool MEASURE, int NC, int RULE = kRuleMetropolis, bool ILP9 = false,
+          bool FULL = false>
 __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, int& e_acc,
-                                            int& m_acc, uint32_t rgroups = 1u) {
+                                            int& m_acc, uint32_t rgroups = 1u,
+                                            uint32_t nq_shift = 0u, uint32_t l_shift = 0u) {
     const uint32_t W = (uint32_t)a.W;
-    const uint32_t nq = (W + 31u) >> 5;
+    const uint32_t nq = FULL ? 1u << nq_shift : (W + 31u) >> 5;
     const uint32_t L = (uint32_t)a.L;
     uint32_t* own = static_cast<uint32_t*>(a.own);
     const uint32_t* other = static_cast<const uint32_t*>(a.other);
-    const uint32_t j = item / nq, q = item - j * nq;
-    const uint32_t r = rgroups > 1u ? grouped_row(j, (uint32_t)a.rows, rgroups) : j;
+    const uint32_t j = FULL ? item >> nq_shift : item / nq, q = item - j * nq;
+    const uint32_t r = !FULL && rgroups > 1u ? grouped_row(j, (uint32_t)a.rows, rgroups) : j;
     uint32_t y = r, z = 0;
     if (DIMS == 3) {
-        z = r / L;
+        z = FULL ? r >> l_shift : r / L;
         y = r - z * L;
     }
-    const uint32_t nb = W - 32u * q < 32u ? W - 32u * q : 32u;  // valid bits
+    const uint32_t nb = FULL ? 32u : (W - 32u * q < 32u ? W - 32u * q : 32u);  // valid bits
     const uint32_t valid = nb == 32u ? 0xFFFFFFFFu : ((1u << nb) - 1u);
     const uint32_t plane = z * L;
     const uint32_t row = r * nq;
@@ -798,7 +806,7 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
     if constexpr (RULE == kRuleHeatBath) {  // every valid site draws
         const Digits k = DIMS == 2 ? digits2(s ^ o, s ^ sh, s ^ oym, s ^ oyp)
                                    : digits3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
-        flip = packed_accept<DIMS, Digits, ILP9>(k, valid, r * W + 32u * q, a, (uint32_t)a.c);
+        flip = packed_accept<DIMS, Digits, ILP9, FULL>(k, valid, r * W + 32u * q, a, (uint32_t)a.c);
     } else if constexpr (RULE == kRuleMultiHit) {  // a.hits trials, neighbours fixed
         uint32_t cur = s;
 #pragma unroll 1
@@ -812,7 +820,7 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
             uint32_t f = k.always;
             const uint32_t need = ~k.always & valid;
             if (need)
-                f |= packed_accept<DIMS, Counts, ILP9>(k, need, r * W + 32u * q, a,
+                f |= packed_accept<DIMS, Counts, ILP9, FULL>(k, need, r * W + 32u * q, a,
                                                        (uint32_t)a.c + 2u * (uint32_t)m);
             cur ^= f & valid;
         }
@@ -826,7 +834,9 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
         }
         flip = k.always;
         const uint32_t need = ~k.always & valid;
-        if (need) flip |= packed_accept<DIMS, Counts, ILP9>(k, need, r * W + 32u * q, a, (uint32_t)a.c);
+        if (need)
+            flip |= packed_accept<DIMS, Counts, ILP9, FULL>(k, need, r * W + 32u * q, a,
+                                                            (uint32_t)a.c);
     }
     const uint32_t snew = s ^ (flip & valid);
     own[row + q] = snew;

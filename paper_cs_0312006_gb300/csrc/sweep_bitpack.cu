@@ -30,15 +30,19 @@ namespace {
 // One item = one 32-site word of the colour array (see packed_word()).
 // Rows that start inside a Philox group are visited grouped by their offset
 // (rgroups, see packed_word).
-template <int DIMS, bool MEASURE, int RULE>
-__global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a, uint32_t rgroups) {
+// FULL instances serve lattices whose words are all full and whose word and
+// row counts are powers of two (packed_word's FULL form; nq_shift, l_shift).
+template <int DIMS, bool MEASURE, int RULE, bool FULL>
+__global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a, uint32_t rgroups,
+                                                      uint32_t nq_shift, uint32_t l_shift) {
     const uint32_t items = (uint32_t)a.rows * (((uint32_t)a.W + 31u) >> 5);
     const uint32_t stride = gridDim.x * blockDim.x;
     int e_acc = 0, m_acc = 0;
     grid_dependency_wait();
     launch_dependents();
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride)
-        packed_word<DIMS, MEASURE, 1, RULE, RULE != kRuleMultiHit>(a, g, e_acc, m_acc, rgroups);
+        packed_word<DIMS, MEASURE, 1, RULE, RULE != kRuleMultiHit, FULL>(a, g, e_acc, m_acc,
+                                                                        rgroups, nq_shift, l_shift);
     if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
 }
 
@@ -116,18 +120,29 @@ unsigned grid_for(int64_t n, const DeviceProps& dp) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
 template <int DIMS, bool MEASURE, int RULE>
 cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream_t st) {
-    const int64_t items = a.rows * ((a.W + 31) >> 5);
+    const int nq = (a.W + 31) >> 5;
+    const int64_t items = a.rows * nq;
+    const bool full = a.W % 32 == 0 && is_pow2(nq) && (DIMS == 2 || is_pow2(a.L));
     int64_t blocks = (items + 255) / 256;
-    const int64_t cap = (int64_t)dp.sm_count * dp.blocks_per_sm_packed[RULE][DIMS - 2][MEASURE];
+    const int64_t cap =
+        (int64_t)dp.sm_count * dp.blocks_per_sm_packed[RULE][DIMS - 2][MEASURE][full ? 1 : 0];
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     // odd W: a row's offset in its Philox group is r W mod 4, set by r mod 4;
     // W = 2 mod 4: by r mod 2
     const uint32_t rgroups = packed_row_groups((uint32_t)a.W);
-    return launch_chained(pass_packed<DIMS, MEASURE, RULE>, (unsigned)blocks, 256u, 0, st, a,
-                          rgroups);
+    if (full) {
+        const uint32_t nq_shift = (uint32_t)__builtin_ctz((unsigned)nq);
+        const uint32_t l_shift = DIMS == 3 ? (uint32_t)__builtin_ctz((unsigned)a.L) : 0u;
+        return launch_chained(pass_packed<DIMS, MEASURE, RULE, true>, (unsigned)blocks, 256u, 0,
+                              st, a, rgroups, nq_shift, l_shift);
+    }
+    return launch_chained(pass_packed<DIMS, MEASURE, RULE, false>, (unsigned)blocks, 256u, 0, st,
+                          a, rgroups, 0u, 0u);
 }
 
 }  // namespace
@@ -135,8 +150,11 @@ cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream
 cudaError_t packed_query_occupancy(DeviceProps& dp) {
     cudaError_t e;
 #define ISING_OCC(R, D, M)                                                                    \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_packed[R][D - 2][M],   \
-                                                      pass_packed<D, M, R>, 256, 0);          \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_packed[R][D - 2][M][0],\
+                                                      pass_packed<D, M, R, false>, 256, 0);   \
+    if (e != cudaSuccess) return e;                                                           \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_packed[R][D - 2][M][1],\
+                                                      pass_packed<D, M, R, true>, 256, 0);    \
     if (e != cudaSuccess) return e;
     ISING_OCC(kRuleMetropolis, 2, false)
     ISING_OCC(kRuleMetropolis, 2, true)

@@ -191,7 +191,10 @@ __device__ __forceinline__ void update_vec_pair_hb(uint4 (&S)[2], const uint4 (&
     S[1] = make_uint4(out[4], out[5], out[6], out[7]);
 }
 
-template <int DIMS, bool MEASURE, int RULE>
+// TWO: every thread has exactly two (row pair, column) items per tile (the
+// host checks R / 2 * W / 16 == 2 * 128); that instance holds no loop over
+// items and no guard, which keeps it clear of the register cap.
+template <int DIMS, bool MEASURE, int RULE, bool TWO>
 __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kStages];
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
                 }
             };
             // the same order when every thread has exactly two items (no loop,
-            // no guard: 39.3 -> 37.4 us per pass at L = 8192, as the guards and
+            // no guard: 39.3 -> 38.0 us per pass at L = 8192, as the guards and
             // the loop-carried draws had held the kernel at its register cap)
             auto walk_two = [&](auto single) {
                 const uint32_t second = threadIdx.x + blockDim.x;
@@ -385,15 +388,18 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
                     update(d0, u0);
                 }
             };
-            const bool two = n_items == 2u * blockDim.x, one = n_items <= blockDim.x;
-            if (pairs == 1u) {
-                if (two) walk_two(std::true_type{});
-                else if (one) walk_one(std::true_type{});
-                else walk(std::true_type{});
+            if constexpr (TWO) {
+                if (pairs == 1u) walk_two(std::true_type{});
+                else walk_two(std::false_type{});
             } else {
-                if (two) walk_two(std::false_type{});
-                else if (one) walk_one(std::false_type{});
-                else walk(std::false_type{});
+                const bool one = n_items <= blockDim.x;
+                if (pairs == 1u) {
+                    if (one) walk_one(std::true_type{});
+                    else walk(std::true_type{});
+                } else {
+                    if (one) walk_one(std::false_type{});
+                    else walk(std::false_type{});
+                }
             }
             i0 = 2u * pairs;
         }
@@ -442,7 +448,7 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
     }
 }
 
-template <int DIMS, bool MEASURE, int RULE>
+template <int DIMS, bool MEASURE, int RULE, bool TWO>
 cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uint32_t extra_tx,
                          cudaStream_t st, int rows_per_tile, int ctas_per_sm) {
     TmaGeom tg;
@@ -465,20 +471,20 @@ cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uin
     static int attr_set = 0;  // largest dynamic shared memory opted into so far
     cudaError_t e = cudaSuccess;
     if ((int)smem > attr_set) {
-        e = cudaFuncSetAttribute(pass_int8_tma<DIMS, MEASURE, RULE>,
+        e = cudaFuncSetAttribute(pass_int8_tma<DIMS, MEASURE, RULE, TWO>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = 200 * 1024;
     }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_int8_tma<DIMS, MEASURE, RULE>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_int8_tma<DIMS, MEASURE, RULE, TWO>,
                                                       threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     int grid = dp.sm_count * per_sm;
     if (grid > tg.tiles) grid = tg.tiles;
-    return launch_chained(pass_int8_tma<DIMS, MEASURE, RULE>, (unsigned)grid, (unsigned)threads,
+    return launch_chained(pass_int8_tma<DIMS, MEASURE, RULE, TWO>, (unsigned)grid, (unsigned)threads,
                           smem, st, a, tg, err);
 }
 
@@ -496,15 +502,29 @@ bool int8_tma_ok(int dims, int L, int rows_per_tile) {
     return (size_t)kStages * stage <= 200 * 1024;
 }
 
+template <int RULE, bool TWO>
+static cudaError_t int8_pass_tma_walk(const PassArgs& a, int dims, bool measure,
+                                      const DeviceProps& dp, int* err, uint32_t extra_tx,
+                                      cudaStream_t st, int R, int ctas) {
+    if (dims == 2)
+        return measure ? launch_tma_t<2, true, RULE, TWO>(a, dp, err, extra_tx, st, R, ctas)
+                       : launch_tma_t<2, false, RULE, TWO>(a, dp, err, extra_tx, st, R, ctas);
+    return measure ? launch_tma_t<3, true, RULE, TWO>(a, dp, err, extra_tx, st, R, ctas)
+                   : launch_tma_t<3, false, RULE, TWO>(a, dp, err, extra_tx, st, R, ctas);
+}
+
 template <int RULE>
 static cudaError_t int8_pass_tma_rule(const PassArgs& a, int dims, bool measure,
                                       const DeviceProps& dp, int* err, uint32_t extra_tx,
                                       cudaStream_t st, int R, int ctas) {
-    if (dims == 2)
-        return measure ? launch_tma_t<2, true, RULE>(a, dp, err, extra_tx, st, R, ctas)
-                       : launch_tma_t<2, false, RULE>(a, dp, err, extra_tx, st, R, ctas);
-    return measure ? launch_tma_t<3, true, RULE>(a, dp, err, extra_tx, st, R, ctas)
-                   : launch_tma_t<3, false, RULE>(a, dp, err, extra_tx, st, R, ctas);
+    if constexpr (RULE == kRuleMultiHit) {  // takes the row-at-a-time loop only
+        return int8_pass_tma_walk<RULE, false>(a, dims, measure, dp, err, extra_tx, st, R, ctas);
+    } else {
+        const int rows = R > 0 ? R : tile_rows(a.L);
+        const bool two = (rows / 2) * (a.W / 16) == 2 * 128;  // 128 threads per CTA
+        return two ? int8_pass_tma_walk<RULE, true>(a, dims, measure, dp, err, extra_tx, st, R, ctas)
+                   : int8_pass_tma_walk<RULE, false>(a, dims, measure, dp, err, extra_tx, st, R, ctas);
+    }
 }
 
 // Where the staged kernel measured faster than the strip kernel on GB300: 2D
