@@ -64,7 +64,10 @@ __device__ __forceinline__ uint32_t uphill_accept(uint32_t D, uint32_t u, int j,
 
 // The same test for four sites by counting: byte j gains 2 for every threshold
 // u_j lies below; since the thresholds fall with k, site j (d_j < dims) flips
-// iff 2*(count_j + d_j) >= 2*dims, read off bit 7 after the bias.
+// iff 2*(count_j + d_j) >= 2*dims, read off bit 7 after the bias.  A site with
+// d_j >= dims has bit 7 set by D + bias alone, and no byte carries (at most
+// 0x80 + 4 dims < 0x100), so the mask already holds every downhill
+// flip: where all four draws are made it is the whole flip mask.
 template <int DIMS>
 __device__ __forceinline__ uint32_t uphill_count(uint32_t D, const Philox4& u, const PassArgs& a) {
     constexpr uint32_t bias = (0x80u - 2u * DIMS) * kByteOnes;
@@ -452,20 +455,23 @@ __device__ __forceinline__ void update_vec_pair(uint4 (&S)[2], const uint4 (&x)[
         D[4 * q + 3] = disagreements<DIMS>(S[q].w, x[q].w, xs[q].w, ym[q].w, yp[q].w, zm[q].w, zp[q].w);
     }
 #pragma unroll
-    for (int w = 0; w < 8; ++w) X[w] = downhill_mask<DIMS>(D[w]) | uphill_count<DIMS>(D[w], u[w], a);
-    uint32_t out[8], en = 0u;
+    for (int w = 0; w < 8; ++w) X[w] = uphill_count<DIMS>(D[w], u[w], a);
+    uint32_t out[8], en = 0u, mn = 0u;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
         out[w] = sv[w] ^ X[w];
         if (MEASURE) {
-            m_neg += __popc(out[w] & kByteBit7);
+            mn += out[w] & kByteBit1;  // 2 per spin -1 (0xFF), at most 16 per byte
             if (a.c == 1) {  // 2 d_new per byte, at most 12: eight words fit a byte
                 constexpr uint32_t q2 = 4u * DIMS * kByteOnes;
                 en += (D[w] & ~X[w]) | ((q2 - D[w]) & X[w]);
             }
         }
     }
-    if (MEASURE && a.c == 1) e_acc = __dp4a((int)en, (int)kByteOnes, e_acc);
+    if (MEASURE) {
+        m_neg += __dp4a((int)mn, (int)kByteOnes, 0) >> 1;
+        if (a.c == 1) e_acc = __dp4a((int)en, (int)kByteOnes, e_acc);
+    }
     S[0] = make_uint4(out[0], out[1], out[2], out[3]);
     S[1] = make_uint4(out[4], out[5], out[6], out[7]);
 }
@@ -698,20 +704,21 @@ __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uin
         }
         return acc;
     }
-    if constexpr (ALIGNED) return acc;
+    if constexpr (!ALIGNED) {
 #pragma unroll 1
-    for (int g = 0; g < 9; ++g) {
-        const int lo = 4 * g - (int)m;  // bit of the group's word 0 (may be < 0)
-        const uint32_t gmask = lo >= 0 ? (0xFu << lo) : (0xFu >> (-lo));
-        if (!(need & gmask)) continue;
-        const Philox4 u = philox4x32_10(g0 + (uint32_t)g, a.t, c2, kTagSweep, a.key0,
-                                        a.key1);
-        const uint32_t w[4] = {u.w0, u.w1, u.w2, u.w3};
+        for (int g = 0; g < 9; ++g) {
+            const int lo = 4 * g - (int)m;  // bit of the group's word 0 (may be < 0)
+            const uint32_t gmask = lo >= 0 ? (0xFu << lo) : (0xFu >> (-lo));
+            if (!(need & gmask)) continue;
+            const Philox4 u = philox4x32_10(g0 + (uint32_t)g, a.t, c2, kTagSweep, a.key0,
+                                            a.key1);
+            const uint32_t w[4] = {u.w0, u.w1, u.w2, u.w3};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int b = lo + j;
-            if (b < 0 || b > 31) continue;
-            acc |= (w[j] < site_threshold<DIMS>(k, b, a) ? 1u : 0u) << b;
+            for (int j = 0; j < 4; ++j) {
+                const int b = lo + j;
+                if (b < 0 || b > 31) continue;
+                acc |= (w[j] < site_threshold<DIMS>(k, b, a) ? 1u : 0u) << b;
+            }
         }
     }
     return acc;
@@ -749,27 +756,80 @@ __device__ __forceinline__ uint32_t grouped_row(uint32_t j, uint32_t rows, uint3
     return k * rgroups + c;
 }
 
-// FULL: W is a multiple of 32 and nq = W / 32 (and L in 3D) a power of two,
-// 2^nq_shift (2^l_shift): every word is full, rows start on a Philox group,
-// and the item's row and word come from shifts instead of divisions.
-template <int DIMS, bool MEASURE, int NC, int RULE = kRuleMetropolis, bool ILP9 = false,
-          bool FULL = false>
+// The rule applied to one packed word, given the word s and its neighbour
+// words (sh: the x-neighbour across the colour, shifted into place), then the
+// store and the word's share of E and M.  valid: the word's sites (nb bits);
+// hbase: the half index of bit 0 (its Philox draw is word hbase & 3 of group
+// hbase >> 2).  ALIGNED: hbase % 4 == 0 is known (packed_accept).
+template <int DIMS, bool MEASURE, int RULE, bool ILP9, bool ALIGNED>
+__device__ __forceinline__ void packed_update(const PassArgs& a, uint32_t* own_word, uint32_t s,
+                                              uint32_t o, uint32_t sh, uint32_t oym,
+                                              uint32_t oyp, uint32_t ozm, uint32_t ozp,
+                                              uint32_t valid, uint32_t nb, uint32_t hbase,
+                                              int& e_acc, int& m_acc) {
+    uint32_t flip;
+    if constexpr (RULE == kRuleHeatBath) {  // every valid site draws
+        const Digits k = DIMS == 2 ? digits2(s ^ o, s ^ sh, s ^ oym, s ^ oyp)
+                                   : digits3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
+        flip = packed_accept<DIMS, Digits, ILP9, ALIGNED>(k, valid, hbase, a, (uint32_t)a.c);
+    } else if constexpr (RULE == kRuleMultiHit) {  // a.hits trials, neighbours fixed
+        uint32_t cur = s;
+#pragma unroll 1
+        for (int m = 0; m < a.hits; ++m) {
+            Counts k;
+            if (DIMS == 2) {
+                k = count2(cur ^ o, cur ^ sh, cur ^ oym, cur ^ oyp);
+            } else {
+                k = count3(cur ^ o, cur ^ sh, cur ^ oym, cur ^ oyp, cur ^ ozm, cur ^ ozp);
+            }
+            uint32_t f = k.always;
+            const uint32_t need = ~k.always & valid;
+            if (need)
+                f |= packed_accept<DIMS, Counts, ILP9, ALIGNED>(k, need, hbase, a,
+                                                               (uint32_t)a.c + 2u * (uint32_t)m);
+            cur ^= f & valid;
+        }
+        flip = cur ^ s;
+    } else {
+        Counts k;
+        if (DIMS == 2) {
+            k = count2(s ^ o, s ^ sh, s ^ oym, s ^ oyp);
+        } else {
+            k = count3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
+        }
+        flip = k.always;
+        const uint32_t need = ~k.always & valid;
+        if (need) flip |= packed_accept<DIMS, Counts, ILP9, ALIGNED>(k, need, hbase, a, (uint32_t)a.c);
+    }
+    const uint32_t snew = s ^ (flip & valid);
+    *own_word = snew;
+    if (MEASURE) {
+        m_acc += 2 * __popc(snew & valid) - (int)nb;
+        if (a.c == 1) {
+            int dsum = __popc((snew ^ o) & valid) + __popc((snew ^ sh) & valid) +
+                       __popc((snew ^ oym) & valid) + __popc((snew ^ oyp) & valid);
+            if (DIMS == 3) dsum += __popc((snew ^ ozm) & valid) + __popc((snew ^ ozp) & valid);
+            e_acc += 2 * dsum - (int)nb * 2 * DIMS;
+        }
+    }
+}
+
+template <int DIMS, bool MEASURE, int NC, int RULE = kRuleMetropolis, bool ILP9 = false>
 __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, int& e_acc,
-                                            int& m_acc, uint32_t rgroups = 1u,
-                                            uint32_t nq_shift = 0u, uint32_t l_shift = 0u) {
+                                            int& m_acc, uint32_t rgroups = 1u) {
     const uint32_t W = (uint32_t)a.W;
-    const uint32_t nq = FULL ? 1u << nq_shift : (W + 31u) >> 5;
+    const uint32_t nq = (W + 31u) >> 5;
     const uint32_t L = (uint32_t)a.L;
     uint32_t* own = static_cast<uint32_t*>(a.own);
     const uint32_t* other = static_cast<const uint32_t*>(a.other);
-    const uint32_t j = FULL ? item >> nq_shift : item / nq, q = item - j * nq;
-    const uint32_t r = !FULL && rgroups > 1u ? grouped_row(j, (uint32_t)a.rows, rgroups) : j;
+    const uint32_t j = item / nq, q = item - j * nq;
+    const uint32_t r = rgroups > 1u ? grouped_row(j, (uint32_t)a.rows, rgroups) : j;
     uint32_t y = r, z = 0;
     if (DIMS == 3) {
-        z = FULL ? r >> l_shift : r / L;
+        z = r / L;
         y = r - z * L;
     }
-    const uint32_t nb = FULL ? 32u : (W - 32u * q < 32u ? W - 32u * q : 32u);  // valid bits
+    const uint32_t nb = W - 32u * q < 32u ? W - 32u * q : 32u;  // valid bits
     const uint32_t valid = nb == 32u ? 0xFFFFFFFFu : ((1u << nb) - 1u);
     const uint32_t plane = z * L;
     const uint32_t row = r * nq;
@@ -802,53 +862,9 @@ __device__ __forceinline__ void packed_word(const PassArgs& a, uint32_t item, in
             sh = __funnelshift_r(o, load_other<NC>(other + row + q + 1u), 1);
         }
     }
-    uint32_t flip;
-    if constexpr (RULE == kRuleHeatBath) {  // every valid site draws
-        const Digits k = DIMS == 2 ? digits2(s ^ o, s ^ sh, s ^ oym, s ^ oyp)
-                                   : digits3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
-        flip = packed_accept<DIMS, Digits, ILP9, FULL>(k, valid, r * W + 32u * q, a, (uint32_t)a.c);
-    } else if constexpr (RULE == kRuleMultiHit) {  // a.hits trials, neighbours fixed
-        uint32_t cur = s;
-#pragma unroll 1
-        for (int m = 0; m < a.hits; ++m) {
-            Counts k;
-            if (DIMS == 2) {
-                k = count2(cur ^ o, cur ^ sh, cur ^ oym, cur ^ oyp);
-            } else {
-                k = count3(cur ^ o, cur ^ sh, cur ^ oym, cur ^ oyp, cur ^ ozm, cur ^ ozp);
-            }
-            uint32_t f = k.always;
-            const uint32_t need = ~k.always & valid;
-            if (need)
-                f |= packed_accept<DIMS, Counts, ILP9, FULL>(k, need, r * W + 32u * q, a,
-                                                       (uint32_t)a.c + 2u * (uint32_t)m);
-            cur ^= f & valid;
-        }
-        flip = cur ^ s;
-    } else {
-        Counts k;
-        if (DIMS == 2) {
-            k = count2(s ^ o, s ^ sh, s ^ oym, s ^ oyp);
-        } else {
-            k = count3(s ^ o, s ^ sh, s ^ oym, s ^ oyp, s ^ ozm, s ^ ozp);
-        }
-        flip = k.always;
-        const uint32_t need = ~k.always & valid;
-        if (need)
-            flip |= packed_accept<DIMS, Counts, ILP9, FULL>(k, need, r * W + 32u * q, a,
-                                                            (uint32_t)a.c);
-    }
-    const uint32_t snew = s ^ (flip & valid);
-    own[row + q] = snew;
-    if (MEASURE) {
-        m_acc += 2 * __popc(snew & valid) - (int)nb;
-        if (a.c == 1) {
-            int dsum = __popc((snew ^ o) & valid) + __popc((snew ^ sh) & valid) +
-                       __popc((snew ^ oym) & valid) + __popc((snew ^ oyp) & valid);
-            if (DIMS == 3) dsum += __popc((snew ^ ozm) & valid) + __popc((snew ^ ozp) & valid);
-            e_acc += 2 * dsum - (int)nb * 2 * DIMS;
-        }
-    }
+    packed_update<DIMS, MEASURE, RULE, ILP9, false>(a, own + row + q, s, o, sh, oym, oyp, ozm,
+                                                     ozp, valid, nb, r * W + 32u * q, e_acc,
+                                                     m_acc);
 }
 
 }  // namespace ising

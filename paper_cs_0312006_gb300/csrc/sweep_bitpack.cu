@@ -30,8 +30,12 @@ namespace {
 // One item = one 32-site word of the colour array (see packed_word()).
 // Rows that start inside a Philox group are visited grouped by their offset
 // (rgroups, see packed_word).
-// FULL instances serve lattices whose words are all full and whose word and
-// row counts are powers of two (packed_word's FULL form; nq_shift, l_shift).
+// FULL instances serve lattices whose words are all full (W % 32 == 0) and
+// whose word count per half row nq = 2^nq_shift is a power of two (then so is
+// L = 64 nq; in 3D l_shift = log2 L): an item's row, word and neighbours come
+// from shifts and masks, every row starts on a Philox group, and a thread
+// loads its next item's six words (eight in 3D) before it updates the current
+// one, so that their latency hides behind the current item's draws.
 template <int DIMS, bool MEASURE, int RULE, bool FULL>
 __global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a, uint32_t rgroups,
                                                       uint32_t nq_shift, uint32_t l_shift) {
@@ -40,9 +44,61 @@ __global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a, uint32_t rgrou
     int e_acc = 0, m_acc = 0;
     grid_dependency_wait();
     launch_dependents();
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride)
-        packed_word<DIMS, MEASURE, 1, RULE, RULE != kRuleMultiHit, FULL>(a, g, e_acc, m_acc,
-                                                                        rgroups, nq_shift, l_shift);
+    if constexpr (!FULL) {
+        for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride)
+            packed_word<DIMS, MEASURE, 1, RULE, RULE != kRuleMultiHit>(a, g, e_acc, m_acc,
+                                                                       rgroups);
+    } else {
+        const uint32_t nq = 1u << nq_shift, L = (uint32_t)a.L, W = (uint32_t)a.W;
+        uint32_t* own = static_cast<uint32_t*>(a.own);
+        const uint32_t* other = static_cast<const uint32_t*>(a.other);
+        struct Words {
+            uint32_t o, x, ym, yp, zm, zp, s;
+        };
+        // the loads only: nothing here waits for them
+        auto load = [&](uint32_t item, Words& w) {
+            const uint32_t r = item >> nq_shift, q = item & (nq - 1u);
+            const uint32_t z = DIMS == 3 ? r >> l_shift : 0u, y = r & (L - 1u);
+            const uint32_t row = r * nq, plane = z * L;
+            const int p = (a.c + (int)y + (int)z) & 1;
+            // x-neighbour word: the one before (p = 0) or after (p = 1), wrapping in the row
+            const uint32_t xq = (p == 0 ? q - 1u : q + 1u) & (nq - 1u);
+            w.o = __ldg(other + row + q);
+            w.x = __ldg(other + row + xq);
+            w.ym = __ldg(other + (plane + ((y - 1u) & (L - 1u))) * nq + q);
+            w.yp = __ldg(other + (plane + ((y + 1u) & (L - 1u))) * nq + q);
+            if (DIMS == 3) {
+                w.zm = __ldg(other + ((((z - 1u) & (L - 1u)) * L + y) * nq + q));
+                w.zp = __ldg(other + ((((z + 1u) & (L - 1u)) * L + y) * nq + q));
+            } else {
+                w.zm = w.zp = 0u;
+            }
+            w.s = own[row + q];
+        };
+        uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+        if (g < items) {
+            Words cur;
+            load(g, cur);
+            for (;;) {
+                const uint32_t gn = g + stride;
+                const bool more = gn < items;
+                Words nxt = cur;
+                if (more) load(gn, nxt);
+                const uint32_t r = g >> nq_shift, q = g & (nq - 1u);
+                const uint32_t z = DIMS == 3 ? r >> l_shift : 0u, y = r & (L - 1u);
+                const int p = (a.c + (int)y + (int)z) & 1;
+                // bit b <- neighbour xh - 1 (p = 0) or xh + 1 (p = 1)
+                const uint32_t sh = p == 0 ? __funnelshift_l(cur.x, cur.o, 1)
+                                           : __funnelshift_r(cur.o, cur.x, 1);
+                packed_update<DIMS, MEASURE, RULE, RULE != kRuleMultiHit, true>(
+                    a, own + r * nq + q, cur.s, cur.o, sh, cur.ym, cur.yp, cur.zm, cur.zp,
+                    0xFFFFFFFFu, 32u, r * W + 32u * q, e_acc, m_acc);
+                if (!more) break;
+                cur = nxt;
+                g = gn;
+            }
+        }
+    }
     if (MEASURE) block_reduce_add(e_acc, m_acc, a.obs, a.c == 1);
 }
 
@@ -126,7 +182,8 @@ template <int DIMS, bool MEASURE, int RULE>
 cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream_t st) {
     const int nq = (a.W + 31) >> 5;
     const int64_t items = a.rows * nq;
-    const bool full = a.W % 32 == 0 && is_pow2(nq) && (DIMS == 2 || is_pow2(a.L));
+    // (multi-hit keeps the general loop: its trials need the registers)
+    const bool full = RULE != kRuleMultiHit && a.W % 32 == 0 && is_pow2(nq);
     int64_t blocks = (items + 255) / 256;
     const int64_t cap =
         (int64_t)dp.sm_count * dp.blocks_per_sm_packed[RULE][DIMS - 2][MEASURE][full ? 1 : 0];
@@ -135,11 +192,13 @@ cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream
     // odd W: a row's offset in its Philox group is r W mod 4, set by r mod 4;
     // W = 2 mod 4: by r mod 2
     const uint32_t rgroups = packed_row_groups((uint32_t)a.W);
-    if (full) {
-        const uint32_t nq_shift = (uint32_t)__builtin_ctz((unsigned)nq);
-        const uint32_t l_shift = DIMS == 3 ? (uint32_t)__builtin_ctz((unsigned)a.L) : 0u;
-        return launch_chained(pass_packed<DIMS, MEASURE, RULE, true>, (unsigned)blocks, 256u, 0,
-                              st, a, rgroups, nq_shift, l_shift);
+    if constexpr (RULE != kRuleMultiHit) {
+        if (full) {
+            const uint32_t nq_shift = (uint32_t)__builtin_ctz((unsigned)nq);
+            const uint32_t l_shift = DIMS == 3 ? (uint32_t)__builtin_ctz((unsigned)a.L) : 0u;
+            return launch_chained(pass_packed<DIMS, MEASURE, RULE, true>, (unsigned)blocks, 256u,
+                                  0, st, a, rgroups, nq_shift, l_shift);
+        }
     }
     return launch_chained(pass_packed<DIMS, MEASURE, RULE, false>, (unsigned)blocks, 256u, 0, st,
                           a, rgroups, 0u, 0u);
@@ -149,13 +208,12 @@ cudaError_t launch_packed_t(const PassArgs& a, const DeviceProps& dp, cudaStream
 
 cudaError_t packed_query_occupancy(DeviceProps& dp) {
     cudaError_t e;
-#define ISING_OCC(R, D, M)                                                                    \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_packed[R][D - 2][M][0],\
-                                                      pass_packed<D, M, R, false>, 256, 0);   \
-    if (e != cudaSuccess) return e;                                                           \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_packed[R][D - 2][M][1],\
-                                                      pass_packed<D, M, R, true>, 256, 0);    \
+#define ISING_OCC1(R, D, M, F)                                                                \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp.blocks_per_sm_packed[R][D - 2][M][F],\
+                                                      pass_packed<D, M, R, F>, 256, 0);       \
     if (e != cudaSuccess) return e;
+#define ISING_OCC(R, D, M) ISING_OCC1(R, D, M, false) ISING_OCC1(R, D, M, true)
+#define ISING_OCC_MH(R, D, M) ISING_OCC1(R, D, M, false)
     ISING_OCC(kRuleMetropolis, 2, false)
     ISING_OCC(kRuleMetropolis, 2, true)
     ISING_OCC(kRuleMetropolis, 3, false)
@@ -164,11 +222,13 @@ cudaError_t packed_query_occupancy(DeviceProps& dp) {
     ISING_OCC(kRuleHeatBath, 2, true)
     ISING_OCC(kRuleHeatBath, 3, false)
     ISING_OCC(kRuleHeatBath, 3, true)
-    ISING_OCC(kRuleMultiHit, 2, false)
-    ISING_OCC(kRuleMultiHit, 2, true)
-    ISING_OCC(kRuleMultiHit, 3, false)
-    ISING_OCC(kRuleMultiHit, 3, true)
+    ISING_OCC_MH(kRuleMultiHit, 2, false)
+    ISING_OCC_MH(kRuleMultiHit, 2, true)
+    ISING_OCC_MH(kRuleMultiHit, 3, false)
+    ISING_OCC_MH(kRuleMultiHit, 3, true)
+#undef ISING_OCC_MH
 #undef ISING_OCC
+#undef ISING_OCC1
     return cudaSuccess;
 }
 

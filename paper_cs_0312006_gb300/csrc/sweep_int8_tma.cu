@@ -174,19 +174,22 @@ __device__ __forceinline__ void update_vec_pair_hb(uint4 (&S)[2], const uint4 (&
         }
         X[w] = m;
     }
-    uint32_t out[8], en = 0u;
+    uint32_t out[8], en = 0u, mn = 0u;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
         out[w] = sv[w] ^ X[w];
         if (MEASURE) {
-            m_neg += __popc(out[w] & kByteBit7);
+            mn += out[w] & kByteBit1;  // 2 per spin -1 (0xFF), at most 16 per byte
             if (a.c == 1) {  // 2 d_new per byte, at most 12: eight words fit a byte
                 constexpr uint32_t q2 = 4u * DIMS * kByteOnes;
                 en += (D[w] & ~X[w]) | ((q2 - D[w]) & X[w]);
             }
         }
     }
-    if (MEASURE && a.c == 1) e_acc = __dp4a((int)en, (int)kByteOnes, e_acc);
+    if (MEASURE) {
+        m_neg += __dp4a((int)mn, (int)kByteOnes, 0) >> 1;
+        if (a.c == 1) e_acc = __dp4a((int)en, (int)kByteOnes, e_acc);
+    }
     S[0] = make_uint4(out[0], out[1], out[2], out[3]);
     S[1] = make_uint4(out[4], out[5], out[6], out[7]);
 }
