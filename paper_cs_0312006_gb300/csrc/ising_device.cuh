@@ -74,6 +74,52 @@ __device__ __forceinline__ Philox4 philox4x32_10_split(uint32_t c0, uint32_t c1,
     return Philox4{c0, c1, c2, c3};
 }
 
+// Eight calls whose counter word 0 runs over two sets of four consecutive
+// values (a .. a + 3 and b .. b + 3, no 32-bit wrap), the other counter words
+// and the key shared, advanced one round at a time so that a caller can place
+// other work between the rounds.  In the first round the product of a + i is
+// the product of a plus i times the multiplier (a 64-bit add instead of a
+// multiply).  result(w) equals philox4x32_10(counter of call w, ...).
+struct PhiloxRuns8 {
+    uint32_t c0[8], c1[8], c2[8], c3[8];
+    uint32_t k0, k1;
+
+    __device__ __forceinline__ void first_round(uint32_t a, uint32_t b, uint32_t ctr1,
+                                                uint32_t ctr2, uint32_t ctr3, uint32_t key0,
+                                                uint32_t key1) {
+        const uint64_t pa_a = (uint64_t)a * kPhiloxMulA, pa_b = (uint64_t)b * kPhiloxMulA;
+        const uint64_t pb = (uint64_t)ctr2 * kPhiloxMulB;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint64_t pa = (w < 4 ? pa_a : pa_b) + (uint64_t)(w & 3) * kPhiloxMulA;
+            c0[w] = (uint32_t)(pb >> 32) ^ ctr1 ^ key0;
+            c1[w] = (uint32_t)pb;
+            c2[w] = (uint32_t)(pa >> 32) ^ ctr3 ^ key1;
+            c3[w] = (uint32_t)pa;
+        }
+        k0 = key0 + kPhiloxWeylA;
+        k1 = key1 + kPhiloxWeylB;
+    }
+
+    __device__ __forceinline__ void next_round() {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint64_t pa = (uint64_t)c0[w] * kPhiloxMulA;
+            const uint64_t pb = (uint64_t)c2[w] * kPhiloxMulB;
+            c0[w] = (uint32_t)(pb >> 32) ^ c1[w] ^ k0;
+            c1[w] = (uint32_t)pb;
+            c2[w] = (uint32_t)(pa >> 32) ^ c3[w] ^ k1;
+            c3[w] = (uint32_t)pa;
+        }
+        k0 += kPhiloxWeylA;
+        k1 += kPhiloxWeylB;
+    }
+
+    __device__ __forceinline__ Philox4 result(int w) const {
+        return Philox4{c0[w], c1[w], c2[w], c3[w]};
+    }
+};
+
 // Programmatic dependent launch (griddepcontrol, sm_90 and later).  The
 // per-lattice pass kernels are launched with programmatic stream
 // serialisation (launch_chained), so the next kernel in the stream can be

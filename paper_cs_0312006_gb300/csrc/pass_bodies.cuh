@@ -431,51 +431,6 @@ __device__ __forceinline__ uint4 update_vec(const uint4& s, const uint4& x, cons
 }
 
 
-// Two vectors at once (Metropolis), their eight Philox calls made by the
-// caller (u[w] is the draw of word w: vector w >> 2, word w & 3).  The
-// calls depend only on counters, so a kernel issues them before its loads
-// of the spins; every word then takes the counting test (the draw is used
-// only where dE > 0, so the result equals the lazy per-group form).
-template <int DIMS, bool MEASURE>
-__device__ __forceinline__ void update_vec_pair(uint4 (&S)[2], const uint4 (&x)[2],
-                                                const uint4 (&xs)[2], const uint4 (&ym)[2],
-                                                const uint4 (&yp)[2], const uint4 (&zm)[2],
-                                                const uint4 (&zp)[2], const Philox4 (&u)[8],
-                                                const PassArgs& a, int& e_acc, int& m_neg) {
-    uint32_t sv[8], D[8], X[8];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        sv[4 * q + 0] = S[q].x;
-        sv[4 * q + 1] = S[q].y;
-        sv[4 * q + 2] = S[q].z;
-        sv[4 * q + 3] = S[q].w;
-        D[4 * q + 0] = disagreements<DIMS>(S[q].x, x[q].x, xs[q].x, ym[q].x, yp[q].x, zm[q].x, zp[q].x);
-        D[4 * q + 1] = disagreements<DIMS>(S[q].y, x[q].y, xs[q].y, ym[q].y, yp[q].y, zm[q].y, zp[q].y);
-        D[4 * q + 2] = disagreements<DIMS>(S[q].z, x[q].z, xs[q].z, ym[q].z, yp[q].z, zm[q].z, zp[q].z);
-        D[4 * q + 3] = disagreements<DIMS>(S[q].w, x[q].w, xs[q].w, ym[q].w, yp[q].w, zm[q].w, zp[q].w);
-    }
-#pragma unroll
-    for (int w = 0; w < 8; ++w) X[w] = uphill_count<DIMS>(D[w], u[w], a);
-    uint32_t out[8], en = 0u, mn = 0u;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        out[w] = sv[w] ^ X[w];
-        if (MEASURE) {
-            mn += out[w] & kByteBit1;  // 2 per spin -1 (0xFF), at most 16 per byte
-            if (a.c == 1) {  // 2 d_new per byte, at most 12: eight words fit a byte
-                constexpr uint32_t q2 = 4u * DIMS * kByteOnes;
-                en += (D[w] & ~X[w]) | ((q2 - D[w]) & X[w]);
-            }
-        }
-    }
-    if (MEASURE) {
-        m_neg += __dp4a((int)mn, (int)kByteOnes, 0) >> 1;
-        if (a.c == 1) e_acc = __dp4a((int)en, (int)kByteOnes, e_acc);
-    }
-    S[0] = make_uint4(out[0], out[1], out[2], out[3]);
-    S[1] = make_uint4(out[4], out[5], out[6], out[7]);
-}
-
 // 16 bytes of the other colour at byte offset o (any alignment): two aligned
 // 16-byte loads and a byte shift.  The shift r = o mod 16 is the same for a
 // whole lattice and direction (it depends only on W, L and the direction), so

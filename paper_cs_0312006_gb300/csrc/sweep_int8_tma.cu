@@ -140,64 +140,77 @@ __device__ __forceinline__ void issue_tile(const PassArgs& a, const TmaGeom& tg,
 }
 
 
-// Heat bath for two vectors at once: every site draws (the eight Philox calls
-// made by the caller, u[w] for word w) and flips iff u < thr[d], the threshold
-// read from a shared table indexed by the site's disagreeing-neighbour count d
-// (byte j of D is 2 d_j).
-template <int DIMS, bool MEASURE>
-__device__ __forceinline__ void update_vec_pair_hb(uint4 (&S)[2], const uint4 (&x)[2],
-                                                   const uint4 (&xs)[2], const uint4 (&ym)[2],
-                                                   const uint4 (&yp)[2], const uint4 (&zm)[2],
-                                                   const uint4 (&zp)[2], const Philox4 (&u)[8],
-                                                   const uint32_t* s_thb, const PassArgs& a,
-                                                   int& e_acc, int& m_neg) {
-    uint32_t sv[8], D[8], X[8];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        sv[4 * q + 0] = S[q].x;
-        sv[4 * q + 1] = S[q].y;
-        sv[4 * q + 2] = S[q].z;
-        sv[4 * q + 3] = S[q].w;
-        D[4 * q + 0] = disagreements<DIMS>(S[q].x, x[q].x, xs[q].x, ym[q].x, yp[q].x, zm[q].x, zp[q].x);
-        D[4 * q + 1] = disagreements<DIMS>(S[q].y, x[q].y, xs[q].y, ym[q].y, yp[q].y, zm[q].y, zp[q].y);
-        D[4 * q + 2] = disagreements<DIMS>(S[q].z, x[q].z, xs[q].z, ym[q].z, yp[q].z, zm[q].z, zp[q].z);
-        D[4 * q + 3] = disagreements<DIMS>(S[q].w, x[q].w, xs[q].w, ym[q].w, yp[q].w, zm[q].w, zp[q].w);
+// One item of the pair walk: two 16-byte vectors (the same column of a row
+// pair), as their 8 words and byte-sliced disagreement counts D (byte j of D
+// is 2 d_j), taken from shared memory when the item is loaded; step(w) then
+// applies the rule to word w with its draw u (word w & 3 of call w: vector
+// w >> 2).  Metropolis takes the counting mask (uphill_count, which holds the
+// downhill flips too); the heat bath reads thr[d] per site from a shared
+// table.  en sums 2 d_new per byte (at most 12 per word: eight words fit a
+// byte), mn sums 2 per spin -1 (at most 16 per byte).
+template <int DIMS, bool MEASURE, int RULE>
+struct PairUpdate {
+    uint32_t sv[8], D[8], rowg[2];
+    uint32_t en, mn;
+
+    __device__ __forceinline__ void set(int q, const uint4& S, const uint4& x, const uint4& xs,
+                                        const uint4& ym, const uint4& yp, const uint4& zm,
+                                        const uint4& zp, uint32_t row) {
+        sv[4 * q + 0] = S.x;
+        sv[4 * q + 1] = S.y;
+        sv[4 * q + 2] = S.z;
+        sv[4 * q + 3] = S.w;
+        D[4 * q + 0] = disagreements<DIMS>(S.x, x.x, xs.x, ym.x, yp.x, zm.x, zp.x);
+        D[4 * q + 1] = disagreements<DIMS>(S.y, x.y, xs.y, ym.y, yp.y, zm.y, zp.y);
+        D[4 * q + 2] = disagreements<DIMS>(S.z, x.z, xs.z, ym.z, yp.z, zm.z, zp.z);
+        D[4 * q + 3] = disagreements<DIMS>(S.w, x.w, xs.w, ym.w, yp.w, zm.w, zp.w);
+        rowg[q] = row;
+        if (q == 0) en = mn = 0u;
     }
+
+    __device__ __forceinline__ void step(int w, const Philox4& u, const PassArgs& a,
+                                         const uint32_t* s_thb) {
+        uint32_t X;
+        if constexpr (RULE == kRuleHeatBath) {
+            const uint32_t uw[4] = {u.w0, u.w1, u.w2, u.w3};
+            X = 0u;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const uint32_t uw[4] = {u[w].w0, u[w].w1, u[w].w2, u[w].w3};
-        uint32_t m = 0u;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t t = s_thb[(D[w] >> (8 * j + 1)) & 7u];
-            m |= uw[j] < t ? (0xFEu << (8 * j)) : 0u;
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t t = s_thb[(D[w] >> (8 * j + 1)) & 7u];
+                X |= uw[j] < t ? (0xFEu << (8 * j)) : 0u;
+            }
+        } else {
+            X = uphill_count<DIMS>(D[w], u, a);
         }
-        X[w] = m;
-    }
-    uint32_t out[8], en = 0u, mn = 0u;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        out[w] = sv[w] ^ X[w];
+        const uint32_t out = sv[w] ^ X;
         if (MEASURE) {
-            mn += out[w] & kByteBit1;  // 2 per spin -1 (0xFF), at most 16 per byte
-            if (a.c == 1) {  // 2 d_new per byte, at most 12: eight words fit a byte
+            mn += out & kByteBit1;
+            if (a.c == 1) {
                 constexpr uint32_t q2 = 4u * DIMS * kByteOnes;
-                en += (D[w] & ~X[w]) | ((q2 - D[w]) & X[w]);
+                en += (D[w] & ~X) | ((q2 - D[w]) & X);
             }
         }
+        sv[w] = out;
     }
-    if (MEASURE) {
-        m_neg += __dp4a((int)mn, (int)kByteOnes, 0) >> 1;
-        if (a.c == 1) e_acc = __dp4a((int)en, (int)kByteOnes, e_acc);
-    }
-    S[0] = make_uint4(out[0], out[1], out[2], out[3]);
-    S[1] = make_uint4(out[4], out[5], out[6], out[7]);
-}
 
-// TWO: every thread has exactly two (row pair, column) items per tile (the
-// host checks R / 2 * W / 16 == 2 * 128); that instance holds no loop over
-// items and no guard, which keeps it clear of the register cap.
-template <int DIMS, bool MEASURE, int RULE, bool TWO>
+    __device__ __forceinline__ void store(uint4* own_g, const PassArgs& a, int& e_acc,
+                                          int& m_neg) const {
+        own_g[rowg[0]] = make_uint4(sv[0], sv[1], sv[2], sv[3]);
+        own_g[rowg[1]] = make_uint4(sv[4], sv[5], sv[6], sv[7]);
+        if (MEASURE) {
+            m_neg += __dp4a((int)mn, (int)kByteOnes, 0) >> 1;
+            if (a.c == 1) e_acc = __dp4a((int)en, (int)kByteOnes, e_acc);
+        }
+    }
+};
+
+// WALK: kWalkTwo when every thread has exactly two (row pair, column) items
+// per tile (R / 2 * W / 16 == 2 * 128), kWalkOne when it has at most one,
+// kWalkLoop otherwise.  The first two instances hold no loop over items and no
+// guard, which keeps them clear of the register cap.
+constexpr int kWalkLoop = 0, kWalkTwo = 1, kWalkOne = 2;
+
+template <int DIMS, bool MEASURE, int RULE, int WALK>
 __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kStages];
@@ -243,17 +256,25 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
         const uint32_t z = DIMS == 3 ? (uint32_t)tile / (uint32_t)tg.bands : 0u;
         const uint32_t y0 = ((uint32_t)tile - z * (uint32_t)tg.bands) * R;
         // a thread's first eight Philox calls depend only on counters: they
-        // run while the tile's copies land
+        // run while the tile's copies land.  An item's calls are two runs of
+        // four consecutive groups (its two rows), so they go through
+        // PhiloxRuns8; `start` makes the first round, and the caller runs the
+        // other nine, alone (draw) or between other work (walk).
         Philox4 u0[8];
-        auto draw = [&](auto single, uint32_t item, Philox4 (&u)[8]) {
+        auto start = [&](auto single, uint32_t item, PhiloxRuns8& ps) {
             uint32_t pr = 0u, v = item;
             if constexpr (!decltype(single)::value) split(item, pr, v);
+            const uint32_t rg = (z * (uint32_t)a.L + y0 + 2u * pr) * nv + v;
+            ps.first_round(rg * 4u, (rg + nv) * 4u, a.t, (uint32_t)a.c, kTagSweep, a.key0,
+                           a.key1);
+        };
+        auto draw = [&](auto single, uint32_t item, Philox4 (&u)[8]) {
+            PhiloxRuns8 ps;
+            start(single, item, ps);
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                const uint32_t rg = (z * (uint32_t)a.L + y0 + 2u * pr + (uint32_t)(w >> 2)) * nv + v;
-                u[w] = philox4x32_10(rg * 4u + (uint32_t)(w & 3), a.t, (uint32_t)a.c,
-                                     kTagSweep, a.key0, a.key1);
-            }
+            for (int r = 1; r < 10; ++r) ps.next_round();
+#pragma unroll
+            for (int w = 0; w < 8; ++w) u[w] = ps.result(w);
         };
         if (RULE == kRuleMetropolis || RULE == kRuleHeatBath) {
             if (R == 2u)  // one pair of rows per tile: an item is a column
@@ -293,10 +314,7 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
             // multiplies overlap the update's logic (39.6 -> 37.4 us per pass
             // at L = 8192 with 128-thread CTAs, two items per thread per tile).
             const uint32_t pairs = R >> 1, n_items = pairs * nv;
-            struct Pair {
-                uint4 S[2], X[2], XS[2], YM[2], YP[2], ZM[2], ZP[2];
-                uint32_t rowg[2];
-            };
+            using Pair = PairUpdate<DIMS, MEASURE, RULE>;
             // with one pair of rows per tile (pairs == 1, the 2D default) an item
             // is a column and every row index below is a constant
             auto load = [&](auto single, uint32_t item, Pair& d) {
@@ -310,56 +328,65 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
                     const int p = (a.c + (int)y + (int)z) & 1;
                     const uint32_t* row32 = reinterpret_cast<const uint32_t*>(oth + (i + 1u) * W);
                     const uint4 oc = oth16[(i + 1u) * nv + v];
-                    d.X[q] = oc;
-                    d.YM[q] = oth16[i * nv + v];
-                    d.YP[q] = oth16[(i + 2u) * nv + v];
-                    d.ZM[q] = make_uint4(0u, 0u, 0u, 0u);
-                    d.ZP[q] = d.ZM[q];
+                    uint4 zm = make_uint4(0u, 0u, 0u, 0u), zp = zm;
                     if (DIMS == 3) {
-                        d.ZM[q] = zm16[i * nv + v];
-                        d.ZP[q] = zp16[i * nv + v];
+                        zm = zm16[i * nv + v];
+                        zp = zp16[i * nv + v];
                     }
+                    uint4 xs;
                     if (p == 0) {
                         const uint32_t prev = row32[(v == 0u ? nv - 1u : v - 1u) * 4u + 3u];
-                        d.XS[q] = make_uint4(__funnelshift_l(prev, oc.x, 8),
-                                             __funnelshift_l(oc.x, oc.y, 8),
-                                             __funnelshift_l(oc.y, oc.z, 8),
-                                             __funnelshift_l(oc.z, oc.w, 8));
+                        xs = make_uint4(__funnelshift_l(prev, oc.x, 8), __funnelshift_l(oc.x, oc.y, 8),
+                                        __funnelshift_l(oc.y, oc.z, 8), __funnelshift_l(oc.z, oc.w, 8));
                     } else {
                         const uint32_t next = row32[(v + 1u == nv ? 0u : v + 1u) * 4u];
-                        d.XS[q] = make_uint4(__funnelshift_r(oc.x, oc.y, 8),
-                                             __funnelshift_r(oc.y, oc.z, 8),
-                                             __funnelshift_r(oc.z, oc.w, 8),
-                                             __funnelshift_r(oc.w, next, 8));
+                        xs = make_uint4(__funnelshift_r(oc.x, oc.y, 8), __funnelshift_r(oc.y, oc.z, 8),
+                                        __funnelshift_r(oc.z, oc.w, 8), __funnelshift_r(oc.w, next, 8));
                     }
-                    d.S[q] = own_s[i * nv + v];
-                    d.rowg[q] = (z * (uint32_t)a.L + y) * nv + v;
+                    d.set(q, own_s[i * nv + v], oc, xs, oth16[i * nv + v], oth16[(i + 2u) * nv + v],
+                          zm, zp, (z * (uint32_t)a.L + y) * nv + v);
                 }
             };
-            auto update = [&](Pair& d, const Philox4 (&u)[8]) {
-                int e_vec = 0;
-                if (RULE == kRuleHeatBath)
-                    update_vec_pair_hb<DIMS, MEASURE>(d.S, d.X, d.XS, d.YM, d.YP, d.ZM, d.ZP, u,
-                                                      s_thb, a, e_vec, m_neg);
-                else
-                    update_vec_pair<DIMS, MEASURE>(d.S, d.X, d.XS, d.YM, d.YP, d.ZM, d.ZP, u, a,
-                                                   e_vec, m_neg);
-                own_g[d.rowg[0]] = d.S[0];
-                own_g[d.rowg[1]] = d.S[1];
-                e_acc += e_vec;
+            auto finish = [&](const Pair& d) {
+                d.store(own_g, a, e_acc, m_neg);
                 n_vec += 2;
             };
-            // order: the first item's loads, the second item's calls, the first
-            // item's update, then the second item (measured 7 % faster than
-            // issuing the calls ahead of the loads)
+            auto update = [&](Pair& d, const Philox4 (&u)[8]) {
+#pragma unroll
+                for (int w = 0; w < 8; ++w) d.step(w, u[w], a, s_thb);
+                finish(d);
+            };
+            // the first item's update with the second item's calls: round r of
+            // the calls, then word r of the update (r < 8); the generator's
+            // multiplies and the update's logic interleave in the instruction
+            // stream (36.1 -> 35.2 us per pass at L = 8192, with the
+            // first-round shortcut)
+            auto update_drawing = [&](auto single, Pair& d, uint32_t next_item,
+                                      Philox4 (&u)[8]) {
+                PhiloxRuns8 ps;
+                start(single, next_item, ps);
+                d.step(0, u0[0], a, s_thb);
+#pragma unroll
+                for (int r = 1; r < 10; ++r) {
+                    ps.next_round();
+                    if (r < 8) d.step(r, u0[r], a, s_thb);
+                }
+                finish(d);
+#pragma unroll
+                for (int w = 0; w < 8; ++w) u[w] = ps.result(w);
+            };
+            // order: the first item's loads, then its update with the second
+            // item's calls, then the second item (the calls placed between
+            // the loads and the update measured 7 % faster than ahead of the
+            // loads)
             auto walk = [&](auto single) {
                 for (uint32_t base = threadIdx.x; base < n_items; base += 2u * blockDim.x) {
                     const uint32_t second = base + blockDim.x;
                     Pair d0;
                     load(single, base, d0);
                     Philox4 u1[8];
-                    draw(single, second, u1);  // counters only: harmless past the last item
-                    update(d0, u0);
+                    // counters only: harmless past the last item
+                    update_drawing(single, d0, second, u1);
                     if (second < n_items) {
                         Pair d1;
                         load(single, second, d1);
@@ -377,8 +404,7 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
                 Pair d0;
                 load(single, threadIdx.x, d0);
                 Philox4 u1[8];
-                draw(single, second, u1);
-                update(d0, u0);
+                update_drawing(single, d0, second, u1);
                 Pair d1;
                 load(single, second, d1);
                 update(d1, u1);
@@ -391,18 +417,15 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
                     update(d0, u0);
                 }
             };
-            if constexpr (TWO) {
+            if constexpr (WALK == kWalkTwo) {
                 if (pairs == 1u) walk_two(std::true_type{});
                 else walk_two(std::false_type{});
+            } else if constexpr (WALK == kWalkOne) {
+                if (pairs == 1u) walk_one(std::true_type{});
+                else walk_one(std::false_type{});
             } else {
-                const bool one = n_items <= blockDim.x;
-                if (pairs == 1u) {
-                    if (one) walk_one(std::true_type{});
-                    else walk(std::true_type{});
-                } else {
-                    if (one) walk_one(std::false_type{});
-                    else walk(std::false_type{});
-                }
+                if (pairs == 1u) walk(std::true_type{});
+                else walk(std::false_type{});
             }
             i0 = 2u * pairs;
         }
@@ -451,7 +474,7 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
     }
 }
 
-template <int DIMS, bool MEASURE, int RULE, bool TWO>
+template <int DIMS, bool MEASURE, int RULE, int WALK>
 cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uint32_t extra_tx,
                          cudaStream_t st, int rows_per_tile, int ctas_per_sm) {
     TmaGeom tg;
@@ -474,20 +497,20 @@ cudaError_t launch_tma_t(const PassArgs& a, const DeviceProps& dp, int* err, uin
     static int attr_set = 0;  // largest dynamic shared memory opted into so far
     cudaError_t e = cudaSuccess;
     if ((int)smem > attr_set) {
-        e = cudaFuncSetAttribute(pass_int8_tma<DIMS, MEASURE, RULE, TWO>,
+        e = cudaFuncSetAttribute(pass_int8_tma<DIMS, MEASURE, RULE, WALK>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = 200 * 1024;
     }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_int8_tma<DIMS, MEASURE, RULE, TWO>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_int8_tma<DIMS, MEASURE, RULE, WALK>,
                                                       threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     int grid = dp.sm_count * per_sm;
     if (grid > tg.tiles) grid = tg.tiles;
-    return launch_chained(pass_int8_tma<DIMS, MEASURE, RULE, TWO>, (unsigned)grid, (unsigned)threads,
+    return launch_chained(pass_int8_tma<DIMS, MEASURE, RULE, WALK>, (unsigned)grid, (unsigned)threads,
                           smem, st, a, tg, err);
 }
 
@@ -505,15 +528,15 @@ bool int8_tma_ok(int dims, int L, int rows_per_tile) {
     return (size_t)kStages * stage <= 200 * 1024;
 }
 
-template <int RULE, bool TWO>
+template <int RULE, int WALK>
 static cudaError_t int8_pass_tma_walk(const PassArgs& a, int dims, bool measure,
                                       const DeviceProps& dp, int* err, uint32_t extra_tx,
                                       cudaStream_t st, int R, int ctas) {
     if (dims == 2)
-        return measure ? launch_tma_t<2, true, RULE, TWO>(a, dp, err, extra_tx, st, R, ctas)
-                       : launch_tma_t<2, false, RULE, TWO>(a, dp, err, extra_tx, st, R, ctas);
-    return measure ? launch_tma_t<3, true, RULE, TWO>(a, dp, err, extra_tx, st, R, ctas)
-                   : launch_tma_t<3, false, RULE, TWO>(a, dp, err, extra_tx, st, R, ctas);
+        return measure ? launch_tma_t<2, true, RULE, WALK>(a, dp, err, extra_tx, st, R, ctas)
+                       : launch_tma_t<2, false, RULE, WALK>(a, dp, err, extra_tx, st, R, ctas);
+    return measure ? launch_tma_t<3, true, RULE, WALK>(a, dp, err, extra_tx, st, R, ctas)
+                   : launch_tma_t<3, false, RULE, WALK>(a, dp, err, extra_tx, st, R, ctas);
 }
 
 template <int RULE>
@@ -521,12 +544,19 @@ static cudaError_t int8_pass_tma_rule(const PassArgs& a, int dims, bool measure,
                                       const DeviceProps& dp, int* err, uint32_t extra_tx,
                                       cudaStream_t st, int R, int ctas) {
     if constexpr (RULE == kRuleMultiHit) {  // takes the row-at-a-time loop only
-        return int8_pass_tma_walk<RULE, false>(a, dims, measure, dp, err, extra_tx, st, R, ctas);
+        return int8_pass_tma_walk<RULE, kWalkLoop>(a, dims, measure, dp, err, extra_tx, st, R,
+                                                   ctas);
     } else {
         const int rows = R > 0 ? R : tile_rows(a.L);
-        const bool two = (rows / 2) * (a.W / 16) == 2 * 128;  // 128 threads per CTA
-        return two ? int8_pass_tma_walk<RULE, true>(a, dims, measure, dp, err, extra_tx, st, R, ctas)
-                   : int8_pass_tma_walk<RULE, false>(a, dims, measure, dp, err, extra_tx, st, R, ctas);
+        const int items = (rows / 2) * (a.W / 16);  // (row pair, column) items per tile
+        if (items == 2 * 128)                        // 128 threads per CTA
+            return int8_pass_tma_walk<RULE, kWalkTwo>(a, dims, measure, dp, err, extra_tx, st, R,
+                                                      ctas);
+        if (items <= 128)
+            return int8_pass_tma_walk<RULE, kWalkOne>(a, dims, measure, dp, err, extra_tx, st, R,
+                                                      ctas);
+        return int8_pass_tma_walk<RULE, kWalkLoop>(a, dims, measure, dp, err, extra_tx, st, R,
+                                                   ctas);
     }
 }
 
