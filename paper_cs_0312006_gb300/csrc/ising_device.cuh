@@ -74,28 +74,35 @@ __device__ __forceinline__ Philox4 philox4x32_10_split(uint32_t c0, uint32_t c1,
     return Philox4{c0, c1, c2, c3};
 }
 
-// Eight calls whose counter word 0 runs over two sets of four consecutive
-// values (a .. a + 3 and b .. b + 3, no 32-bit wrap), the other counter words
-// and the key shared, advanced one round at a time so that a caller can place
-// other work between the rounds.  In the first round the product of a + i is
-// the product of a plus i times the multiplier (a 64-bit add instead of a
-// multiply).  result(w) equals philox4x32_10(counter of call w, ...).
-struct PhiloxRuns8 {
-    uint32_t c0[8], c1[8], c2[8], c3[8];
+// 4 * RUNS calls whose counter word 0 runs over RUNS sets of four
+// consecutive values (base[r] .. base[r] + 3, no 32-bit wrap), the other
+// counter words and the key shared, advanced one round at a time so that a
+// caller can place other work between the rounds.  In the first round the
+// product of base + i is the product of base plus i times the multiplier (a
+// 64-bit add instead of a multiply).  result(w) equals philox4x32_10 of call
+// w's counter (base[w / 4] + w % 4, ctr1, ctr2, ctr3) under the same key.
+template <int RUNS>
+struct PhiloxRuns {
+    static constexpr int N = 4 * RUNS;
+    uint32_t c0[N], c1[N], c2[N], c3[N];
     uint32_t k0, k1;
 
-    __device__ __forceinline__ void first_round(uint32_t a, uint32_t b, uint32_t ctr1,
+    __device__ __forceinline__ void first_round(const uint32_t (&base)[RUNS], uint32_t ctr1,
                                                 uint32_t ctr2, uint32_t ctr3, uint32_t key0,
                                                 uint32_t key1) {
-        const uint64_t pa_a = (uint64_t)a * kPhiloxMulA, pa_b = (uint64_t)b * kPhiloxMulA;
         const uint64_t pb = (uint64_t)ctr2 * kPhiloxMulB;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            const uint64_t pa = (w < 4 ? pa_a : pa_b) + (uint64_t)(w & 3) * kPhiloxMulA;
-            c0[w] = (uint32_t)(pb >> 32) ^ ctr1 ^ key0;
-            c1[w] = (uint32_t)pb;
-            c2[w] = (uint32_t)(pa >> 32) ^ ctr3 ^ key1;
-            c3[w] = (uint32_t)pa;
+        for (int r = 0; r < RUNS; ++r) {
+            const uint64_t pa0 = (uint64_t)base[r] * kPhiloxMulA;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int w = 4 * r + i;
+                const uint64_t pa = pa0 + (uint64_t)i * kPhiloxMulA;
+                c0[w] = (uint32_t)(pb >> 32) ^ ctr1 ^ key0;
+                c1[w] = (uint32_t)pb;
+                c2[w] = (uint32_t)(pa >> 32) ^ ctr3 ^ key1;
+                c3[w] = (uint32_t)pa;
+            }
         }
         k0 = key0 + kPhiloxWeylA;
         k1 = key1 + kPhiloxWeylB;
@@ -103,7 +110,7 @@ struct PhiloxRuns8 {
 
     __device__ __forceinline__ void next_round() {
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
+        for (int w = 0; w < N; ++w) {
             const uint64_t pa = (uint64_t)c0[w] * kPhiloxMulA;
             const uint64_t pb = (uint64_t)c2[w] * kPhiloxMulB;
             c0[w] = (uint32_t)(pb >> 32) ^ c1[w] ^ k0;

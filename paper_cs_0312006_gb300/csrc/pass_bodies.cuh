@@ -649,13 +649,14 @@ __device__ __forceinline__ uint32_t packed_accept(const K& k, uint32_t need, uin
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             if (!((need >> (16 * half)) & 0xFFFFu)) continue;
-            Philox4 u[4];
+            // four consecutive groups: one first-round product for the four
+            PhiloxRuns<1> ps;
+            const uint32_t base[1] = {g0 + (uint32_t)(4 * half)};
+            ps.first_round(base, a.t, c2, kTagSweep, a.key0, a.key1);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                u[i] = philox4x32_10(g0 + (uint32_t)(4 * half + i), a.t, c2, kTagSweep, a.key0,
-                                     a.key1);
+            for (int r = 1; r < 10; ++r) ps.next_round();
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc |= group_accept<DIMS>(k, u[i], 4 * half + i, a);
+            for (int i = 0; i < 4; ++i) acc |= group_accept<DIMS>(k, ps.result(i), 4 * half + i, a);
         }
         return acc;
     }

@@ -258,18 +258,19 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
         // a thread's first eight Philox calls depend only on counters: they
         // run while the tile's copies land.  An item's calls are two runs of
         // four consecutive groups (its two rows), so they go through
-        // PhiloxRuns8; `start` makes the first round, and the caller runs the
-        // other nine, alone (draw) or between other work (walk).
+        // PhiloxRuns<2>; `start` makes the first round, and the caller runs
+        // the other nine, alone (draw) or between other work (walk).
         Philox4 u0[8];
-        auto start = [&](auto single, uint32_t item, PhiloxRuns8& ps) {
+        using Runs = PhiloxRuns<2>;
+        auto start = [&](auto single, uint32_t item, Runs& ps) {
             uint32_t pr = 0u, v = item;
             if constexpr (!decltype(single)::value) split(item, pr, v);
             const uint32_t rg = (z * (uint32_t)a.L + y0 + 2u * pr) * nv + v;
-            ps.first_round(rg * 4u, (rg + nv) * 4u, a.t, (uint32_t)a.c, kTagSweep, a.key0,
-                           a.key1);
+            const uint32_t base[2] = {rg * 4u, (rg + nv) * 4u};
+            ps.first_round(base, a.t, (uint32_t)a.c, kTagSweep, a.key0, a.key1);
         };
         auto draw = [&](auto single, uint32_t item, Philox4 (&u)[8]) {
-            PhiloxRuns8 ps;
+            Runs ps;
             start(single, item, ps);
 #pragma unroll
             for (int r = 1; r < 10; ++r) ps.next_round();
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, 
             // first-round shortcut)
             auto update_drawing = [&](auto single, Pair& d, uint32_t next_item,
                                       Philox4 (&u)[8]) {
-                PhiloxRuns8 ps;
+                Runs ps;
                 start(single, next_item, ps);
                 d.step(0, u0[0], a, s_thb);
 #pragma unroll
