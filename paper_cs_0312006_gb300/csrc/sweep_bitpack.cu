@@ -35,7 +35,9 @@ namespace {
 // L = 64 nq; in 3D l_shift = log2 L): an item's row, word and neighbours come
 // from shifts and masks, every row starts on a Philox group, and a thread
 // loads its next item's six words (eight in 3D) before it updates the current
-// one, so that their latency hides behind the current item's draws.
+// one, so that their latency hides behind the current item's draws (at most
+// 64 registers for four CTAs per SM measured slower: 2D L = 8192 29.2 ->
+// 29.4 us per pass, 3D L = 256 9.0e11 -> 8.0e11 site updates/s).
 template <int DIMS, bool MEASURE, int RULE, bool FULL>
 __global__ void __launch_bounds__(256, 3) pass_packed(PassArgs a, uint32_t rgroups,
                                                       uint32_t nq_shift, uint32_t l_shift) {

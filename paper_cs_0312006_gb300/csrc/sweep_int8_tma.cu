@@ -207,11 +207,12 @@ struct PairUpdate {
 // WALK: kWalkTwo when every thread has exactly two (row pair, column) items
 // per tile (R / 2 * W / 16 == 2 * 128), kWalkOne when it has at most one,
 // kWalkLoop otherwise.  The first two instances hold no loop over items and no
-// guard, which keeps them clear of the register cap.
+// guard, which keeps them clear of the register cap; the one-item instance
+// fits five CTAs per SM (at most 102 registers: 3D tiles of 32 rows).
 constexpr int kWalkLoop = 0, kWalkTwo = 1, kWalkOne = 2;
 
 template <int DIMS, bool MEASURE, int RULE, int WALK>
-__global__ void __launch_bounds__(128, 4) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
+__global__ void __launch_bounds__(128, WALK == kWalkOne ? 5 : 4) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kStages];
     __shared__ uint32_t s_thb[8];  // heat bath: thr[d] by d, read per site
