@@ -208,11 +208,12 @@ struct PairUpdate {
 // per tile (R / 2 * W / 16 == 2 * 128), kWalkOne when it has at most one,
 // kWalkLoop otherwise.  The first two instances hold no loop over items and no
 // guard, which keeps them clear of the register cap; the one-item instance
-// fits five CTAs per SM (at most 102 registers: 3D tiles of 32 rows).
+// runs six CTAs per SM (at most 85 registers; 3D L = 256 with 32-row tiles:
+// 6.7e11 at four, 7.0e11 at five, 7.2e11 site updates/s at six).
 constexpr int kWalkLoop = 0, kWalkTwo = 1, kWalkOne = 2;
 
 template <int DIMS, bool MEASURE, int RULE, int WALK>
-__global__ void __launch_bounds__(128, WALK == kWalkOne ? 5 : 4) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
+__global__ void __launch_bounds__(128, WALK == kWalkOne ? 6 : 4) pass_int8_tma(PassArgs a, TmaGeom tg, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kStages];
     __shared__ uint32_t s_thb[8];  // heat bath: thr[d] by d, read per site
