@@ -1,9 +1,9 @@
 // sweep_int8_tma.cu -- the int8 colour pass with its inputs staged in shared
 // memory by the Tensor Memory Accelerator (bulk asynchronous copies).
 //
-// Same arithmetic and draws as the register-window strip kernel
-// (sweep_int8.cu, update_vec in pass_bodies.cuh); only the data movement
-// differs.  A tile is a band of R consecutive half rows of one plane (full
+// Same rule and draws as the register-window strip kernel (sweep_int8.cu,
+// update_vec in pass_bodies.cuh); the data movement and the order of the work
+// differ.  A tile is a band of R consecutive half rows of one plane (full
 // width W = L/2 bytes, W % 16 == 0).  For each tile one thread issues
 // cp.async.bulk copies of
 //   - the tile's own-colour rows (R*W contiguous bytes),
@@ -13,10 +13,13 @@
 //   - for 3D, the other colour's bands in planes z-1 and z+1,
 // into one of S pipeline stages, completing on that stage's mbarrier.
 // Persistent CTAs walk their tiles while the copies for the next S-1 tiles
-// are in flight.  Every thread owns 16-byte columns of the band and slides
-// down them, reading its neighbour rows from shared memory (x-neighbour edge
-// bytes from the adjacent column in shared memory, so no shuffles), and
-// writes its updated vectors straight to global memory.
+// are in flight.  A tile's work items are (row pair, 16-byte column); a
+// thread takes its items two at a time, reads each item's own and neighbour
+// rows from shared memory (x-neighbour edge bytes from the adjacent column,
+// so no shuffles), and writes the updated vectors straight to global memory.
+// Its Philox calls run from counters alone: the first item's while the
+// tile's copies land, the second item's round by round between the first
+// item's word updates.
 //
 // Waits on an mbarrier are bounded: if a phase does not complete within the
 // limit the kernel raises the error flag, waits (bounded again) for its own

@@ -58,3 +58,13 @@ def test_measured_traffic_follows_the_kernel_sources():
             assert got is None
         assert bench.measured_traffic(workload, layout, 10, rule="heatbath") is None
     assert bench.measured_traffic("cubic", "int8", 10) is None
+
+
+def test_source_hash_ignores_comments_but_not_code():
+    """A comment edit keeps a traffic capture valid; a code edit does not."""
+    import bench
+    src = "int f(int x) {  // doubles\n    /* the\n       product */ return 2 * x;\n}\n"
+    same = "// header\nint f(int x) {   \n    return 2 * x;  // changed comment\n}\n\n"
+    other = "int f(int x) {\n    return 3 * x;\n}\n"
+    assert bench.code_only(src) == bench.code_only(same)
+    assert bench.code_only(src) != bench.code_only(other)
