@@ -7,8 +7,8 @@ fallback: without the compiled library, ``engine.load_library()`` raises.
 """
 from .engine import (AUTO, BITPACK, COLD_DOWN, COLD_UP, HOT, INT8, RULE_DEMON,  # noqa: F401
                      RULE_HEATBATH, RULE_METROPOLIS, RULE_MULTIHIT, Batch, IsingError, Lattice,
-                     load_library, observables_gather)
+                     batch_run, batch_run_static, load_library, observables_gather)
 
 __all__ = ["Lattice", "Batch", "IsingError", "load_library", "INT8", "BITPACK", "AUTO", "HOT",
            "COLD_UP", "COLD_DOWN", "RULE_METROPOLIS", "RULE_HEATBATH", "RULE_DEMON", "RULE_MULTIHIT",
-           "observables_gather"]
+           "batch_run", "batch_run_static", "observables_gather"]
