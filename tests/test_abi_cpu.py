@@ -154,3 +154,14 @@ def test_int8_configuration_arguments_checked_on_host():
         assert ei.value.code == engine.EINVAL
     engine.set_int8_config(3, 16, 256, kernel=2, tile_rows=4, ctas_per_sm=2)
     engine.clear_int8_configs()
+
+
+def test_package_exports_the_public_python_api():
+    """Every name of the package's public API resolves (the README's calls)."""
+    import paper_cs_0312006_gb300 as ising
+    from paper_cs_0312006_gb300 import percolation
+    for name in ising.__all__:
+        assert hasattr(ising, name), name
+    for name in ("Lattice", "Batch", "batch_run", "batch_run_static", "observables_gather"):
+        assert callable(getattr(ising, name))
+    assert callable(percolation.batch) and hasattr(percolation, "FACE")
