@@ -633,7 +633,10 @@ def run_gpu(args, world, rank, local):
                 {"value": world * len(betas) * n_sites * e2e_steps / dt,
                  "seconds": dt, "h2d_bytes": h2d, "d2h_bytes": d2h,
                  "h2d_bytes_per_step": h2d / e2e_steps,
-                 "d2h_bytes_per_step": d2h / e2e_steps})
+                 "d2h_bytes_per_step": d2h / e2e_steps,
+                 # the copies' bytes over the leg's wall time (they overlap
+                 # the sweeps, so this is what the job moved, not a link rate)
+                 "h2d_gb_per_s": h2d / dt / 1e9, "d2h_gb_per_s": d2h / dt / 1e9})
         for name, legs in e2e.items():
             med = sorted(legs, key=lambda x: x["value"])[len(legs) // 2]
             e2e[name] = dict(med, repeats=[x["value"] for x in legs])
@@ -641,7 +644,9 @@ def run_gpu(args, world, rank, local):
         head_e2e = e2e[head]
         e2e = {"value": head_e2e["value"], "unit": "site updates/s",
                "h2d_bytes_per_step": head_e2e["h2d_bytes_per_step"],
-               "d2h_bytes_per_step": head_e2e["d2h_bytes_per_step"], "steps": e2e_steps,
+               "d2h_bytes_per_step": head_e2e["d2h_bytes_per_step"],
+               "h2d_gb_per_s": head_e2e["h2d_gb_per_s"],
+               "d2h_gb_per_s": head_e2e["d2h_gb_per_s"], "steps": e2e_steps,
                "layout": head, "layouts": e2e,
                "over_device_value": head_e2e["value"] / value,
                "note": "per layout: every lattice's initial spins copied from pinned host "
