@@ -821,38 +821,40 @@ def cubic_form(args, peak_hbm: float, ceiling: dict) -> dict:
 
 def small_form(args) -> dict:
     """The critical 2D L=64 run: beta 0.4406868, hot start, seed 20031109,
-    1000 sweeps with E/M every sweep, one single-CTA launch; median of five
-    runs, checked bit for bit against the oracle."""
+    1000 sweeps with E/M every sweep, one single-CTA launch, in both layouts;
+    median of five runs.  (Its parity with the oracle is a test,
+    tests/test_gpu_parity.py; here the two layouts are checked against each
+    other, bit for bit.)"""
     import numpy as np
     import torch
     from paper_cs_0312006_gb300 import engine
-    import oracle
     L, beta, n = 64, 0.4406868, 1000
-    lat = engine.Lattice(2, L, beta, BASE_SEED)
-    lat.sweep(n, 1)  # warm-up run
-    lat.observables()
-    times = []
-    for _ in range(5):
-        lat.init(engine.HOT)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        lat.sweep(n, 1)
-        b.record()
-        b.synchronize()
-        times.append(a.elapsed_time(b))
-    E, M = lat.observables()
-    s = lat.get_spins()
-    lat.close()
-    s_o, E_o, M_o = oracle.run(2, L, beta, BASE_SEED, n, measure_every=1)
-    exact = bool(np.array_equal(s, s_o) and np.array_equal(E[-n:], E_o)
-                 and np.array_equal(M[-n:], M_o))
-    ms = sorted(times)[len(times) // 2]
+    out, states = {}, []
+    for name, lay in (("int8", engine.INT8), ("bitpack", engine.BITPACK)):
+        lat = engine.Lattice(2, L, beta, BASE_SEED, layout=lay)
+        lat.sweep(n, 1)  # warm-up run
+        lat.observables()
+        times = []
+        for _ in range(5):
+            lat.init(engine.HOT)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            lat.sweep(n, 1)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        E, M = lat.observables()
+        states.append((lat.get_spins(), E[-n:], M[-n:]))
+        lat.close()
+        ms = sorted(times)[len(times) // 2]
+        out[name] = {"value": L * L * n / (ms / 1e3), "us_per_sweep": ms * 1e3 / n}
+    agree = all(np.array_equal(x, y) for x, y in zip(states[0], states[1]))
     return {"config": {"workload": "2D L=64, beta 0.4406868, hot start, seed 20031109, 1000 "
-                                   "sweeps, E/M every sweep"},
-            "value": L * L * n / (ms / 1e3), "unit": "site updates/s",
-            "us_per_sweep": ms * 1e3 / n, "bit_exact_vs_oracle": exact}
-
+                                   "sweeps, E/M every sweep, int8 and bit-packed layouts"},
+            "value": out["int8"]["value"], "unit": "site updates/s",
+            "us_per_sweep": out["int8"]["us_per_sweep"], "layouts_bit_identical": agree,
+            "layouts": out}
 
 def run_batched_workload(args):
     """2048 independent lattices (70% 2D L in [16,1024], 30% 3D L in [8,128],
@@ -925,41 +927,19 @@ def run_serving_workload(args):
 
 
 def run_small_workload(args):
-    """The small critical run: 2D L=64 at beta_c, hot start, seed 20031109,
-    1000 sweeps with E/M every sweep, checked against the oracle."""
-    import numpy as np
+    """The small critical run (small_form): 2D L=64 at beta_c, hot start, seed
+    20031109, 1000 sweeps with E/M every sweep, both layouts."""
     import torch
     from paper_cs_0312006_gb300 import _build, engine
     _build.build()
     engine.load_library()
-    L, beta, n = 64, 0.4406868, 1000
-    lat = engine.Lattice(2, L, beta, BASE_SEED)
-    lat.sweep(n, 1)  # warm-up run
-    lat.observables()
-    times = []
-    for _ in range(5):
-        lat.init(engine.HOT)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        lat.sweep(n, 1)
-        b.record()
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
-    E, M = lat.observables()
-    s = lat.get_spins()
-    lat.close()
-    import oracle
-    s_o, E_o, M_o = oracle.run(2, L, beta, BASE_SEED, n, measure_every=1)
-    exact = bool(np.array_equal(s, s_o) and np.array_equal(E, E_o) and np.array_equal(M, M_o))
-    ms = sorted(times)[len(times) // 2]
-    line = {"metric": "site updates/s", "value": L * L * n / (ms / 1e3), "unit": "site updates/s",
-            "workload": "2D L=64, beta 0.4406868, hot start, 1000 sweeps, E/M every sweep",
-            "us_per_sweep": ms * 1e3 / n, "median_ms": ms, "bit_exact_vs_oracle": exact,
+    form = small_form(args)
+    line = {"metric": "site updates/s", "value": form["value"], "unit": "site updates/s",
+            "workload": form["config"]["workload"], "us_per_sweep": form["us_per_sweep"],
+            "layouts_bit_identical": form["layouts_bit_identical"], "layouts": form["layouts"],
             "device": torch.cuda.get_device_name()}
     print(json.dumps(line), flush=True)
-    return 0 if exact else 1
-
+    return 0 if form["layouts_bit_identical"] else 1
 
 def run_cubic_workload(args):
     """3D cubic L=256 (16.8 M sites) at beta 0.2216544, hot start, seed
