@@ -128,6 +128,20 @@ def measured_traffic(workload: str, layout: str, updates_per_launch: int,
     return t["bytes_per_update"] * updates_per_launch
 
 
+def issue_schedule(n_lattices: int, steps: int, order: str = "wave"):
+    """The e2e leg's issue order: a list of wavefronts, each a list of
+    (lattice, sweep) pairs.  "step": wavefront k holds every lattice's sweep
+    k.  "wave": lattice j's sweep k is in wavefront k + j, so lattice j starts
+    j wavefronts after lattice 0 (its upload has more of the others' sweeps to
+    hide behind) and every lattice still runs its sweeps in order."""
+    skew = 1 if order == "wave" else 0
+    waves = []
+    for wave in range(steps + skew * (n_lattices - 1)):
+        waves.append([(j, wave - skew * j) for j in range(n_lattices)
+                      if 0 <= wave - skew * j < steps])
+    return waves
+
+
 def max_over_ranks(value: float, world: int, device=None) -> float:
     """The largest of every rank's value (the job's time is its slowest rank)."""
     if world <= 1:
@@ -615,13 +629,9 @@ def run_gpu(args, world, rank, local):
             # ones are still copied (the lattices are independent: the same
             # sweeps and results, only their interleaving differs); one
             # records gather per wavefront
-            skew = 1 if args.e2e_order == "wave" else 0
-            n_waves = e2e_steps + skew * (len(lats) - 1)
-            for wave in range(n_waves):
-                for j, lat in enumerate(lats):
-                    k = wave - skew * j
-                    if k < 0 or k >= e2e_steps:
-                        continue
+            for wave, work in enumerate(issue_schedule(len(lats), e2e_steps, args.e2e_order)):
+                for j, k in work:
+                    lat = lats[j]
                     if k == 0:
                         if direct:  # the import kernel reads the pinned host buffer itself
                             lat.set_spins_async(host_init.data_ptr(), 0)

@@ -68,3 +68,23 @@ def test_source_hash_ignores_comments_but_not_code():
     other = "int f(int x) {\n    return 3 * x;\n}\n"
     assert bench.code_only(src) == bench.code_only(same)
     assert bench.code_only(src) != bench.code_only(other)
+
+
+@pytest.mark.parametrize("order", ["step", "wave"])
+@pytest.mark.parametrize("n_lat,steps", [(1, 1), (16, 20), (16, 3), (3, 16)])
+def test_e2e_issue_schedule_runs_every_sweep_once_in_order(order, n_lat, steps):
+    """Every (lattice, sweep) pair is issued exactly once, each lattice's
+    sweeps in increasing order, at most one sweep per lattice per wavefront;
+    in wave order lattice j starts in wavefront j."""
+    import bench
+    waves = bench.issue_schedule(n_lat, steps, order)
+    seen = [(j, k) for w in waves for (j, k) in w]
+    assert sorted(seen) == [(j, k) for j in range(n_lat) for k in range(steps)]
+    for w in waves:
+        assert len({j for j, _ in w}) == len(w)
+    for j in range(n_lat):
+        ks = [k for w in waves for (jj, k) in w if jj == j]
+        assert ks == list(range(steps))
+        first = next(i for i, w in enumerate(waves) if any(jj == j for jj, _ in w))
+        assert first == (j if order == "wave" else 0)
+    assert len(waves) == steps + (n_lat - 1 if order == "wave" else 0)
