@@ -613,6 +613,7 @@ def run_gpu(args, world, rank, local):
             t0 = time.perf_counter()
             h2d = d2h = 0
             host_sum = 0
+            n_valid = [0, 0]  # records gathered into each half of the pinned buffer
             uploaded = []
             direct = args.e2e_mode == "direct"
             if not direct:
@@ -653,14 +654,15 @@ def run_gpu(args, world, rank, local):
                                 host_out[j].copy_(dev_out[j], non_blocking=True)
                         d2h += n_sites
                 half = wave % 2
-                d2h += 16 * int(engine.observables_gather(lats, pairs[half]).sum())
+                n_valid[half] = int(engine.observables_gather(lats, pairs[half]).sum())
+                d2h += 16 * n_valid[half]
                 ready[half].record(stream)
                 if last is not None:
                     ready[last].synchronize()
-                    host_sum += int(pairs[last, :, 0].sum())
+                    host_sum += int(pairs[last, :n_valid[last], 0].sum())
                 last = half
             torch.cuda.synchronize()
-            host_sum += int(pairs[last, :, 0].sum())
+            host_sum += int(pairs[last, :n_valid[last], 0].sum())
             dt = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
             for lat in lats:
                 lat.synchronize()  # a bounded wait or an invalid input would be reported here
@@ -671,7 +673,9 @@ def run_gpu(args, world, rank, local):
                  "d2h_bytes_per_step": d2h / e2e_steps,
                  # the copies' bytes over the leg's wall time (they overlap
                  # the sweeps, so this is what the job moved, not a link rate)
-                 "h2d_gb_per_s": h2d / dt / 1e9, "d2h_gb_per_s": d2h / dt / 1e9})
+                 "h2d_gb_per_s": h2d / dt / 1e9, "d2h_gb_per_s": d2h / dt / 1e9,
+                 # the host's own sum of every E record it read (same for every leg)
+                 "records_E_sum": host_sum})
         for name, legs in e2e.items():
             med = sorted(legs, key=lambda x: x["value"])[len(legs) // 2]
             e2e[name] = dict(med, repeats=[x["value"] for x in legs])
